@@ -1,0 +1,283 @@
+"""FP64 oracle of the CoNet receiver network, its BCE loss, backward pass and Adam.
+
+Architecture (Sec. III, Fig. "Example I", Fig. RB, Fig. MRB; readings O7-O13):
+
+* Branch 0 is the main net, branches 1..M the support nets; every branch sees the
+  whole input grid (Sec. III: the TTI is processed concurrently by all subnets).
+* Input layer of every branch: 3x3 conv + bias + ReLU.
+* Plain networks: ``depth`` 3x3 conv + ReLU layers per branch (the input layer
+  included).  Residual networks: input layer then ``depth`` blocks; support branches
+  use the pre-activation residual block RB (LN -> ReLU -> conv -> LN -> ReLU -> conv,
+  plus the skip), the main branch the modified block MRB (the RB without its first
+  normalisation, because its input was normalised right after the fusion).
+* Fusion after layer / block i (bit i of ``fuse_mask``): the main activation becomes
+  the element-wise (Hadamard) product of the main and all support activations,
+  followed by LayerNorm over channels when ``norm`` is set; the support branches
+  continue with their own unfused activations.
+* Head: 1x1 conv of the main activation to Q LLRs per resource element.
+
+3x3 convolutions are 'same' (zero padding 1 on the symbol and subcarrier axes), with
+bias, weights laid out [C_out][3][3][C_in] and activations channels-last [B,T,F,C].
+A tiny reverse-mode tape gives the gradients; every op's backward is its textbook
+derivative.  LayerNorm uses eps = 1e-5.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LN_EPS = 1e-5
+ADAM_BETA1 = 0.9
+ADAM_BETA2 = 0.999
+ADAM_EPS = 1e-8
+
+
+# ----------------------------------------------------------------------------- parameters
+def param_layout(cfg):
+    """Ordered list of (name, shape) of the flat float parameter vector."""
+    C, Q = cfg.width, cfg.qam_bits
+    out = []
+    for b in range(cfg.n_branches):
+        out += [(f"b{b}.in.w", (C, 3, 3, cfg.c_in)), (f"b{b}.in.b", (C,))]
+        if not cfg.residual:
+            for l in range(1, cfg.depth):
+                out += [(f"b{b}.l{l}.w", (C, 3, 3, C)), (f"b{b}.l{l}.b", (C,))]
+        else:
+            for k in range(cfg.depth):
+                if b >= 1 or cfg.resnet_baseline:
+                    out += [(f"b{b}.k{k}.ln1.g", (C,)), (f"b{b}.k{k}.ln1.b", (C,))]
+                out += [(f"b{b}.k{k}.c1.w", (C, 3, 3, C)), (f"b{b}.k{k}.c1.b", (C,)),
+                        (f"b{b}.k{k}.ln2.g", (C,)), (f"b{b}.k{k}.ln2.b", (C,)),
+                        (f"b{b}.k{k}.c2.w", (C, 3, 3, C)), (f"b{b}.k{k}.c2.b", (C,))]
+    if cfg.norm:
+        n_points = cfg.depth + 1 if cfg.residual else cfg.depth
+        for i in range(n_points):
+            if cfg.fused(i):
+                out += [(f"f{i}.g", (C,)), (f"f{i}.b", (C,))]
+    out += [("head.w", (Q, C)), ("head.b", (Q,))]
+    return out
+
+
+def param_count(cfg) -> int:
+    return int(sum(np.prod(s) for _, s in param_layout(cfg)))
+
+
+def unflatten(cfg, flat):
+    P, o = {}, 0
+    for name, shape in param_layout(cfg):
+        n = int(np.prod(shape))
+        P[name] = flat[o:o + n].reshape(shape)
+        o += n
+    assert o == flat.size, (o, flat.size)
+    return P
+
+
+def init_params(cfg, seed: int) -> np.ndarray:
+    """He-normal weights (std sqrt(2 / fan_in), fan_in = 9 C_in for 3x3 convs, C for the
+    head), zero biases, LayerNorm gain 1 and shift 0 (O13 reading)."""
+    g = np.random.default_rng(seed)
+    parts = []
+    for name, shape in param_layout(cfg):
+        if name.endswith(".w"):
+            fan_in = int(np.prod(shape[1:]))
+            parts.append(g.standard_normal(shape).ravel() * np.sqrt(2.0 / fan_in))
+        elif name.endswith(".g"):
+            parts.append(np.ones(int(np.prod(shape))))
+        else:
+            parts.append(np.zeros(int(np.prod(shape))))
+    return np.concatenate(parts)
+
+
+# ----------------------------------------------------------------------------- tape
+class Tape:
+    """Minimal reverse-mode recorder: values, and per op (inputs, backward fn)."""
+
+    def __init__(self):
+        self.vals, self.recs = [], []
+
+    def leaf(self, v):
+        self.vals.append(v)
+        self.recs.append(None)
+        return len(self.vals) - 1
+
+    def op(self, v, inputs, grad_fn):
+        self.vals.append(v)
+        self.recs.append((inputs, grad_fn))
+        return len(self.vals) - 1
+
+    def __getitem__(self, i):
+        return self.vals[i]
+
+    def backward(self, out, g_out):
+        grads = {out: g_out}
+        for i in range(len(self.vals) - 1, -1, -1):
+            rec = self.recs[i]
+            if rec is None or i not in grads:
+                continue
+            inputs, fn = rec
+            for j, g in zip(inputs, fn(grads[i])):
+                grads[j] = grads[j] + g if j in grads else g
+        return grads
+
+
+def _pad(x):
+    return np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
+
+
+def conv3x3(tp, x, w, b):
+    X, W, bias = tp[x], tp[w], tp[b]
+    B, T, F, _ = X.shape
+    Xp = _pad(X)
+    out = np.broadcast_to(bias, (B, T, F, W.shape[0])).copy()
+    for kh in range(3):
+        for kw in range(3):
+            out += Xp[:, kh:kh + T, kw:kw + F, :] @ W[:, kh, kw, :].T
+
+    def grad(g):
+        dXp = np.zeros_like(Xp)
+        dW = np.zeros_like(W)
+        for kh in range(3):
+            for kw in range(3):
+                dXp[:, kh:kh + T, kw:kw + F, :] += g @ W[:, kh, kw, :]
+                dW[:, kh, kw, :] = np.einsum("btfo,btfi->oi", g, Xp[:, kh:kh + T, kw:kw + F, :])
+        return dXp[:, 1:T + 1, 1:F + 1, :], dW, g.sum(axis=(0, 1, 2))
+
+    return tp.op(out, (x, w, b), grad)
+
+
+def relu(tp, x):
+    X = tp[x]
+
+    def grad(g):
+        return (g * (X > 0),)
+
+    return tp.op(np.maximum(X, 0.0), (x,), grad)
+
+
+def layernorm(tp, x, gam, bet):
+    X, G, Bt = tp[x], tp[gam], tp[bet]
+    mu = X.mean(-1, keepdims=True)
+    var = ((X - mu) ** 2).mean(-1, keepdims=True)
+    r = 1.0 / np.sqrt(var + LN_EPS)
+    xh = (X - mu) * r
+
+    def grad(g):
+        dxh = g * G
+        dx = r * (dxh - dxh.mean(-1, keepdims=True) - xh * (dxh * xh).mean(-1, keepdims=True))
+        return dx, (g * xh).sum(axis=(0, 1, 2)), g.sum(axis=(0, 1, 2))
+
+    return tp.op(xh * G + Bt, (x, gam, bet), grad)
+
+
+def hadamard(tp, xs):
+    vals = [tp[x] for x in xs]
+    out = vals[0].copy()
+    for v in vals[1:]:
+        out = out * v
+
+    def grad(g):
+        gs = []
+        for j in range(len(vals)):
+            o = g.copy()
+            for i, v in enumerate(vals):
+                if i != j:
+                    o = o * v
+            gs.append(o)
+        return tuple(gs)
+
+    return tp.op(out, tuple(xs), grad)
+
+
+def add(tp, x, y):
+    return tp.op(tp[x] + tp[y], (x, y), lambda g: (g, g))
+
+
+def head1x1(tp, x, w, b):
+    X, W, bias = tp[x], tp[w], tp[b]
+
+    def grad(g):
+        return g @ W, np.einsum("btfq,btfc->qc", g, X), g.sum(axis=(0, 1, 2))
+
+    return tp.op(X @ W.T + bias, (x, w, b), grad)
+
+
+# ----------------------------------------------------------------------------- network
+def forward(cfg, flat, X0, keep_tape=False):
+    """LLR [B, T, F, Q] of the CoNet described by ``cfg`` with flat parameters ``flat``."""
+    tp = Tape()
+    P = unflatten(cfg, np.asarray(flat, dtype=np.float64))
+    ids = {k: tp.leaf(v) for k, v in P.items()}
+    x_in = tp.leaf(np.asarray(X0, dtype=np.float64))
+    nb = cfg.n_branches
+
+    def fuse(i, acts):
+        if not cfg.fused(i):
+            return list(acts)
+        m = hadamard(tp, acts)
+        if cfg.norm:
+            m = layernorm(tp, m, ids[f"f{i}.g"], ids[f"f{i}.b"])
+        return [m] + list(acts[1:])
+
+    acts = [relu(tp, conv3x3(tp, x_in, ids[f"b{b}.in.w"], ids[f"b{b}.in.b"])) for b in range(nb)]
+    x = fuse(0, acts)
+    if not cfg.residual:
+        for l in range(1, cfg.depth):
+            acts = [relu(tp, conv3x3(tp, x[b], ids[f"b{b}.l{l}.w"], ids[f"b{b}.l{l}.b"]))
+                    for b in range(nb)]
+            x = fuse(l, acts)
+    else:
+        for k in range(cfg.depth):
+            u = []
+            for b in range(nb):
+                p = f"b{b}.k{k}."
+                if b >= 1 or cfg.resnet_baseline:
+                    h1 = relu(tp, layernorm(tp, x[b], ids[p + "ln1.g"], ids[p + "ln1.b"]))
+                else:
+                    h1 = relu(tp, x[b])
+                t1 = conv3x3(tp, h1, ids[p + "c1.w"], ids[p + "c1.b"])
+                h2 = relu(tp, layernorm(tp, t1, ids[p + "ln2.g"], ids[p + "ln2.b"]))
+                u.append(add(tp, x[b], conv3x3(tp, h2, ids[p + "c2.w"], ids[p + "c2.b"])))
+            x = fuse(k + 1, u)
+    llr = head1x1(tp, x[0], ids["head.w"], ids["head.b"])
+    if keep_tape:
+        return tp[llr], (tp, llr, ids, x_in)
+    return tp[llr]
+
+
+def bce_loss(llr, bits, pilot_mask):
+    """Mean BCE-with-logits over data REs and bits, and its gradient w.r.t. the LLRs:
+    l = softplus(L) - b L = max(L, 0) - b L + log1p(exp(-|L|)); dl/dL = sigmoid(L) - b."""
+    data = (~pilot_mask.astype(bool))[None, :, :, None]
+    count = llr.shape[0] * int(data.sum()) * llr.shape[-1]
+    b = bits.astype(np.float64)
+    per = np.maximum(llr, 0.0) - b * llr + np.log1p(np.exp(-np.abs(llr)))
+    loss = float((per * data).sum() / count)
+    sig = 1.0 / (1.0 + np.exp(-llr))
+    dllr = (sig - b) * data / count
+    return loss, dllr
+
+
+def backward(cfg, tape_info, dllr):
+    """Flat parameter gradient (same layout as the parameters) and dX0 for dLLR."""
+    tp, out, ids, x_in = tape_info
+    grads = tp.backward(out, np.asarray(dllr, dtype=np.float64))
+    parts = []
+    for name, shape in param_layout(cfg):
+        g = grads.get(ids[name])
+        parts.append(np.zeros(int(np.prod(shape))) if g is None else np.asarray(g).ravel())
+    return np.concatenate(parts), grads.get(x_in)
+
+
+def loss_and_grad(cfg, flat, X0, bits, pilot_mask):
+    llr, info = forward(cfg, flat, X0, keep_tape=True)
+    loss, dllr = bce_loss(llr, bits, pilot_mask)
+    g, _ = backward(cfg, info, dllr)
+    return loss, g, llr
+
+
+def adam_step(w, g, m, v, step: int, lr: float, beta1=ADAM_BETA1, beta2=ADAM_BETA2, eps=ADAM_EPS):
+    """One bias-corrected Adam update (Kingma & Ba 2015), ``step`` counted from 1."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** step)
+    vh = v / (1.0 - beta2 ** step)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v

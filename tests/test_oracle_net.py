@@ -1,0 +1,198 @@
+"""Pins of the oracle's CoNet network: brute-force 3x3 convolution on tiny tensors,
+1x1 / identity special cases, LayerNorm moments, structural invariants of the
+Hadamard fusion (support nets that output 1 leave the main net alone; support nets
+commute), identity residual blocks, central finite differences of the whole
+forward + BCE loss (rel. err <= 1e-6), and Adam's closed-form first step."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import net as onet
+from workloads import tiny_net, replace
+
+
+def brute_conv(x, w, b):
+    B, T, F, Ci = x.shape
+    Co = w.shape[0]
+    out = np.zeros((B, T, F, Co))
+    for bb, t, f, o in itertools.product(range(B), range(T), range(F), range(Co)):
+        acc = b[o]
+        for kh, kw, i in itertools.product(range(3), range(3), range(Ci)):
+            tt, ff = t + kh - 1, f + kw - 1
+            if 0 <= tt < T and 0 <= ff < F:
+                acc += w[o, kh, kw, i] * x[bb, tt, ff, i]
+        out[bb, t, f, o] = acc
+    return out
+
+
+def run_conv(x, w, b):
+    tp = onet.Tape()
+    return tp[onet.conv3x3(tp, tp.leaf(x), tp.leaf(w), tp.leaf(b))]
+
+
+def test_conv3x3_matches_brute_force():
+    g = np.random.default_rng(0)
+    x = g.standard_normal((2, 4, 5, 3))
+    w = g.standard_normal((2, 3, 3, 3))
+    b = g.standard_normal(2)
+    assert np.allclose(run_conv(x, w, b), brute_conv(x, w, b), atol=1e-12)
+
+
+def test_conv3x3_special_cases():
+    g = np.random.default_rng(1)
+    x = g.standard_normal((1, 3, 4, 3))
+    w = np.zeros((3, 3, 3, 3))
+    M = g.standard_normal((3, 3))
+    w[:, 1, 1, :] = M
+    assert np.allclose(run_conv(x, w, np.zeros(3)), x @ M.T)          # centre tap only = 1x1
+    wi = np.zeros((3, 3, 3, 3))
+    wi[:, 1, 1, :] = np.eye(3)
+    assert np.allclose(run_conv(x, wi, np.zeros(3)), x)
+    ws = np.zeros((1, 3, 3, 1))
+    ws[0, 0, 0, 0] = 1.0                                               # picks x[t-1, f-1]
+    y = run_conv(x[..., :1], ws, np.zeros(1))
+    assert np.allclose(y[0, 1:, 1:, 0], x[0, :-1, :-1, 0]) and np.all(y[0, 0, :, 0] == 0)
+
+
+def test_layernorm_moments():
+    g = np.random.default_rng(2)
+    x = g.standard_normal((2, 3, 4, 16)) * 3 + 1
+    tp = onet.Tape()
+    y = tp[onet.layernorm(tp, tp.leaf(x), tp.leaf(np.ones(16)), tp.leaf(np.zeros(16)))]
+    assert np.allclose(y.mean(-1), 0, atol=1e-12)
+    assert np.allclose(y.var(-1), x.var(-1) / (x.var(-1) + onet.LN_EPS), atol=1e-12)
+
+
+def _inputs(cfg, seed, B=2):
+    g = np.random.default_rng(seed)
+    X0 = g.standard_normal((B, cfg.n_sym, cfg.n_sc, cfg.c_in))
+    mask = np.zeros((cfg.n_sym, cfg.n_sc), dtype=np.uint8)
+    mask[list(cfg.pilot_syms), ::2] = 1
+    bits = g.integers(0, 2, (B, cfg.n_sym, cfg.n_sc, cfg.qam_bits)).astype(np.uint8)
+    bits[:, mask.astype(bool)] = 0
+    return X0, bits, mask
+
+
+def _set(cfg, flat, name, value):
+    P = onet.unflatten(cfg, flat)
+    P[name][...] = value
+
+
+def test_support_branches_outputting_one_leave_the_main_net():
+    cfg = tiny_net(n_branches=3, depth=3, width=4)
+    single = replace(cfg, n_branches=1)
+    flat = onet.init_params(cfg, 5)
+    for b in (1, 2):
+        for l in range(cfg.depth):
+            key = "in" if l == 0 else f"l{l}"
+            _set(cfg, flat, f"b{b}.{key}.w", 0.0)
+            _set(cfg, flat, f"b{b}.{key}.b", 1.0)
+    P = onet.unflatten(cfg, flat)
+    flat1 = np.concatenate([P[n].ravel() for n, _ in onet.param_layout(single)])
+    X0, _, _ = _inputs(cfg, 3)
+    assert np.allclose(onet.forward(cfg, flat, X0), onet.forward(single, flat1, X0), atol=1e-12)
+
+
+@pytest.mark.parametrize("residual", [0, 1])
+def test_support_branches_commute(residual):
+    cfg = tiny_net(n_branches=3, depth=2, width=4, residual=residual, norm=residual)
+    flat = onet.init_params(cfg, 8)
+    P = onet.unflatten(cfg, flat)
+    swapped = flat.copy()
+    Q = onet.unflatten(cfg, swapped)
+    for n in P:
+        if n.startswith("b1."):
+            Q[n][...] = P["b2." + n[3:]]
+            Q["b2." + n[3:]][...] = P[n]
+    X0, _, _ = _inputs(cfg, 4)
+    assert np.allclose(onet.forward(cfg, flat, X0), onet.forward(cfg, swapped, X0), atol=1e-12)
+    # swapping main with a support branch changes the result (the main net is special)
+    M = flat.copy()
+    R = onet.unflatten(cfg, M)
+    for n in P:
+        if n.startswith("b1.") and ("b0." + n[3:]) in P:
+            R[n][...] = P["b0." + n[3:]]
+            R["b0." + n[3:]][...] = P[n]
+    assert not np.allclose(onet.forward(cfg, flat, X0), onet.forward(cfg, M, X0))
+
+
+def test_identity_residual_blocks_reduce_to_fused_input_layer():
+    cfg = tiny_net(n_branches=2, depth=2, width=4, residual=1, norm=1)
+    flat = onet.init_params(cfg, 9)
+    P = onet.unflatten(cfg, flat)
+    g = np.random.default_rng(10)
+    for n in P:
+        if ".c2." in n:
+            P[n][...] = 0.0
+        if n.startswith("f") and n.endswith(".b"):
+            P[n][...] = g.standard_normal(P[n].shape)
+    X0, _, _ = _inputs(cfg, 11)
+
+    def ln(v, gam, bet):
+        mu = v.mean(-1, keepdims=True)
+        return (v - mu) / np.sqrt(((v - mu) ** 2).mean(-1, keepdims=True) + 1e-5) * gam + bet
+
+    a = [np.maximum(brute_conv(X0, P[f"b{b}.in.w"], P[f"b{b}.in.b"]), 0) for b in range(2)]
+    x0 = ln(a[0] * a[1], P["f0.g"], P["f0.b"])
+    for i in (1, 2):
+        x0 = ln(x0 * a[1], P[f"f{i}.g"], P[f"f{i}.b"])
+    want = x0 @ P["head.w"].T + P["head.b"]
+    assert np.allclose(onet.forward(cfg, flat, X0), want, atol=1e-10)
+
+
+FD_CASES = [
+    dict(),
+    dict(norm=1),
+    dict(n_branches=3, depth=3),
+    dict(residual=1, norm=1),
+    dict(residual=1, norm=1, n_branches=3, depth=1),
+    dict(n_branches=1, residual=1, norm=1, resnet_baseline=1, width=4),
+    dict(fuse_mask=0b01),
+]
+
+
+@pytest.mark.parametrize("kw", FD_CASES)
+def test_gradient_central_finite_differences(kw):
+    cfg = tiny_net(**kw)
+    flat = onet.init_params(cfg, 12)
+    flat = flat + 0.1 * np.random.default_rng(13).standard_normal(flat.size)
+    X0, bits, mask = _inputs(cfg, 14)
+    loss, g, _ = onet.loss_and_grad(cfg, flat, X0, bits, mask)
+    idx = np.random.default_rng(15).choice(flat.size, size=min(40, flat.size), replace=False)
+    for i in idx:
+        h = 1e-6 * max(1.0, abs(flat[i]))
+        fp, fm = flat.copy(), flat.copy()
+        fp[i] += h
+        fm[i] -= h
+        lp, _ = onet.bce_loss(onet.forward(cfg, fp, X0), bits, mask)
+        lm, _ = onet.bce_loss(onet.forward(cfg, fm, X0), bits, mask)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1e-3) + 1e-9, (i, fd, g[i])
+
+
+def test_bce_closed_forms():
+    mask = np.zeros((1, 2), dtype=np.uint8)
+    llr = np.zeros((1, 1, 2, 3))
+    bits = np.zeros((1, 1, 2, 3), dtype=np.uint8)
+    loss, d = onet.bce_loss(llr, bits, mask)
+    assert np.isclose(loss, np.log(2.0)) and np.allclose(d, 0.5 / 6)
+    llr = np.array([[[[40.0, -40.0]]]])
+    loss, _ = onet.bce_loss(llr, np.array([[[[1, 0]]]], dtype=np.uint8), np.zeros((1, 1), np.uint8))
+    assert loss < 1e-15
+
+
+def test_adam_first_step_closed_form():
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    w = np.ones(4)
+    w1, m, v = onet.adam_step(w, g, np.zeros(4), np.zeros(4), 1, 1e-3)
+    assert np.allclose(w1, w - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_param_counts_of_named_networks():
+    from workloads import WORKLOADS
+    n2 = onet.param_count(WORKLOADS["resid_14x624_b256_fp32"].net)
+    r2 = onet.param_count(WORKLOADS["resnet_14x624_b256_fp32"].net)
+    assert abs(n2 - r2) / r2 < 0.02          # matched model size (Sec. III, last paragraph)
+    assert onet.param_count(WORKLOADS["plain_14x72_b16_fp32"].net) == 2 * (9 * 5 * 32 + 32 + 3 * (9 * 32 * 32 + 32)) + 32 * 4 + 4
