@@ -1,0 +1,258 @@
+/*
+ * conet.h -- C ABI of libconet, a GB300 (sm_103a) implementation of the hot path of
+ * "CoNet-Rx: Collaborative Neural Networks for OFDM Receivers": the collaborative
+ * network receiver's forward pass (received grid -> per-bit LLRs), the backward pass
+ * and optimiser step that train it, the synthetic OFDM link that feeds it, and the
+ * LS-LMMSE receiver it is compared against.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Tensor arguments marked "dev" are device pointers in caller-owned memory on the
+ *    current CUDA device; "host" pointers are ordinary host memory.  The library never
+ *    frees caller memory.  All device tensors are dense, row-major, with the layouts
+ *    given per argument, and 16-byte aligned (as cudaMalloc / torch allocations are).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *    are asynchronous on that stream unless they say they synchronise.
+ *  - Complex values are interleaved (re, im) float32 pairs: a complex [..] tensor is a
+ *    float [.., 2] tensor.
+ *  - Grid axes: B slots, N receive antennas, T OFDM symbols per slot (14), F
+ *    subcarriers, Q bits per QAM symbol.  A resource element (RE) is one (t, f).
+ *  - LLR sign: LLR = log P(b = 1) / P(b = 0); the hard decision is b = [LLR > 0].
+ *  - Every function returns CONET_OK (0) or a negative conet_status.  Argument and
+ *    shape errors are detected on the host before any launch and leave outputs
+ *    untouched; CUDA errors surface as CONET_ERR_CUDA.  conet_last_error() returns a
+ *    thread-local message for the last failure.
+ */
+#ifndef CONET_H
+#define CONET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct conet_s* conet_t;   /* opaque: owns weights, gradients, Adam state, workspace */
+
+typedef enum {
+  CONET_OK = 0,
+  CONET_ERR_ARG = -1,          /* null pointer or invalid value */
+  CONET_ERR_SHAPE = -2,        /* sizes out of range (e.g. B > max_batch) */
+  CONET_ERR_CUDA = -3,         /* a CUDA runtime call or launch failed */
+  CONET_ERR_NOMEM = -4,        /* device allocation failed at create time */
+  CONET_ERR_WEIGHTS = -5,      /* weight vector of the wrong size */
+  CONET_ERR_NONFINITE = -6,    /* NaN / Inf met in a loss */
+  CONET_ERR_TIMEOUT = -7,      /* a bounded device-side wait gave up */
+  CONET_ERR_UNSUPPORTED = -8   /* valid request this build does not implement */
+} conet_status;
+
+typedef enum {
+  CONET_FP32 = 0,              /* FP32 storage, FP32 FFMA convolutions */
+  CONET_BF16 = 1,              /* BF16 activations / weights, FP32 accumulate (tcgen05) */
+  CONET_FP8E4M3 = 2            /* E4M3 weights with per-output-channel scales (tcgen05) */
+} conet_precision;
+
+/*
+ * Network and grid description (Sec. III, Fig. "Example I"; Sec. II for the grid).
+ *   n_rx, n_sym, n_sc, qam_bits : N, T, F, Q.  Input channels C_in = 2 N + 3:
+ *       Re Y_1..N, Im Y_1..N, pilot mask, Re / Im of the antenna-averaged LS estimate.
+ *   n_branches       : 1 main net + (n_branches - 1) support nets (Sec. III, M nets).
+ *   depth            : conv layers per branch (plain) or residual blocks (residual).
+ *   width            : channels per conv layer in every branch.
+ *   residual         : 0 plain conv+ReLU branches; 1 support = RB, main = MRB blocks.
+ *   norm             : 1 = LayerNorm over channels after each Hadamard fusion.
+ *   fuse_mask        : bit i = fuse after layer / block i (bit 0 = input layer);
+ *                      -1 = every layer.
+ *   resnet_baseline  : 1 = single pre-activation ResNet branch without fusion.
+ *   max_batch        : largest B any later call may pass (sizes the workspace).
+ *   train            : 1 = keep every layer's activations so that conet_backward and
+ *                      conet_train_step can run (more workspace); 0 = inference only.
+ *   pilot_syms[0..n_pilot_syms-1], pilot_comb, pilot_seed : the fixed pilot grid
+ *       (Sec. II-A: pilots are fixed) -- QPSK pilots on symbols pilot_syms, every
+ *       pilot_comb-th subcarrier starting at 0, drawn once from pilot_seed.
+ */
+typedef struct {
+  int n_rx, n_sym, n_sc, qam_bits;
+  int n_branches, depth, width;
+  int residual, norm, fuse_mask, resnet_baseline;
+  int max_batch;
+  int train;                   /* 1 = keep every layer's activations for backward */
+  int pilot_syms[4];
+  int n_pilot_syms;
+  int pilot_comb;
+  uint64_t pilot_seed;
+} conet_config;
+
+/*
+ * Synthetic link of Sec. II, Eq. (1): y = h x + g z + n, per receive antenna.
+ *   scs_hz                 subcarrier spacing (OFDM symbol = (1 + 9/128) / scs_hz).
+ *   n_taps, delay_spread_s TDL with exponential power-delay profile e^-l whose rms
+ *                          delay spread equals delay_spread_s.
+ *   fd_lo..fd_hi           max Doppler shift, drawn uniformly per slot (Hz).
+ *   snr_lo..snr_hi         Es/N0 per antenna, drawn uniformly per slot (dB);
+ *                          +inf gives a noiseless grid.
+ *   interferer             1 = add a co-channel QAM interferer (iqam_bits) through an
+ *                          independent TDL channel, SIR drawn in sir_lo..sir_hi dB, with
+ *                          a random time offset inside the cyclic prefix.
+ *   awgn                   1 = replace the fading channel by h = 1.
+ *   n_sinusoids            sum-of-sinusoids terms per tap (16).
+ */
+typedef struct {
+  float scs_hz;
+  int n_taps;
+  float delay_spread_s;
+  float fd_lo, fd_hi;
+  float snr_lo, snr_hi;
+  int interferer;
+  float sir_lo, sir_hi;
+  int iqam_bits;
+  int awgn;
+  int n_sinusoids;
+} conet_sim_params;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Number of float parameters of the network `cfg` describes (flat layout below). */
+int conet_param_count(const conet_config* cfg, size_t* n_out);
+
+/*
+ * Create a receiver.  Allocates all device memory the handle will ever need (weights
+ * in every precision, gradients, Adam moments, activations for max_batch slots) on
+ * the current device; later calls allocate nothing.  precision: conet_precision.
+ * Flat parameter layout (FP32, the order save/load use), per branch b = 0..n_br-1:
+ *   input conv W [C][3][3][C_in], bias [C];
+ *   plain: layers l = 1..depth-1: W [C][3][3][C], bias [C];
+ *   residual: blocks k: (support or resnet only) ln1 gain [C], ln1 shift [C];
+ *             conv1 W, bias; ln2 gain, shift; conv2 W, bias;
+ * then (norm = 1) one LayerNorm gain [C], shift [C] per fusion point in order;
+ * then head W [Q][C], bias [Q].
+ */
+int conet_create(const conet_config* cfg, int precision, conet_t* out);
+void conet_destroy(conet_t h);
+
+/* He-normal weights (std sqrt(2 / fan_in)), zero biases, LayerNorm gain 1 / shift 0,
+ * drawn on the device from Philox4x32-10 with the given seed; zeroes Adam state. */
+int conet_init_he(conet_t h, uint64_t seed, void* stream);
+
+/* Copy n floats (must equal conet_param_count) from / to host memory; synchronises.
+ * A wrong n returns CONET_ERR_WEIGHTS and changes nothing.  Load zeroes Adam state. */
+int conet_load_weights(conet_t h, const float* host_params, size_t n);
+int conet_save_weights(conet_t h, float* host_params, size_t n);
+
+/* Views of the library's FP32 master parameters and their gradients (device, n floats,
+ * flat layout above), valid until conet_destroy. */
+int conet_params_device(conet_t h, float** dev_params, size_t* n);
+int conet_grads_device(conet_t h, float** dev_grads, size_t* n);
+
+/* ---------------------------------------------------------------- forward / backward */
+
+/*
+ * Receive B slots: input assembly (Sec. II-A) -> all CoNet branches with Hadamard
+ * fusion (Sec. III) -> 1x1 head, writing per-RE per-bit LLRs.
+ *   Y          dev float [B][N][T][F][2]   received grid
+ *   pilot_mask dev uint8 [T][F]            1 on pilot REs (must match the config's grid)
+ *   noise_var  dev float [B] or NULL       per-slot noise variance (unused by the
+ *                                          network inputs; accepted for the ABI)
+ *   llr        dev float [B][T][F][Q]      output (pilot REs hold values that
+ *                                          loss and BER ignore)
+ * 0 < B <= max_batch, else CONET_ERR_SHAPE.  Keeps the activations for a following
+ * conet_backward on the same handle.
+ */
+int conet_forward(conet_t h, const float* Y, const uint8_t* pilot_mask, const float* noise_var,
+                  int B, float* llr, void* stream);
+
+/*
+ * Backward of the last conet_forward on this handle for upstream gradient dllr (dev
+ * float [B][T][F][Q], same B).  Writes the parameter gradient (flat layout) into the
+ * buffer conet_grads_device exposes (overwritten, not accumulated).
+ * CONET_ERR_ARG if no forward with this B preceded it or the handle was created with
+ * train = 0.
+ */
+int conet_backward(conet_t h, const float* dllr, int B, void* stream);
+
+/* One bias-corrected Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the master
+ * parameters with the current gradient; `step` counts from 1. */
+int conet_adam_step(conet_t h, float lr, int step, void* stream);
+
+/*
+ * One training step on freshly simulated slots (the paper trains on simulated TDL
+ * slots, Sec. IV): simulate B slots (seed, global slots step*B .. step*B+B-1) ->
+ * forward -> mean BCE-with-logits over data REs -> backward -> Adam (step + 1).
+ * loss_out (host, may be NULL): when non-NULL the call synchronises and returns the
+ * mean loss; CONET_ERR_NONFINITE if it is not finite.
+ */
+int conet_train_step(conet_t h, const conet_sim_params* sim, uint64_t seed, uint64_t step, int B,
+                     float lr, double* loss_out, void* stream);
+
+/* ---------------------------------------------------------------- link and DSP */
+
+/* Fixed pilot grid of `cfg`: mask dev uint8 [T][F], pilot symbols dev float [T][F][2]
+ * (0 on data REs). */
+int conet_pilots(const conet_config* cfg, uint8_t* mask, float* pilot_sym, void* stream);
+
+/*
+ * Simulate B slots of Eq. (1) (global slot ids slot0 .. slot0+B-1) with Philox4x32-10
+ * keyed by `seed`.  fixed_snr_db: NaN = draw per slot from sim->snr_lo..snr_hi.
+ *   Y dev float [B][N][T][F][2]; bits dev uint8 [B][T][F][Q] (0 on pilot REs);
+ *   H dev float [B][N][T][F][2] or NULL; noise_var dev float [B]; interf_var dev
+ *   float [B] or NULL (P_I, 0 without interferer).
+ */
+int conet_sim_generate(const conet_config* cfg, const conet_sim_params* sim, uint64_t seed,
+                       uint64_t slot0, int B, float fixed_snr_db, float* Y, uint8_t* bits,
+                       float* H, float* noise_var, float* interf_var, void* stream);
+
+/*
+ * Network input of Sec. II-A: X0 dev float [B][T][F][C_in] with channels Re Y_n,
+ * Im Y_n (n = 1..N), pilot mask, Re / Im of (1/N) sum_n y_n conj(p) / |p|^2 at pilot
+ * REs (0 elsewhere).  pilot_sym dev float [T][F][2].
+ */
+int conet_assemble_input(const conet_config* cfg, const float* Y, const uint8_t* pilot_mask,
+                         const float* pilot_sym, int B, float* X0, void* stream);
+
+/*
+ * LS-LMMSE receiver (the conventional baseline of Sec. I and Sec. IV): LS at pilots,
+ * linear interpolation across subcarriers then symbols, SIMO LMMSE with
+ * s2 = noise_var (+ interf_var, interference as noise), then exact (demap_exact = 1)
+ * or max-log demapping.  H_perfect (dev [B][N][T][F][2]) replaces the estimate when
+ * non-NULL (perfect CSI).  llr dev float [B][T][F][Q].
+ */
+int conet_ls_lmmse(const conet_config* cfg, const float* Y, const uint8_t* pilot_mask,
+                   const float* pilot_sym, const float* noise_var, const float* interf_var,
+                   const float* H_perfect, int demap_exact, int B, float* llr, void* stream);
+
+/*
+ * Mean-BCE loss and bit-error counters over data REs (hard decision [LLR > 0]).
+ * Accumulates into caller-owned device counters (zero them first):
+ *   loss_sum  dev double[1]  += sum of softplus(L) - b L
+ *   err_bits  dev u64[1]     += hard-decision errors;  n_bits dev u64[1] += bits counted.
+ * dllr (dev float [B][T][F][Q] or NULL) receives (sigmoid(L) - b) * grad_scale on data
+ * REs and 0 on pilots.  Any of loss_sum / err_bits / n_bits may be NULL.
+ */
+int conet_loss_ber(const float* llr, const uint8_t* bits, const uint8_t* pilot_mask, int B, int T,
+                   int F, int Q, float grad_scale, float* dllr, double* loss_sum,
+                   unsigned long long* err_bits, unsigned long long* n_bits, void* stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/*
+ * Per-kernel timing of a handle's launches with CUDA events recorded on the launch
+ * stream (no synchronisation while enabled).  kind: 0 = body 3x3 convolutions
+ * (C -> C), 1 = input convolution, 2 = fusion / LayerNorm / head stage, 3 = input
+ * assembly, 4 = backward kernels, 5 = Adam.  conet_profile_read synchronises the
+ * device, returns the summed milliseconds and the launch count of that kind since the
+ * last enable, and leaves profiling on.  At most 65536 launches are recorded.
+ */
+int conet_profile_enable(conet_t h, int enable);
+int conet_profile_read(conet_t h, int kind, double* total_ms, long long* launches);
+
+/* Kernel launches issued by this library in this process so far (all handles). */
+unsigned long long conet_launch_count(void);
+
+/* Thread-local text of the last error (never NULL). */
+const char* conet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONET_H */

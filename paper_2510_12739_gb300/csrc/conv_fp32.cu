@@ -1,0 +1,236 @@
+// FP32 3x3 'same' convolution of channels-last activations [B][T][F][C] as an implicit
+// GEMM on the FP32 FFMA pipes (the exact-FP32 path).  M = B*T*F resource elements,
+// N = Cout, K = 9*Cin (tap-major, input channel fastest).  One launch covers every
+// branch of a layer (blockIdx.y).  A CTA owns 128 consecutive REs x all Cout channels, so
+// the epilogue can apply bias, residual add, ReLU and a per-RE LayerNorm in place.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace conet {
+
+namespace {
+
+constexpr int TM = 128;   // REs per CTA
+constexpr int RM = 8;     // REs per thread
+
+template <int CIN, int COUT, int KC>
+__global__ void __launch_bounds__(COUT * 4) conv3x3_fp32_kernel(ConvArgs a) {
+  constexpr int NT = COUT * 4;            // (COUT/4) channel groups x 16 RE groups
+  constexpr int CG = COUT / 4;
+  constexpr int NCH = 9 * (CIN / KC);     // K chunks
+  constexpr int A_F4 = TM * KC / 4;
+  constexpr int A_PER_T = (A_F4 + NT - 1) / NT;
+  constexpr int B_F4 = KC * COUT / 4;
+  constexpr int B_PER_T = (B_F4 + NT - 1) / NT;
+  constexpr int CS = COUT + 4;            // padded row of the epilogue tile
+
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  float* As = smem;                       // [2][KC][TM]
+  float* Bs = As + 2 * KC * TM;           // [2][KC][COUT]
+
+  const int br = blockIdx.y;
+  const float* __restrict__ in = a.in[br];
+  const float* __restrict__ w = a.w[br];
+  const int tid = threadIdx.x;
+  const int cg = tid % CG, rg = tid / CG;
+  const long long m0 = (long long)blockIdx.x * TM;
+  const int T = a.T, F = a.F, TF = T * F;
+
+  int a_re[A_PER_T], a_q[A_PER_T], a_t[A_PER_T], a_f[A_PER_T];
+  bool a_ok[A_PER_T], a_st[A_PER_T];
+#pragma unroll
+  for (int j = 0; j < A_PER_T; ++j) {
+    const int idx = tid + j * NT;
+    a_st[j] = idx < A_F4;
+    a_re[j] = idx / (KC / 4);
+    a_q[j] = idx % (KC / 4);
+    const long long m = m0 + a_re[j];
+    a_ok[j] = a_st[j] && m < a.M;
+    const int r = (int)(m % TF);
+    a_t[j] = r / F;
+    a_f[j] = r % F;
+  }
+  float4 ra[A_PER_T], rb[B_PER_T];
+
+  auto load_chunk = [&](int c) {
+    const int tap = c / (CIN / KC), ci0 = (c % (CIN / KC)) * KC;
+    const int dt = tap / 3 - 1, df = tap % 3 - 1;
+#pragma unroll
+    for (int j = 0; j < A_PER_T; ++j) {
+      const int tt = a_t[j] + dt, ff = a_f[j] + df;
+      if (a_ok[j] && tt >= 0 && tt < T && ff >= 0 && ff < F) {
+        const long long m = m0 + a_re[j] + (long long)dt * F + df;
+        ra[j] = __ldg(reinterpret_cast<const float4*>(in + m * CIN + ci0) + a_q[j]);
+      } else {
+        ra[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < B_PER_T; ++j) {
+      const int idx = tid + j * NT;
+      if (idx < B_F4) rb[j] = __ldg(reinterpret_cast<const float4*>(w + (size_t)(tap * CIN + ci0) * COUT) + idx);
+    }
+  };
+  auto store_chunk = [&](int buf) {
+    float* Ab = As + buf * KC * TM;
+#pragma unroll
+    for (int j = 0; j < A_PER_T; ++j) {
+      if (a_st[j]) {
+        Ab[(4 * a_q[j] + 0) * TM + a_re[j]] = ra[j].x;
+        Ab[(4 * a_q[j] + 1) * TM + a_re[j]] = ra[j].y;
+        Ab[(4 * a_q[j] + 2) * TM + a_re[j]] = ra[j].z;
+        Ab[(4 * a_q[j] + 3) * TM + a_re[j]] = ra[j].w;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < B_PER_T; ++j) {
+      const int idx = tid + j * NT;
+      if (idx < B_F4) reinterpret_cast<float4*>(Bs + buf * KC * COUT)[idx] = rb[j];
+    }
+  };
+
+  float acc[RM][4];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+
+  load_chunk(0);
+  store_chunk(0);
+  __syncthreads();
+  for (int c = 0; c < NCH; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < NCH) load_chunk(c + 1);
+    const float* Ab = As + buf * KC * TM;
+    const float* Bb = Bs + buf * KC * COUT;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(Ab + k * TM + rg * RM);
+      const float4 a1 = *reinterpret_cast<const float4*>(Ab + k * TM + rg * RM + 4);
+      const float4 b = *reinterpret_cast<const float4*>(Bb + k * COUT + cg * 4);
+      const float av[RM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+      for (int i = 0; i < RM; ++i) {
+        acc[i][0] = fmaf(av[i], b.x, acc[i][0]);
+        acc[i][1] = fmaf(av[i], b.y, acc[i][1]);
+        acc[i][2] = fmaf(av[i], b.z, acc[i][2]);
+        acc[i][3] = fmaf(av[i], b.w, acc[i][3]);
+      }
+    }
+    if (c + 1 < NCH) store_chunk(buf ^ 1);
+    __syncthreads();
+  }
+
+  // ---------------------------------------------------------------- epilogue
+  const float4 bv = __ldg(reinterpret_cast<const float4*>(a.bias[br]) + cg);
+  const float* __restrict__ resid = a.resid[br];
+  float* __restrict__ out0 = a.out0[br];
+  const bool ln = a.ln_g[br] != nullptr;
+  float* Cs = smem;   // [TM][CS], reuses the mainloop buffers (all reads done)
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int re = rg * RM + i;
+    const long long m = m0 + re;
+    if (m >= a.M) continue;
+    float4 v = make_float4(acc[i][0] + bv.x, acc[i][1] + bv.y, acc[i][2] + bv.z, acc[i][3] + bv.w);
+    if (resid) {
+      const float4 r = __ldg(reinterpret_cast<const float4*>(resid + m * COUT) + cg);
+      v.x += r.x;
+      v.y += r.y;
+      v.z += r.z;
+      v.w += r.w;
+    }
+    if (out0) {
+      float4 o = v;
+      if (a.relu0) o = make_float4(fmaxf(o.x, 0.f), fmaxf(o.y, 0.f), fmaxf(o.z, 0.f), fmaxf(o.w, 0.f));
+      reinterpret_cast<float4*>(out0 + m * COUT)[cg] = o;
+    }
+    if (ln) *reinterpret_cast<float4*>(Cs + re * CS + cg * 4) = v;
+  }
+  if (!ln) return;
+  __syncthreads();
+  const float* __restrict__ g = a.ln_g[br];
+  const float* __restrict__ be = a.ln_b[br];
+  float* __restrict__ out1 = a.out1[br];
+  constexpr int NW = NT / 32;
+  constexpr int CPL = (COUT + 31) / 32;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int re = warp; re < TM; re += NW) {
+    const long long m = m0 + re;
+    if (m >= a.M) break;
+    float x[CPL];
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j;
+      x[j] = c < COUT ? Cs[re * CS + c] : 0.f;
+      s += x[j];
+    }
+    const float mean = warp_sum(s) * (1.0f / COUT);
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j;
+      const float d = c < COUT ? x[j] - mean : 0.f;
+      q += d * d;
+    }
+    const float rstd = rsqrtf(warp_sum(q) * (1.0f / COUT) + 1e-5f);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j;
+      if (c < COUT) out1[m * COUT + c] = fmaxf((x[j] - mean) * rstd * __ldg(g + c) + __ldg(be + c), 0.f);
+    }
+  }
+}
+
+template <int CIN, int COUT, int KC>
+int launch_t(const ConvArgs& a, int n_br, cudaStream_t s) {
+  constexpr size_t main_smem = (size_t)(2 * KC * TM + 2 * KC * COUT) * sizeof(float);
+  constexpr size_t epi_smem = (size_t)TM * (COUT + 4) * sizeof(float);
+  constexpr size_t smem = main_smem > epi_smem ? main_smem : epi_smem;
+  static bool attr = false;
+  if (!attr) {
+    CONET_CUDA(cudaFuncSetAttribute(conv3x3_fp32_kernel<CIN, COUT, KC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid((unsigned)((a.M + TM - 1) / TM), n_br);
+  conv3x3_fp32_kernel<CIN, COUT, KC><<<grid, COUT * 4, smem, s>>>(a);
+  return check_launch("conv3x3_fp32_kernel");
+}
+
+}  // namespace
+
+int launch_conv3x3_fp32(const ConvArgs& a, int n_br, int cin, int cout, cudaStream_t s) {
+#define CONV_CASE(CI, CO, KC) \
+  if (cin == CI && cout == CO) return launch_t<CI, CO, KC>(a, n_br, s);
+  CONV_CASE(8, 32, 8)
+  CONV_CASE(32, 32, 8)
+  CONV_CASE(8, 64, 8)
+  CONV_CASE(64, 64, 8)
+  CONV_CASE(8, 112, 8)
+  CONV_CASE(112, 112, 8)
+  CONV_CASE(12, 96, 4)
+  CONV_CASE(96, 96, 8)
+  CONV_CASE(8, 16, 8)
+  CONV_CASE(16, 16, 8)
+#undef CONV_CASE
+  return fail(CONET_ERR_UNSUPPORTED, "FP32 conv3x3 with Cin=%d Cout=%d is not instantiated", cin, cout);
+}
+
+// [Cout][3][3][cin_src] -> [9][cin_dst][Cout], zero rows for cin_src <= ci < cin_dst
+__global__ void weights_tap_major_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+                                         float* __restrict__ out) {
+  const int n = 9 * cin_dst * cout;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int co = i % cout, rem = i / cout, ci = rem % cin_dst, tap = rem / cin_dst;
+    out[i] = ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f;
+  }
+}
+
+int launch_weights_to_tap_major(const float* w, int cout, int cin_src, int cin_dst, float* out, cudaStream_t s) {
+  weights_tap_major_kernel<<<grid_for((long long)cout * 9 * cin_dst, 256, 512), 256, 0, s>>>(w, cout, cin_src,
+                                                                                             cin_dst, out);
+  return check_launch("weights_tap_major_kernel");
+}
+
+}  // namespace conet

@@ -1,0 +1,97 @@
+// Handle state and network orchestration of libconet (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <vector>
+
+#include "../../include/conet.h"
+#include "kernels.cuh"
+
+namespace conet {
+
+struct BlockOff {
+  long ln1g = -1, ln1b = -1, c1w = -1, c1b = -1, ln2g = -1, ln2b = -1, c2w = -1, c2b = -1;
+};
+
+struct Seg {
+  size_t off, n;
+  int kind;      // 0 He-normal, 1 ones, 2 zeros
+  float stdv;
+};
+
+struct ConvT {
+  size_t off;
+  int cout, cin;
+};
+
+// Offsets (in floats) of every tensor in the flat parameter vector; -1 = absent.
+struct Layout {
+  long in_w[MAX_BR] = {}, in_b[MAX_BR] = {};
+  std::vector<long> lw[MAX_BR], lb[MAX_BR];   // plain layers 1..depth-1
+  std::vector<BlockOff> blk[MAX_BR];          // residual blocks
+  std::vector<long> fg, fb;                   // fusion LayerNorm per fusion point
+  long hw = 0, hb = 0;
+  size_t total = 0;
+  std::vector<Seg> segs;
+  std::vector<ConvT> convs;
+};
+
+bool fused_at(const conet_config& c, int i);
+Layout build_layout(const conet_config& c);
+
+}  // namespace conet
+
+struct conet_s {
+  conet_config cfg;
+  int prec = 0;
+  conet::Layout L;
+  int T = 0, F = 0, N = 0, Q = 0, C = 0, nb = 0, cin = 0, c_pad = 0;
+  float* params = nullptr;
+  float* grads = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* wt = nullptr;                       // conv weights in [9][Cin_pad][Cout] order
+  std::map<size_t, size_t> wt_off;           // master offset -> wt offset
+  size_t wt_total = 0;
+  uint8_t* mask = nullptr;                   // fixed pilot grid [T][F]
+  float* psym = nullptr;                     // pilot symbols [T][F][2]
+  float* X0 = nullptr;                       // assembled input [B][T][F][c_pad]
+  std::vector<float*> act;                   // activation buffers, max_batch*T*F*C floats each
+  float* sim_Y = nullptr;                    // training-step slots
+  uint8_t* sim_bits = nullptr;
+  float* sim_nv = nullptr;
+  float* llr = nullptr;
+  float* dllr = nullptr;
+  double* d_loss = nullptr;
+  unsigned long long* d_cnt = nullptr;
+  int fwd_B = 0;
+  std::vector<void*> allocs;
+  bool prof_on = false;                      // CUDA-event timing of launches by kind
+  std::vector<cudaEvent_t> prof_ev;          // 2 events per recorded launch
+  std::vector<int> prof_kind;
+  int prof_open = -1;
+};
+
+namespace conet {
+
+int dev_alloc(conet_s* h, void** p, size_t bytes);
+
+enum ProfKind { PK_CONV = 0, PK_CONV_IN = 1, PK_FUSE = 2, PK_ASSEMBLE = 3, PK_BACKWARD = 4, PK_ADAM = 5, PK_N = 6 };
+constexpr size_t PROF_CAP = 65536;
+void prof_begin(conet_s* h, int kind, cudaStream_t s);
+void prof_end(conet_s* h, cudaStream_t s);
+template <typename Tp>
+inline int dev_alloc_t(conet_s* h, Tp** p, size_t count) {
+  return dev_alloc(h, reinterpret_cast<void**>(p), count * sizeof(Tp));
+}
+
+int net_setup(conet_s* h);
+int net_weights_changed(conet_s* h, cudaStream_t s);
+int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
+int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s);
+int net_adam(conet_s* h, float lr, int step, cudaStream_t s);
+int net_train_step(conet_s* h, const SimArgs& a, uint64_t step, int B, float lr, double* loss_out, cudaStream_t s);
+
+}  // namespace conet
