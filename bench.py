@@ -43,6 +43,10 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="resid_14x624_b256_fp32")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    p.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling runs)")
+    p.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default=None,
+                   help="override the workload's conv precision")
     return p.parse_args()
 
 
@@ -50,6 +54,22 @@ def conv_flops(net, B):
     """Algorithmic FLOPs (2 x MACs) of one body 3x3 conv launch (all branches)."""
     M = B * net.n_sym * net.n_sc
     return 2.0 * M * 9 * net.width * net.width * net.n_branches
+
+
+def n_body_convs(net):
+    """Body (C -> C) 3x3 conv layers per branch."""
+    return 2 * net.depth if net.residual else net.depth - 1
+
+
+def tensor_peak():
+    """Dense BF16/FP16 tensor peak in TFLOP/s: the measured sustained cuBLAS figure
+    (the conv is timed inside a long step), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, "fallback sustained BF16 1.7 PFLOP/s (of fallback)"
 
 
 def net_flops_per_re(net):
@@ -176,7 +196,10 @@ def main():
     from paper_2510_12739_gb300 import api
 
     w = WORKLOADS[args.workload]
-    net, B = w.net, w.batch
+    if args.precision:
+        import dataclasses
+        w = dataclasses.replace(w, precision=args.precision)
+    net, B = w.net, (args.batch or w.batch)
     T, F, Q = net.n_sym, net.n_sc, net.qam_bits
     rx = api.Receiver(net, precision=w.precision, max_batch=B)
     rx.init_he(0)
@@ -235,9 +258,16 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = B * world / (ms / 1e3)
 
     # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(args, rx, count, Y, nv, mask, llr, cnt, flush, stream, B, world, dist, barrier)
+    return finish(args, rank, world, local, w, net, B, T, F, Q, ms, times, conv_ms, conv_n, clk, n_launch, e2e, dist)
+
+
+def end_to_end(args, rx, count, Y, nv, mask, llr, cnt, flush, stream, B, world, dist, barrier):
+    import torch
     Y_h = Y.cpu().pin_memory()
     nv_h = nv.cpu().pin_memory()
     llr_h = torch.empty(llr.shape, dtype=llr.dtype, pin_memory=True)
@@ -268,21 +298,34 @@ def main():
         t = torch.tensor([ms_e2e], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e2e = float(t.item())
-    e2e = {"value": B * world / (ms_e2e / 1e3), "unit": "slots/s",
-           "h2d_bytes_per_step": int(Y.nbytes + nv.nbytes),
-           "d2h_bytes_per_step": int(llr.nbytes + cnt.nbytes)}
+    return {"value": B * world / (ms_e2e / 1e3), "unit": "slots/s",
+            "h2d_bytes_per_step": int(Y.nbytes + nv.nbytes),
+            "d2h_bytes_per_step": int(llr.nbytes + cnt.nbytes)}
 
+
+def finish(args, rank, world, local, w, net, B, T, F, Q, ms, times, conv_ms, conv_n, clk, n_launch, e2e, dist):
+    import torch
+    value = B * world / (ms / 1e3)
     # ---------------------------------------------------------------- roofline of the body conv
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     avg_conv_s = (conv_ms / max(conv_n, 1)) / 1e3
-    achieved = conv_flops(net, B) / avg_conv_s / 1e12 if conv_n else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    # one launch per body layer and batch chunk: spread the step's body-conv FLOPs over them
+    launches_per_step = conv_n / max(1, args.steps)
+    flops_per_launch = conv_flops(net, B) * n_body_convs(net) / max(1e-9, launches_per_step)
+    achieved = flops_per_launch / avg_conv_s / 1e12 if conv_n else None
+    if w.precision == "fp32":
+        peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        bound, src = "alu", f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {SM_MAX_MHZ:.0f} MHz"
+        kname = f"conv3x3_fp32_kernel<{net.width},{net.width},8> (body 3x3 conv, {net.n_branches} branches per launch)"
+    else:
+        peak, src = tensor_peak()
+        bound = "tensor"
+        kname = (f"conv_tc_kernel<{w.precision},{net.n_branches},{net.width},{net.width}> "
+                 f"(tcgen05 body 3x3 conv, {net.n_branches} branches per launch)")
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic_per_launch(net, B),
-                "kernel": "conv3x3_fp32_kernel<64,64,8> (body 3x3 conv, 3 branches per launch)",
-                "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {SM_MAX_MHZ:.0f} MHz",
-                "launches": conv_n, "avg_launch_ms": avg_conv_s * 1e3}
+                "kernel": kname, "peak_source": src, "launches": conv_n, "avg_launch_ms": avg_conv_s * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -293,7 +336,9 @@ def main():
     if rank == 0:
         line = {"metric": "conet_infer_slots_per_s", "value": value, "unit": "slots/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[w.precision],
+                "data": "synthetic",
                 "config": {"workload": w.name, "global_batch": B * world, "batch_per_gpu": B, "n_rx": net.n_rx,
                            "grid": f"{T}x{F}", "qam_bits": Q, "branches": net.n_branches, "blocks": net.depth,
                            "width": net.width, "flop_per_slot": net_flops_per_re(net) * T * F,

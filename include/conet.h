@@ -50,7 +50,8 @@ typedef enum {
 typedef enum {
   CONET_FP32 = 0,              /* FP32 storage, FP32 FFMA convolutions */
   CONET_BF16 = 1,              /* BF16 activations / weights, FP32 accumulate (tcgen05) */
-  CONET_FP8E4M3 = 2            /* E4M3 weights with per-output-channel scales (tcgen05) */
+  CONET_FP8E4M3 = 2,           /* E4M3 weights with per-output-channel scales (tcgen05) */
+  CONET_FP16 = 3               /* FP16 activations / weights, FP32 accumulate (tcgen05) */
 } conet_precision;
 
 /*
@@ -245,6 +246,13 @@ int conet_loss_ber(const float* llr, const uint8_t* bits, const uint8_t* pilot_m
  */
 int conet_profile_enable(conet_t h, int enable);
 int conet_profile_read(conet_t h, int kind, double* total_ms, long long* launches);
+
+/*
+ * Wait for `stream` and report device-side failures of this handle's kernels since the
+ * last call: CONET_ERR_TIMEOUT when a bounded pipeline wait gave up (the word is then
+ * cleared), CONET_ERR_CUDA for an asynchronous CUDA error.
+ */
+int conet_sync(conet_t h, void* stream);
 
 /* Kernel launches issued by this library in this process so far (all handles). */
 unsigned long long conet_launch_count(void);

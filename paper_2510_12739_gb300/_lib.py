@@ -59,6 +59,7 @@ SIGNATURES = {
     "conet_profile_enable": (I, [P, I]),
     "conet_profile_read": (I, [P, I, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "conet_launch_count": (C.c_ulonglong, []),
+    "conet_sync": (I, [P, P]),
     "conet_last_error": (C.c_char_p, []),
 }
 

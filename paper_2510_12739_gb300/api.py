@@ -14,7 +14,7 @@ import torch
 
 from ._lib import check, conet_config, conet_sim_params, lib
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
 
 
 def make_config(net, max_batch: int = 1, train: bool = False) -> conet_config:
@@ -126,6 +126,10 @@ class Receiver:
 
     def adam_step(self, lr: float, step: int, stream=None):
         check(lib().conet_adam_step(self.h, lr, step, _stream(stream)))
+
+    def sync(self, stream=None):
+        """Wait for the stream; raise on a device-side timeout or CUDA error."""
+        check(lib().conet_sync(self.h, _stream(stream)))
 
     def profile_enable(self, enable: bool = True):
         check(lib().conet_profile_enable(self.h, int(bool(enable))))

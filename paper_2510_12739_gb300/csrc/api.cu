@@ -146,6 +146,20 @@ const char* conet_last_error(void) { return g_err.c_str(); }
 
 unsigned long long conet_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+int conet_sync(conet_t h, void* stream) {
+  if (!h) return fail(CONET_ERR_ARG, "handle is NULL");
+  CONET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (h->d_err) {
+    int e = 0;
+    CONET_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      CONET_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+      return fail(CONET_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (site %d)", e);
+    }
+  }
+  return CONET_OK;
+}
+
 int conet_profile_enable(conet_t h, int enable) {
   if (!h) return fail(CONET_ERR_ARG, "handle is NULL");
   CONET_CUDA(cudaDeviceSynchronize());
@@ -191,7 +205,7 @@ int conet_create(const conet_config* cfg, int precision, conet_t* out) {
   CONET_TRY(validate_config(cfg));
   if (!out) return fail(CONET_ERR_ARG, "out is NULL");
   if (cfg->max_batch < 1) return fail(CONET_ERR_SHAPE, "max_batch %d < 1", cfg->max_batch);
-  if (precision != CONET_FP32 && precision != CONET_BF16 && precision != CONET_FP8E4M3)
+  if (precision != CONET_FP32 && precision != CONET_BF16 && precision != CONET_FP8E4M3 && precision != CONET_FP16)
     return fail(CONET_ERR_ARG, "unknown precision %d", precision);
   conet_s* h = new conet_s();
   h->cfg = *cfg;

@@ -1,0 +1,481 @@
+// Backward pass of the CoNet receiver (the training of Sec. IV) and the Adam update:
+//  - head backward (1x1 conv): dX0 = dLLR W_h, partial dW_h / db_h per CTA;
+//  - Hadamard-fusion backward with the post-fusion LayerNorm and the ReLU mask of the
+//    fused activations: d a_j = d p * prod_{i != j} a_i (+ the branch's own gradient);
+//  - LayerNorm(+ReLU) backward of the pre-activations inside RB / MRB blocks;
+//  - 3x3 weight gradient dW[co][tap][ci] = sum_RE dz[RE][co] x[RE + shift(tap)][ci],
+//    split over RE ranges into per-split partials that a second kernel sums in a fixed
+//    order (deterministic);
+//  - per-channel sums (bias gradients) and the partial-sum reduction;
+//  - bias-corrected Adam.
+// The data gradient of a 3x3 conv reuses the forward conv kernel with the weights
+// rotated by 180 degrees and transposed (see launch_weights_dgrad_layout).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace conet {
+
+namespace {
+
+constexpr int CPL = 4;          // channels per lane (C <= 128)
+constexpr int EW_THREADS = 256;
+constexpr int EW_WARPS = EW_THREADS / 32;
+
+__device__ __forceinline__ void load_row(const float* __restrict__ p, long long m, int C, int lane, float (&x)[CPL]) {
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int c = lane + 32 * j;
+    x[j] = c < C ? p[m * C + c] : 0.f;
+  }
+}
+
+__device__ __forceinline__ void store_row(float* __restrict__ p, long long m, int C, int lane, const float (&x)[CPL]) {
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int c = lane + 32 * j;
+    if (c < C) p[m * C + c] = x[j];
+  }
+}
+
+// LayerNorm backward for one RE held by a warp.  x: LN input, gy: grad wrt the LN output
+// (before the affine gain is applied, gy is the grad of y = g*xhat + b).
+// Returns dx; accumulates dgamma (gy*xhat) and dbeta (gy) in the lane's registers.
+__device__ __forceinline__ void ln_backward(const float (&x)[CPL], const float (&gy)[CPL], const float* __restrict__ g,
+                                            int C, int lane, float (&dx)[CPL], float (&dg)[CPL], float (&db)[CPL]) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) s += (lane + 32 * j < C) ? x[j] : 0.f;
+  const float mean = warp_sum(s) / (float)C;
+  float q = 0.f;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const float d = (lane + 32 * j < C) ? x[j] - mean : 0.f;
+    q += d * d;
+  }
+  const float rstd = rsqrtf(warp_sum(q) / (float)C + 1e-5f);
+  float xh[CPL], gxh[CPL];
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const int c = lane + 32 * j;
+    xh[j] = c < C ? (x[j] - mean) * rstd : 0.f;
+    gxh[j] = c < C ? gy[j] * __ldg(g + c) : 0.f;
+    dg[j] += gy[j] * xh[j];
+    db[j] += gy[j];
+    s1 += gxh[j];
+    s2 += gxh[j] * xh[j];
+  }
+  const float m1 = warp_sum(s1) / (float)C, m2 = warp_sum(s2) / (float)C;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) dx[j] = rstd * (gxh[j] - m1 - xh[j] * m2);
+}
+
+// Block reduction of per-lane channel partials [n_vec][CPL] into part[blockIdx][n_vec * C].
+template <int NV>
+__device__ void block_store_partials(float (&v)[NV][CPL], int C, float* __restrict__ part) {
+  __shared__ float red[EW_WARPS][NV][128];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j;
+      if (c < C) red[w][k][c] = v[k][j];
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NV * C; i += blockDim.x) {
+    const int k = i / C, c = i % C;
+    float s = 0.f;
+    for (int ww = 0; ww < EW_WARPS; ++ww) s += red[ww][k][c];
+    part[(size_t)blockIdx.x * NV * C + i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(EW_THREADS) fuse_bwd_kernel(FuseBwdArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int C = a.C;
+  float pv[2][CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) pv[0][j] = pv[1][j] = 0.f;
+  for (long long m = warp0; m < a.M; m += nwarps) {
+    float u[MAX_BR][CPL], gx0[CPL];
+#pragma unroll
+    for (int b = 0; b < MAX_BR; ++b) {
+      if (b < a.n_br) load_row(a.u[b], m, C, lane, u[b]);
+      else
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) u[b][j] = 1.f;
+    }
+    load_row(a.gx0, m, C, lane, gx0);
+    float gu[MAX_BR][CPL];
+#pragma unroll
+    for (int b = 1; b < MAX_BR; ++b) {
+      if (b < a.n_br && a.gxs[b]) load_row(a.gxs[b], m, C, lane, gu[b]);
+      else
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) gu[b][j] = 0.f;
+    }
+    if (a.fuse) {
+      float gp[CPL];
+      if (a.ln_g) {
+        float p[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) p[j] = u[0][j] * u[1][j] * u[2][j] * u[3][j];
+        ln_backward(p, gx0, a.ln_g, C, lane, gp, pv[0], pv[1]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) gp[j] = gx0[j];
+      }
+#pragma unroll
+      for (int b = 0; b < MAX_BR; ++b) {
+        if (b >= a.n_br) continue;
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+          float o = gp[j];
+#pragma unroll
+          for (int i = 0; i < MAX_BR; ++i)
+            if (i != b) o *= u[i][j];
+          gu[b][j] = (b == 0 ? 0.f : gu[b][j]) + o;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) gu[0][j] = gx0[j];
+    }
+#pragma unroll
+    for (int b = 0; b < MAX_BR; ++b) {
+      if (b >= a.n_br) continue;
+      if (a.relu_mask)
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) gu[b][j] = u[b][j] > 0.f ? gu[b][j] : 0.f;
+      store_row(a.gu[b], m, C, lane, gu[b]);
+    }
+  }
+  if (a.part) block_store_partials<2>(pv, C, a.part);
+}
+
+__global__ void __launch_bounds__(EW_THREADS) ln_relu_bwd_kernel(LnReluBwdArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int C = a.C;
+  float pv[2][CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) pv[0][j] = pv[1][j] = 0.f;
+  for (long long m = warp0; m < a.M; m += nwarps) {
+    float x[CPL], g[CPL], out[CPL];
+    load_row(a.x, m, C, lane, x);
+    load_row(a.g, m, C, lane, g);
+    if (a.ln_g) {
+      // recompute y = LN(x) * gamma + beta to get the ReLU mask, then LN backward
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) s += (lane + 32 * j < C) ? x[j] : 0.f;
+      const float mean = warp_sum(s) / (float)C;
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const float d = (lane + 32 * j < C) ? x[j] - mean : 0.f;
+        q += d * d;
+      }
+      const float rstd = rsqrtf(warp_sum(q) / (float)C + 1e-5f);
+      float gy[CPL];
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int c = lane + 32 * j;
+        const float y = c < C ? (x[j] - mean) * rstd * __ldg(a.ln_g + c) + __ldg(a.ln_b + c) : 0.f;
+        gy[j] = y > 0.f ? g[j] : 0.f;
+      }
+      ln_backward(x, gy, a.ln_g, C, lane, out, pv[0], pv[1]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) out[j] = x[j] > 0.f ? g[j] : 0.f;
+    }
+    if (a.add) {
+      float ad[CPL];
+      load_row(a.add, m, C, lane, ad);
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) out[j] += ad[j];
+    }
+    store_row(a.out, m, C, lane, out);
+  }
+  if (a.part) block_store_partials<2>(pv, C, a.part);
+}
+
+__global__ void __launch_bounds__(EW_THREADS) head_bwd_kernel(HeadBwdArgs a) {
+  constexpr int QMAX = 8;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int C = a.C, Q = a.Q;
+  float pw[QMAX][CPL], pb[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+    pb[q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) pw[q][j] = 0.f;
+  }
+  for (long long m = warp0; m < a.M; m += nwarps) {
+    float x[CPL], g[CPL];
+    load_row(a.x0, m, C, lane, x);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) g[j] = 0.f;
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      if (q >= Q) continue;
+      const float d = __ldg(a.dllr + m * Q + q);
+      pb[q] += d;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int c = lane + 32 * j;
+        if (c < C) {
+          g[j] += d * __ldg(a.w + q * C + c);
+          pw[q][j] += d * x[j];
+        }
+      }
+    }
+    store_row(a.gx0, m, C, lane, g);
+  }
+  __shared__ float red[EW_WARPS][QMAX * 128 + QMAX];
+  const int w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j;
+      if (q < Q && c < C) red[w][q * C + c] = pw[q][j];
+    }
+    if (lane == 0 && q < Q) red[w][QMAX * 128 + q] = pb[q];
+  }
+  __syncthreads();
+  const int n = Q * C + Q;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int src = i < Q * C ? i : QMAX * 128 + (i - Q * C);
+    float s = 0.f;
+    for (int ww = 0; ww < EW_WARPS; ++ww) s += red[ww][src];
+    a.part[(size_t)blockIdx.x * n + i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(EW_THREADS) channel_sums_kernel(const float* __restrict__ g, long long M, int C,
+                                                                  float* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  float pv[1][CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) pv[0][j] = 0.f;
+  for (long long m = warp0; m < M; m += nwarps) {
+    float x[CPL];
+    load_row(g, m, C, lane, x);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) pv[0][j] += x[j];
+  }
+  block_store_partials<1>(pv, C, part);
+}
+
+// out[j] (+)= sum_i part[i * n + j]
+__global__ void reduce_partials_kernel(const float* __restrict__ part, int n_part, int n, float* __restrict__ out,
+                                       int accumulate) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int i = 0; i < n_part; ++i) s += part[(size_t)i * n + j];
+    out[j] = accumulate ? out[j] + s : s;
+  }
+}
+
+// Weight gradient of a 3x3 conv for one tap per blockIdx.y, one branch per blockIdx.z and
+// one RE range per blockIdx.x.  256 threads = 64 (4 ci x 4 co) output blocks x 4 RE lanes;
+// blocks beyond the (CIN/4)(COUT/4) grid are handled by further CTAs (blk chunk in y).
+constexpr int WG_CHUNK = 32;
+__global__ void __launch_bounds__(256) wgrad_kernel(WgradArgs a) {
+  extern __shared__ float4 wg_smem4[];
+  float* xs = reinterpret_cast<float*>(wg_smem4);          // [WG_CHUNK][CIN]
+  const int CIN = a.cin, COUT = a.cout;
+  float* gs = xs + WG_CHUNK * CIN;                          // [WG_CHUNK][COUT]
+  const int br = blockIdx.z;
+  const int tap = blockIdx.y % 9, chunk = blockIdx.y / 9;
+  const int dt = tap / 3 - 1, df = tap % 3 - 1;
+  const int slot = threadIdx.x & 63, lane_r = threadIdx.x >> 6;
+  const int nblk_co = COUT / 4;
+  const int blk = chunk * 64 + slot;
+  const bool active = blk < (CIN / 4) * nblk_co;
+  const int ci0 = active ? (blk / nblk_co) * 4 : 0, co0 = active ? (blk % nblk_co) * 4 : 0;
+  const long long per = (a.M + gridDim.x - 1) / gridDim.x;
+  const long long r0 = blockIdx.x * per, r1 = min(a.M, r0 + per);
+  const float* __restrict__ x = a.x[br];
+  const float* __restrict__ g = a.g[br];
+  const int TF = a.T * a.F;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (long long rc = r0; rc < r1; rc += WG_CHUNK) {
+    const int n = (int)min((long long)WG_CHUNK, r1 - rc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < WG_CHUNK * CIN / 4; i += blockDim.x) {
+      const int r = i / (CIN / 4), q = i % (CIN / 4);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < n) {
+        const long long m = rc + r;
+        const int rr = (int)(m % TF), t = rr / a.F + dt, f = rr % a.F + df;
+        if (t >= 0 && t < a.T && f >= 0 && f < a.F)
+          v = __ldg(reinterpret_cast<const float4*>(x + (m + (long long)dt * a.F + df) * CIN) + q);
+      }
+      reinterpret_cast<float4*>(xs)[i] = v;
+    }
+    for (int i = threadIdx.x; i < WG_CHUNK * COUT / 4; i += blockDim.x) {
+      const int r = i / (COUT / 4), q = i % (COUT / 4);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < n) v = __ldg(reinterpret_cast<const float4*>(g + (rc + r) * COUT) + q);
+      reinterpret_cast<float4*>(gs)[i] = v;
+    }
+    __syncthreads();
+    if (active) {
+      for (int r = lane_r; r < n; r += 4) {
+        const float4 xv = *reinterpret_cast<const float4*>(xs + r * CIN + ci0);
+        const float4 gv = *reinterpret_cast<const float4*>(gs + r * COUT + co0);
+        const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+        const float ga[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], ga[j], acc[i][j]);
+      }
+    }
+  }
+  // reduce the 4 RE lanes through shared memory, then write this split's partial
+  __syncthreads();
+  float* red = xs;   // [4][64][16]
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[(lane_r * 64 + slot) * 16 + i * 4 + j] = acc[i][j];
+  __syncthreads();
+  if (lane_r == 0 && active) {
+    float* out = a.part + ((((size_t)blockIdx.x * a.n_br + br) * 9 + tap) * CIN) * COUT;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float s = 0.f;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) s += red[(l * 64 + slot) * 16 + i * 4 + j];
+        out[(size_t)(ci0 + i) * COUT + co0 + j] = s;
+      }
+  }
+}
+
+// Sum the per-split partials [S][n_br][9][CIN][COUT] of branch `br` into the master
+// gradient layout [COUT][3][3][cin_src] (padded input channels dropped).
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int S, int n_br, int br, int cin, int cout,
+                                    int cin_src, float* __restrict__ dW) {
+  const int n = cout * 9 * cin_src;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int co = i / (9 * cin_src), rem = i % (9 * cin_src), tap = rem / cin_src, ci = rem % cin_src;
+    float s = 0.f;
+    for (int k = 0; k < S; ++k) s += part[((((size_t)k * n_br + br) * 9 + tap) * cin + ci) * cout + co];
+    dW[i] = s;
+  }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+// dgrad weights: Wd[tap'][co][ci] = W[co][8 - tap'][ci]  (conv of dz with the kernel
+// rotated by 180 degrees, input and output channels exchanged)
+__global__ void weights_dgrad_kernel(const float* __restrict__ w, int C, float* __restrict__ out) {
+  const int n = 9 * C * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int ci = i % C, rem = i / C, co = rem % C, tp = rem / C;
+    out[i] = w[((size_t)co * 9 + (8 - tp)) * C + ci];
+  }
+}
+
+}  // namespace
+
+int ew_grid(long long M) { return grid_for(M * 32, EW_THREADS, EW_PART_CTAS); }
+
+int launch_fuse_bwd(const FuseBwdArgs& a, cudaStream_t s) {
+  fuse_bwd_kernel<<<ew_grid(a.M), EW_THREADS, 0, s>>>(a);
+  return check_launch("fuse_bwd_kernel");
+}
+
+int launch_ln_relu_bwd(const LnReluBwdArgs& a, cudaStream_t s) {
+  ln_relu_bwd_kernel<<<ew_grid(a.M), EW_THREADS, 0, s>>>(a);
+  return check_launch("ln_relu_bwd_kernel");
+}
+
+int launch_head_bwd(const HeadBwdArgs& a, cudaStream_t s) {
+  if (a.Q > 8) return fail(CONET_ERR_UNSUPPORTED, "Q > 8");
+  head_bwd_kernel<<<ew_grid(a.M), EW_THREADS, 0, s>>>(a);
+  return check_launch("head_bwd_kernel");
+}
+
+int launch_channel_sums(const float* g, long long M, int C, float* part, cudaStream_t s) {
+  channel_sums_kernel<<<ew_grid(M), EW_THREADS, 0, s>>>(g, M, C, part);
+  return check_launch("channel_sums_kernel");
+}
+
+int launch_reduce_partials(const float* part, int n_part, int n, float* out, int accumulate, cudaStream_t s) {
+  reduce_partials_kernel<<<grid_for(n, 256, 256), 256, 0, s>>>(part, n_part, n, out, accumulate);
+  return check_launch("reduce_partials_kernel");
+}
+
+int wgrad_splits(long long M, int cin, int cout, int n_br) {
+  const int chunks = ((cin / 4) * (cout / 4) + 63) / 64;
+  long long s = (152LL * 4) / (9LL * chunks * n_br);
+  if (s < 1) s = 1;
+  if (s > WG_MAX_SPLITS) s = WG_MAX_SPLITS;
+  const long long by_size = (M + 4 * WG_CHUNK - 1) / (4 * WG_CHUNK);   // >= 128 REs per split
+  if (s > by_size) s = by_size < 1 ? 1 : by_size;
+  return (int)s;
+}
+
+size_t wgrad_partial_floats(long long M, int cin, int cout, int n_br) {
+  return (size_t)wgrad_splits(M, cin, cout, n_br) * n_br * 9 * cin * cout;
+}
+
+int launch_wgrad(const WgradArgs& a, cudaStream_t s) {
+  if (a.cin % 4 || a.cout % 4 || a.cin > 128 || a.cout > 128) return fail(CONET_ERR_UNSUPPORTED, "wgrad channels");
+  const int S = wgrad_splits(a.M, a.cin, a.cout, a.n_br);
+  const int chunks = ((a.cin / 4) * (a.cout / 4) + 63) / 64;
+  const size_t smem = (size_t)WG_CHUNK * (a.cin + a.cout) * sizeof(float);
+  const size_t red = 4 * 64 * 16 * sizeof(float);
+  const size_t sm = smem > red ? smem : red;
+  dim3 grid(S, 9 * chunks, a.n_br);
+  wgrad_kernel<<<grid, 256, sm, s>>>(a);
+  CONET_LAUNCHED("wgrad_kernel");
+  for (int b = 0; b < a.n_br; ++b) {
+    wgrad_reduce_kernel<<<grid_for((long long)a.cout * 9 * a.cin_src[b], 256, 512), 256, 0, s>>>(
+        a.part, S, a.n_br, b, a.cin, a.cout, a.cin_src[b], a.dW[b]);
+    CONET_LAUNCHED("wgrad_reduce_kernel");
+  }
+  return CONET_OK;
+}
+
+int launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2, float eps,
+                float bc1, float bc2, cudaStream_t s) {
+  adam_kernel<<<grid_for((long long)n, 256, 152 * 8), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+  return check_launch("adam_kernel");
+}
+
+int launch_weights_dgrad_layout(const float* w, int C, float* out, cudaStream_t s) {
+  weights_dgrad_kernel<<<grid_for(9LL * C * C, 256, 512), 256, 0, s>>>(w, C, out);
+  return check_launch("weights_dgrad_kernel");
+}
+
+}  // namespace conet

@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(COUT * 4) conv3x3_fp32_kernel(ConvArgs a) {
   }
 
   // ---------------------------------------------------------------- epilogue
-  const float4 bv = __ldg(reinterpret_cast<const float4*>(a.bias[br]) + cg);
+  const float4 bv = a.bias[br] ? __ldg(reinterpret_cast<const float4*>(a.bias[br]) + cg)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
   const float* __restrict__ resid = a.resid[br];
   float* __restrict__ out0 = a.out0[br];
   const bool ln = a.ln_g[br] != nullptr;

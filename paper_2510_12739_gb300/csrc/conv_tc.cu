@@ -1,0 +1,537 @@
+// 3x3 'same' convolution of every CoNet branch as an implicit GEMM on the 5th-generation
+// tensor cores (tcgen05) with TMEM accumulators and TMA-fed shared-memory operands.
+//
+// Tile: 128 resource elements = 128 consecutive subcarriers of one OFDM symbol of one slot
+// (rows of the MMA), all Cout channels of every branch (one MMA N = Cout per branch, the
+// branches' accumulators side by side in TMEM).  K runs over the 9 taps x Cin channels in
+// chunks of KC channels: for tap (dt, df) the A operand is the TMA box of the input
+// shifted by (dt, df); rows or subcarriers outside the grid come back as TMA zero fill,
+// which is exactly the conv's zero padding.  The B operand is the tap's [Cout][KC] weight
+// slice, both K-major.
+//
+// Warp roles (192 threads): warp 0 issues TMA loads into a ring of shared-memory stages,
+// warp 1 issues tcgen05.mma from one thread and commits each stage back to the producer,
+// warps 2-5 (one TMEM lane quarter each, one RE per thread) run the fused epilogue:
+// bias, residual add, ReLU / LayerNorm, the Hadamard fusion of the branches with its
+// LayerNorm, the next layer's pre-activation, and the 1x1 LLR head.  Two TMEM accumulator
+// sets (when they fit) let the epilogue of one tile overlap the MMAs of the next.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace conet {
+
+namespace {
+
+constexpr int TILE_M = 128;
+constexpr int EPI_WARPS = 4;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+__host__ __device__ constexpr int pow2_ceil(int x) {
+  int p = 32;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+template <int KIND, int NB, int CIN, int COUT, int KC>
+struct Cfg {
+  static constexpr int ELT = (KIND == 0 || KIND == 3) ? 2 : KIND == 1 ? 4 : 1;
+  static constexpr int ROW = KC * ELT;                  // bytes per operand row (= swizzle span)
+  static_assert(ROW == 32 || ROW == 64 || ROW == 128, "row bytes");
+  static constexpr int SLICES = ROW / 32;               // MMAs (32 bytes of K each) per chunk
+  static constexpr int A_BYTES = TILE_M * ROW;
+  static constexpr int B_BYTES = COUT * ROW;
+  static constexpr int STAGE_TX = NB * (A_BYTES + B_BYTES);
+  static constexpr int STAGE = (STAGE_TX + 1023) / 1024 * 1024;
+  static constexpr int K_ITERS = 9 * (CIN / KC);
+  static constexpr int COLS = pow2_ceil(NB * COUT);
+  static constexpr int N_ACC = 2 * COLS <= 512 ? 2 : 1;
+  static constexpr int TMEM_COLS = N_ACC * COLS;
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256) / STAGE);
+  static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
+  static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT);   // BF16 / TF32 / F16, E4M3
+  static_assert(STAGES >= 2, "not enough shared memory for two stages");
+  static_assert(COUT % 16 == 0 && COUT <= 256, "MMA N");
+  static_assert(NB * COUT <= 512, "TMEM columns");
+  static_assert(CIN % KC == 0, "K chunking");
+};
+
+// Shifted first and second moments of one channel vector (shift = its first element).
+struct Moments {
+  float k = 0.f, s1 = 0.f, s2 = 0.f;
+  __device__ __forceinline__ void add(float x, bool first) {
+    if (first) k = x;
+    const float d = x - k;
+    s1 += d;
+    s2 += d * d;
+  }
+  __device__ __forceinline__ void finish(int C, float& mean, float& rstd) const {
+    const float m1 = s1 / (float)C;
+    mean = k + m1;
+    rstd = rsqrtf(fmaxf(s2 / (float)C - m1 * m1, 0.f) + 1e-5f);
+  }
+};
+
+// v_b = acc_b + bias_b (+ resid_b) for the 16 channels of chunk j of every branch.
+template <int NB, int COUT>
+__device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, int j, bool valid, long long m,
+                                           float (&v)[NB][16]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b) tc::tmem_ld16(tacc + (uint32_t)(b * COUT + 16 * j), v[b]);
+  if (!valid) return;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const float4* bp = reinterpret_cast<const float4*>(a.bias[b] + 16 * j);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 x = __ldg(bp + i);
+      v[b][4 * i] += x.x;
+      v[b][4 * i + 1] += x.y;
+      v[b][4 * i + 2] += x.z;
+      v[b][4 * i + 3] += x.w;
+    }
+    if (a.resid[b]) {
+      const float4* rp = reinterpret_cast<const float4*>(a.resid[b] + m * COUT + 16 * j);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 x = __ldg(rp + i);
+        v[b][4 * i] += x.x;
+        v[b][4 * i + 1] += x.y;
+        v[b][4 * i + 2] += x.z;
+        v[b][4 * i + 3] += x.w;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void store16_f32(float* p, const float (&x)[16]) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+}
+
+__device__ __forceinline__ void store16_f16(__half* p, const float (&x)[16]) {
+  __align__(16) __half2 h[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+  uint4* q = reinterpret_cast<uint4*>(p);
+  q[0] = reinterpret_cast<const uint4*>(h)[0];
+  q[1] = reinterpret_cast<const uint4*>(h)[1];
+}
+
+__device__ __forceinline__ void store16_bf16(__nv_bfloat16* p, const float (&x)[16]) {
+  __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+  uint4* q = reinterpret_cast<uint4*>(p);
+  q[0] = reinterpret_cast<const uint4*>(h)[0];
+  q[1] = reinterpret_cast<const uint4*>(h)[1];
+}
+
+// The fused epilogue for one RE (this thread's TMEM lane): two passes over the
+// accumulator columns -- statistics of every LayerNorm it applies, then the outputs.
+template <int KIND, int NB, int COUT>
+__device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, bool valid, long long m) {
+  constexpr int CH = COUT / 16;
+  constexpr int QMAX = 8;
+  const bool pre_ln = a.pre == 2;
+  const bool fuse_ln = a.fuse && a.lnf_g != nullptr;
+  bool need_ln1[NB];
+  bool any_ln1 = false;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    need_ln1[b] = a.post[b] == 2;
+    any_ln1 = any_ln1 || need_ln1[b];
+  }
+  Moments mb[NB], mp;
+  if (pre_ln || fuse_ln || any_ln1) {
+    for (int j = 0; j < CH; ++j) {
+      float v[NB][16];
+      __syncwarp();
+      load_chunk<NB, COUT>(a, tacc, j, valid, m, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const bool first = (j == 0 && c == 0);
+        float p = 1.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const float x = v[b][c];
+          const float ab = a.pre == 1 ? fmaxf(x, 0.f) : x;
+          if (pre_ln) mb[b].add(x, first);
+          else if (need_ln1[b]) mb[b].add(ab, first);
+          p *= ab;
+        }
+        if (fuse_ln) mp.add(p, first);
+      }
+    }
+  }
+  float mean_b[NB], rstd_b[NB], mean_p = 0.f, rstd_p = 1.f;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) mb[b].finish(COUT, mean_b[b], rstd_b[b]);
+  if (fuse_ln) mp.finish(COUT, mean_p, rstd_p);
+
+  float hq[QMAX];
+#pragma unroll
+  for (int qq = 0; qq < QMAX; ++qq) hq[qq] = 0.f;
+  for (int j = 0; j < CH; ++j) {
+    float v[NB][16];
+    __syncwarp();
+    load_chunk<NB, COUT>(a, tacc, j, valid, m, v);
+    const int c0 = 16 * j;
+    // rows past the grid edge compute on don't-care values and store nothing
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (valid && a.t_out[b]) store16_f32(a.t_out[b] + m * COUT + c0, v[b]);
+    // a_b = pre(v_b), in place
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (a.pre == 1) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[b][c] = fmaxf(v[b][c], 0.f);
+      } else if (pre_ln) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          v[b][c] = fmaxf((v[b][c] - mean_b[b]) * rstd_b[b] * __ldg(a.ln2_g[b] + c0 + c) + __ldg(a.ln2_b[b] + c0 + c),
+                          0.f);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (valid && a.a_out[b]) store16_f32(a.a_out[b] + m * COUT + c0, v[b]);
+    // x_0 = fused (and normalised) product, or a_0; it replaces v[0] from here on
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float p = v[0][c];
+      if (a.fuse) {
+#pragma unroll
+        for (int b = 1; b < NB; ++b) p *= v[b][c];
+        if (fuse_ln) p = (p - mean_p) * rstd_p * __ldg(a.lnf_g + c0 + c) + __ldg(a.lnf_b + c0 + c);
+      }
+      v[0][c] = p;
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (valid && a.xs_out[b]) store16_f32(a.xs_out[b] + m * COUT + c0, v[b]);
+      if (valid && a.nx_out[b]) {
+        float o[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          float y = v[b][c];
+          if (a.post[b] == 2) y = (y - mean_b[b]) * rstd_b[b] * __ldg(a.ln1_g[b] + c0 + c) + __ldg(a.ln1_b[b] + c0 + c);
+          o[c] = a.post[b] ? fmaxf(y, 0.f) : y;
+        }
+        if constexpr (KIND == 3) store16_f16(reinterpret_cast<__half*>(a.nx_out[b]) + m * COUT + c0, o);
+        else store16_bf16(reinterpret_cast<__nv_bfloat16*>(a.nx_out[b]) + m * COUT + c0, o);
+      }
+    }
+    if (a.head_w) {
+#pragma unroll
+      for (int qq = 0; qq < QMAX; ++qq) {
+        if (qq >= a.Q) break;
+        float s = 0.f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) s += __ldg(a.head_w + qq * COUT + c0 + c) * v[0][c];
+        hq[qq] += s;
+      }
+    }
+  }
+  if (a.head_w && valid) {
+    for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) a.llr[m * a.Q + qq] = hq[qq] + __ldg(a.head_b + qq);
+  }
+}
+
+__device__ __forceinline__ void decode_tile(int tile, int T, int nfb, int& slot, int& t, int& fb) {
+  fb = tile % nfb;
+  const int st = tile / nfb;
+  t = st % T;
+  slot = st / T;
+}
+
+template <int KIND, int NB, int CIN, int COUT, int KC>
+__global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ TcMaps maps, TcConvArgs a) {
+  using K = Cfg<KIND, NB, CIN, COUT, KC>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)K::STAGES * K::STAGE);
+  uint64_t* empty = full + K::STAGES;
+  uint64_t* tfull = empty + K::STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < K::STAGES; ++s) {
+        tc::mbar_init(&full[s], 1);
+        tc::mbar_init(&empty[s], 1);
+      }
+      for (int i = 0; i < 2; ++i) {
+        tc::mbar_init(&tfull[i], 1);
+        tc::mbar_init(&tempty[i], EPI_WARPS);
+      }
+      tc::fence_mbar_init();
+      for (int b = 0; b < NB; ++b) {
+        tc::prefetch_tmap(&maps.a[b]);
+        tc::prefetch_tmap(&maps.w[b]);
+      }
+    }
+    __syncwarp();
+    tc::tmem_alloc(tmem_slot, K::TMEM_COLS);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tmem_slot;
+  int* err = a.err;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA producer
+    int s = 0;
+    uint32_t ph = 0;
+    uint32_t last_par[8];
+    bool used[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) used[i] = false;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x) {
+      int slot, t, fb;
+      decode_tile(tile, a.T, a.nfb, slot, t, fb);
+      for (int k = 0; k < K::K_ITERS; ++k) {
+        if (!tc::mbar_wait(&empty[s], ph ^ 1u, err, 1)) {
+          ok = false;
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&full[s], K::STAGE_TX);
+        const int tap = k / (CIN / KC), ch = (k % (CIN / KC)) * KC;
+        const int dt = tap / 3 - 1, df = tap % 3 - 1;
+        uint8_t* st = smem + (size_t)s * K::STAGE;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          tc::tma_load_4d(st + b * K::A_BYTES, &maps.a[b], &full[s], ch, fb * TILE_M + df, t + dt, slot);
+          tc::tma_load_3d(st + NB * K::A_BYTES + b * K::B_BYTES, &maps.w[b], &full[s], ch, 0, tap);
+        }
+        used[s] = true;
+        last_par[s] = ph;
+        if (++s == K::STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    // drain: every issued load has landed before the CTA may exit
+    for (int i = 0; i < K::STAGES; ++i)
+      if (used[i]) tc::mbar_wait(&full[i], last_par[i], err, 9);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    int s = 0;
+    uint32_t ph = 0;
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++it) {
+      const int acc = it % K::N_ACC;
+      const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
+      if (!tc::mbar_wait(&tempty[acc], aph ^ 1u, err, 2)) break;
+      tc::fence_after_sync();
+      const uint32_t dcol = tbase + (uint32_t)(acc * K::COLS);
+      for (int k = 0; k < K::K_ITERS; ++k) {
+        if (!tc::mbar_wait(&full[s], ph, err, 3)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t st = tc::smem_u32(smem + (size_t)s * K::STAGE);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+#pragma unroll
+          for (int j = 0; j < K::SLICES; ++j) {
+            const uint64_t ad = tc::smem_desc(st + b * K::A_BYTES + 32 * j, K::ROW);
+            const uint64_t bd = tc::smem_desc(st + NB * K::A_BYTES + b * K::B_BYTES + 32 * j, K::ROW);
+            tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, bd, K::IDESC, (k | j) != 0);
+          }
+        }
+        tc::mma_commit(&empty[s]);
+        if (++s == K::STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      tc::mma_commit(&tfull[acc]);
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ fused epilogue
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int row = 32 * q + lane;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+      const int acc = it % K::N_ACC;
+      const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
+      if (!tc::mbar_wait(&tfull[acc], aph, err, 4)) break;
+      tc::fence_after_sync();
+      int slot, t, fb;
+      decode_tile(tile, a.T, a.nfb, slot, t, fb);
+      const int f = fb * TILE_M + row;
+      const bool valid = f < a.F;
+      const long long m = ((long long)slot * a.T + t) * a.F + f;
+      const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + ((uint32_t)(32 * q) << 16);
+      tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m);
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, K::TMEM_COLS);
+  }
+}
+
+template <int KIND, int NB, int CIN, int COUT, int KC>
+int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
+  using K = Cfg<KIND, NB, CIN, COUT, KC>;
+  static int attr_done = 0;
+  if (!attr_done) {
+    CONET_CUDA(cudaFuncSetAttribute(conv_tc_kernel<KIND, NB, CIN, COUT, KC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM));
+    attr_done = 1;
+  }
+  int dev = 0, n_sm = 0;
+  CONET_CUDA(cudaGetDevice(&dev));
+  CONET_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = a.n_tiles < n_sm ? a.n_tiles : n_sm;
+  conv_tc_kernel<KIND, NB, CIN, COUT, KC><<<grid, TC_THREADS, K::SMEM, s>>>(maps, a);
+  return check_launch("conv_tc_kernel");
+}
+
+}  // namespace
+
+int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
+#define TC_CASE(KI, NBV, CI, CO, KCV) \
+  if (kind == KI && nb == NBV && cin == CI && cout == CO) return launch_tc_t<KI, NBV, CI, CO, KCV>(maps, a, s);
+  // BF16 (kind::f16): input layers take 16 padded channels (32-byte rows)
+  TC_CASE(0, 2, 16, 32, 16)
+  TC_CASE(0, 2, 32, 32, 32)
+  TC_CASE(0, 3, 16, 64, 16)
+  TC_CASE(0, 3, 64, 64, 32)
+  TC_CASE(0, 4, 16, 96, 16)
+  TC_CASE(0, 4, 96, 96, 32)
+  TC_CASE(0, 1, 16, 64, 16)
+  TC_CASE(0, 1, 64, 64, 32)
+  TC_CASE(0, 3, 16, 16, 16)
+  TC_CASE(0, 3, 16, 32, 16)
+  TC_CASE(0, 3, 32, 32, 32)
+  // FP16 operands (kind::f16, same rate, 11-bit significands)
+  TC_CASE(3, 2, 16, 32, 16)
+  TC_CASE(3, 2, 32, 32, 32)
+  TC_CASE(3, 3, 16, 64, 16)
+  TC_CASE(3, 3, 64, 64, 32)
+  TC_CASE(3, 4, 16, 96, 16)
+  TC_CASE(3, 4, 96, 96, 32)
+  TC_CASE(3, 3, 16, 32, 16)
+  TC_CASE(3, 3, 32, 32, 32)
+#undef TC_CASE
+  return fail(CONET_ERR_UNSUPPORTED, "tensor-core conv kind=%d branches=%d Cin=%d Cout=%d not instantiated", kind, nb,
+              cin, cout);
+}
+
+// ------------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+static CUtensorMapSwizzle swizzle_of(int row_bytes) {
+  return row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                          : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+}
+
+static CUtensorMapDataType dtype_of(int kind) {
+  if (kind == 3) return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                   : kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+}
+
+int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return fail(CONET_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const int e = (kind == 0 || kind == 3) ? 2 : kind == 1 ? 4 : 1;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)F, (cuuint64_t)T, (cuuint64_t)slots};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * e, (cuuint64_t)F * C * e, (cuuint64_t)T * F * C * e};
+  const cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)TILE_M, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = enc(map, dtype_of(kind), 4, const_cast<void*>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(kc * e), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CONET_ERR_CUDA, "activation tensor map encode failed (%d)", (int)r);
+  return CONET_OK;
+}
+
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return fail(CONET_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const int e = (kind == 0 || kind == 3) ? 2 : kind == 1 ? 4 : 1;
+  const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)cout, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)cin * e, (cuuint64_t)cout * cin * e};
+  const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)cout, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(map, dtype_of(kind), 3, const_cast<void*>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(kc * e), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CONET_ERR_CUDA, "weight tensor map encode failed (%d)", (int)r);
+  return CONET_OK;
+}
+
+int tc_chunk(int kind, int cin) {
+  (void)kind;
+  return cin <= 16 ? 16 : 32;
+}
+
+// [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] BF16, zero padded input channels
+__global__ void weights_bf16_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+                                    __nv_bfloat16* __restrict__ out) {
+  const int n = 9 * cout * cin_dst;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int ci = i % cin_dst, rem = i / cin_dst, co = rem % cout, tap = rem / cout;
+    out[i] = __float2bfloat16_rn(ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f);
+  }
+}
+
+__global__ void weights_f16_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+                                   __half* __restrict__ out) {
+  const int n = 9 * cout * cin_dst;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int ci = i % cin_dst, rem = i / cin_dst, co = rem % cout, tap = rem / cout;
+    out[i] = __float2half_rn(ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f);
+  }
+}
+
+int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s) {
+  if (kind == 3)
+    weights_f16_kernel<<<grid_for(9LL * cout * cin_dst, 256, 512), 256, 0, s>>>(w, cout, cin_src, cin_dst,
+                                                                                reinterpret_cast<__half*>(out));
+  else
+    weights_bf16_kernel<<<grid_for(9LL * cout * cin_dst, 256, 512), 256, 0, s>>>(
+        w, cout, cin_src, cin_dst, reinterpret_cast<__nv_bfloat16*>(out));
+  return check_launch("weights_16_kernel");
+}
+
+}  // namespace conet

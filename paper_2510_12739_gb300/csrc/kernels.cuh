@@ -1,6 +1,7 @@
 // Internal kernel launchers of libconet and their argument blocks.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,8 +45,8 @@ int launch_init_segment(float* p, size_t off, size_t n, float std, float constan
 // ---------------------------------------------------------------- receiver DSP
 int launch_assemble(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
                     int c_pad, float* X0, cudaStream_t s);
-int launch_assemble_bf16(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
-                         int c_pad, void* X0, cudaStream_t s);
+int launch_assemble_16(int kind, const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
+                       int c_pad, void* X0, cudaStream_t s);
 
 struct LmmseArgs {
   const float* Y;
@@ -103,6 +104,110 @@ struct FuseArgs {
   long long M;
 };
 int launch_fuse(const FuseArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- backward
+constexpr int EW_PART_CTAS = 512;     // CTAs (hence partial rows) of the elementwise bwd kernels
+constexpr int WG_MAX_SPLITS = 64;
+
+// Hadamard fusion backward (+ post-fusion LN, + ReLU mask of the fused activations):
+// gu_0 = dp prod_{i>0} u_i,  gu_b = gxs_b + dp prod_{i!=b} u_i  (fuse), else gu_b = gx_b.
+struct FuseBwdArgs {
+  const float* u[MAX_BR];
+  const float* gx0;
+  const float* gxs[MAX_BR];   // [0] unused; NULL = zero
+  float* gu[MAX_BR];
+  const float* ln_g;          // post-fusion LN gain or NULL
+  float* part;                // [grid][2][C] dgamma / dbeta partials (when ln_g)
+  int n_br, fuse, relu_mask, C;
+  long long M;
+};
+int launch_fuse_bwd(const FuseBwdArgs& a, cudaStream_t s);
+
+// out = add + d/dx relu(LN(x)*g + b) . g_out   (or add + [x > 0] g_out without LN)
+struct LnReluBwdArgs {
+  const float* g;
+  const float* x;
+  const float* ln_g;
+  const float* ln_b;
+  const float* add;
+  float* out;
+  float* part;                // [grid][2][C] dgamma / dbeta partials (when ln_g)
+  int C;
+  long long M;
+};
+int launch_ln_relu_bwd(const LnReluBwdArgs& a, cudaStream_t s);
+
+struct HeadBwdArgs {
+  const float* dllr;
+  const float* x0;
+  const float* w;
+  float* gx0;
+  float* part;                // [grid][Q*C + Q]
+  int C, Q;
+  long long M;
+};
+int launch_head_bwd(const HeadBwdArgs& a, cudaStream_t s);
+int launch_channel_sums(const float* g, long long M, int C, float* part, cudaStream_t s);
+int launch_reduce_partials(const float* part, int n_part, int n, float* out, int accumulate, cudaStream_t s);
+int ew_grid(long long M);
+
+struct WgradArgs {
+  const float* x[MAX_BR];     // conv input [M][cin]
+  const float* g[MAX_BR];     // grad wrt conv output [M][cout]
+  float* dW[MAX_BR];          // master layout [cout][3][3][cin_src]
+  int cin_src[MAX_BR];
+  float* part;                // split partials
+  int cin, cout, n_br, T, F;
+  long long M;
+};
+int wgrad_splits(long long M, int cin, int cout, int n_br);
+size_t wgrad_partial_floats(long long M, int cin, int cout, int n_br);
+int launch_wgrad(const WgradArgs& a, cudaStream_t s);
+
+int launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2, float eps,
+                float bc1, float bc2, cudaStream_t s);
+int launch_weights_dgrad_layout(const float* w, int C, float* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- tensor-core convolution
+struct TcMaps {
+  CUtensorMap a[MAX_BR];       // activations [slots][T][F][Cin], box {KC, 128, 1, 1}
+  CUtensorMap w[MAX_BR];       // weights [9][Cout][Cin], box {KC, Cout, 1}
+};
+
+// Fused epilogue, per RE and branch b:
+//   v_b = conv_b + bias_b (+ resid_b)                  -> t_out[b]   (FP32, optional)
+//   a_b = v_b | relu(v_b) | relu(LN2_b(v_b))            (pre = 0 | 1 | 2)
+//   x_0 = fuse ? LN_f?(prod_b a_b) : a_0;  x_b = a_b    -> xs_out[b]  (FP32, optional)
+//   next_b = x_b | relu(x_b) | relu(LN1_b(x_b))         (post[b] = 0 | 1 | 2) -> nx_out[b]
+//   llr = head_w x_0 + head_b                           (when head_w)
+struct TcConvArgs {
+  int n_tiles, T, F, nfb;
+  const float* bias[MAX_BR];
+  const float* resid[MAX_BR];
+  int pre;
+  const float* ln2_g[MAX_BR];
+  const float* ln2_b[MAX_BR];
+  int fuse;
+  const float* lnf_g;
+  const float* lnf_b;
+  float* t_out[MAX_BR];
+  float* a_out[MAX_BR];        // a_b (FP32, optional; kept for backward)
+  float* xs_out[MAX_BR];
+  void* nx_out[MAX_BR];
+  int post[MAX_BR];
+  const float* ln1_g[MAX_BR];
+  const float* ln1_b[MAX_BR];
+  const float* head_w;
+  const float* head_b;
+  float* llr;
+  int Q;
+  int* err;                    // device error word (first timed-out wait)
+};
+int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
+int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc);
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc);
+int tc_chunk(int kind, int cin);
+int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- weights
 // Re-layout of the FP32 master conv weights [Cout][3][3][cin_src] into the kernels'

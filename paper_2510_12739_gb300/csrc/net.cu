@@ -69,8 +69,9 @@ struct Acts {
   }
   static size_t count(const conet_s* h) {
     const int nb = h->nb, d = h->cfg.depth;
-    if (!h->cfg.residual) return h->cfg.train ? (size_t)d * nb + d : 2 * (size_t)nb;
-    return h->cfg.train ? (size_t)nb + d + 1 + 4 * (size_t)d * nb : 4 * (size_t)nb;
+    const bool tc = h->prec != CONET_FP32;   // tensor-core inference keeps its conv inputs in 16 bits
+    if (!h->cfg.residual) return h->cfg.train ? (size_t)d * nb + d : (tc ? 0 : 2 * (size_t)nb);
+    return h->cfg.train ? (size_t)nb + d + 1 + 4 * (size_t)d * nb : (tc ? 2 : 4) * (size_t)nb;
   }
 };
 
@@ -78,6 +79,10 @@ const float* P(const conet_s* h, long off) { return off < 0 ? nullptr : h->param
 const float* W(const conet_s* h, long off) { return h->wt + h->wt_off.at((size_t)off); }
 
 }  // namespace
+
+int tc_setup(conet_s* h);
+int tc_weights_changed(conet_s* h, cudaStream_t s);
+int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
 
 int net_setup(conet_s* h) {
   const size_t n = h->L.total;
@@ -95,9 +100,18 @@ int net_setup(conet_s* h) {
   CONET_TRY(dev_alloc_t(h, &h->wt, wt));
   CONET_TRY(dev_alloc_t(h, &h->mask, (size_t)h->T * h->F));
   CONET_TRY(dev_alloc_t(h, &h->psym, (size_t)h->T * h->F * 2));
-  const size_t re = (size_t)h->cfg.max_batch * h->T * h->F;
-  CONET_TRY(dev_alloc_t(h, &h->X0, re * h->c_pad));
+  // Tensor-core inference streams the batch through activation buffers sized for a chunk of
+  // slots (at most ~48 GB of activations); FP32 and training keep the whole batch.
   const size_t na = Acts::count(h);
+  h->chunk = h->cfg.max_batch;
+  if (h->prec != CONET_FP32 && !h->cfg.train) {
+    const double per_slot = (double)h->T * h->F * ((double)na * h->C * 4 + 2.0 * h->nb * h->C * 2 + 16 * 2);
+    const double fit = 48e9 / per_slot;
+    h->chunk = fit < 1 ? 1 : (fit < h->cfg.max_batch ? (int)fit : h->cfg.max_batch);
+  }
+  const size_t re = (size_t)h->chunk * h->T * h->F;
+  const bool need_x0 = h->prec == CONET_FP32 || h->cfg.train;
+  CONET_TRY(dev_alloc_t(h, &h->X0, need_x0 ? re * h->c_pad : 4));
   h->act.resize(na);
   for (size_t i = 0; i < na; ++i) CONET_TRY(dev_alloc_t(h, &h->act[i], re * h->C));
   CONET_TRY(dev_alloc_t(h, &h->d_loss, 1));
@@ -114,6 +128,33 @@ int net_setup(conet_s* h) {
   pg.k0 = (uint32_t)h->cfg.pilot_seed;
   pg.k1 = (uint32_t)(h->cfg.pilot_seed >> 32);
   CONET_TRY(launch_pilots(h->T, h->F, pg, h->mask, h->psym, 0));
+  h->n_pilot_re = 0;
+  for (int t = 0; t < h->T; ++t) {
+    bool p = false;
+    for (int i = 0; i < h->cfg.n_pilot_syms; ++i) p = p || h->cfg.pilot_syms[i] == t;
+    if (p) h->n_pilot_re += (h->F + h->cfg.pilot_comb - 1) / h->cfg.pilot_comb;
+  }
+  if (h->cfg.train) {
+    size_t wd = 0;
+    for (const auto& c : h->L.convs) {
+      if (c.cin == h->cin) continue;   // the input conv needs no data gradient
+      h->wd_off[c.off] = wd;
+      wd += (size_t)9 * c.cin * c.cout;
+    }
+    CONET_TRY(dev_alloc_t(h, &h->wd, wd ? wd : 1));
+    for (int k = 0; k < 3; ++k)
+      for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->G[k][b], re * h->C));
+    CONET_TRY(dev_alloc_t(h, &h->ew_part, (size_t)EW_PART_CTAS * (size_t)(h->Q * h->C + h->Q + 2 * h->C)));
+    // split partials of the weight gradient, sized for the largest split count
+    const size_t wg = (size_t)WG_MAX_SPLITS * h->nb * 9 * (size_t)(h->C > h->c_pad ? h->C : h->c_pad) * h->C;
+    CONET_TRY(dev_alloc_t(h, &h->wg_part, wg));
+    CONET_TRY(dev_alloc_t(h, &h->sim_Y, re * h->N * 2));
+    CONET_TRY(dev_alloc_t(h, &h->sim_bits, re * h->Q));
+    CONET_TRY(dev_alloc_t(h, &h->sim_nv, (size_t)h->cfg.max_batch));
+    CONET_TRY(dev_alloc_t(h, &h->llr, re * h->Q));
+    CONET_TRY(dev_alloc_t(h, &h->dllr, re * h->Q));
+  }
+  CONET_TRY(tc_setup(h));
   CONET_CUDA(cudaDeviceSynchronize());
   return CONET_OK;
 }
@@ -122,8 +163,10 @@ int net_weights_changed(conet_s* h, cudaStream_t s) {
   for (const auto& c : h->L.convs) {
     const int cin_dst = c.cin == h->cin ? h->c_pad : c.cin;
     CONET_TRY(launch_weights_to_tap_major(h->params + c.off, c.cout, c.cin, cin_dst, h->wt + h->wt_off.at(c.off), s));
+    if (h->cfg.train && c.cin != h->cin)
+      CONET_TRY(launch_weights_dgrad_layout(h->params + c.off, c.cout, h->wd + h->wd_off.at(c.off), s));
   }
-  return CONET_OK;
+  return tc_weights_changed(h, s);
 }
 
 static int conv_layer(conet_s* h, ConvArgs& a, int cin, cudaStream_t s) {
@@ -158,6 +201,7 @@ static FuseArgs fuse_args(conet_s* h, int B) {
 }
 
 int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
+  if (h->prec == CONET_BF16 || h->prec == CONET_FP16) return net_forward_tc(h, Y, mask, B, llr, s);
   if (h->prec != CONET_FP32) return fail(CONET_ERR_UNSUPPORTED, "precision %d forward not built yet", h->prec);
   const Acts A{h};
   const Layout& L = h->L;
@@ -247,19 +291,390 @@ int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* l
   return CONET_OK;
 }
 
+// ------------------------------------------------------------------ tensor-core (BF16) path
+namespace {
+
+constexpr int TC_CIN0 = 16;   // padded input channels of the BF16 input layer
+
+int tc_kind(const conet_s* h) { return h->prec == CONET_BF16 ? 0 : h->prec == CONET_FP16 ? 3 : -1; }
+
+// conv launch index -> (per branch) master weight offset
+long tc_conv_w(const conet_s* h, int idx, int b) {
+  const Layout& L = h->L;
+  if (idx == 0) return L.in_w[b];
+  if (!h->cfg.residual) return L.lw[b][idx - 1];
+  const int k = (idx - 1) / 2;
+  return (idx - 1) % 2 == 0 ? L.blk[b][k].c1w : L.blk[b][k].c2w;
+}
+
+int tc_n_convs(const conet_s* h) { return h->cfg.residual ? 1 + 2 * h->cfg.depth : h->cfg.depth; }
+
+// input buffer of conv launch idx for branch b
+const void* tc_conv_in(const conet_s* h, int idx, int b) {
+  if (idx == 0) return h->X0b;
+  if (!h->cfg.residual) return h->nxb[(idx - 1) & 1][b];
+  return h->nxb[(idx - 1) % 2 == 0 ? 0 : 1][b];
+}
+
+}  // namespace
+
+int tc_setup(conet_s* h) {
+  if (tc_kind(h) < 0) return CONET_OK;
+  const int kind = tc_kind(h);
+  if (h->cin > TC_CIN0) return fail(CONET_ERR_UNSUPPORTED, "BF16 path takes at most %d input channels", TC_CIN0);
+  if (h->C % 16) return fail(CONET_ERR_UNSUPPORTED, "BF16 path needs width %% 16 == 0");
+  const size_t re = (size_t)h->chunk * h->T * h->F;
+  CONET_TRY(dev_alloc(h, &h->X0b, re * TC_CIN0 * 2));
+  for (int i = 0; i < 2; ++i)
+    for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc(h, &h->nxb[i][b], re * h->C * 2));
+  size_t wb = 0;
+  for (const auto& c : h->L.convs) {
+    const int cin_dst = c.cin == h->cin ? TC_CIN0 : c.cin;
+    h->wb_off[c.off] = wb;
+    wb += (size_t)9 * cin_dst * c.cout;
+  }
+  CONET_TRY(dev_alloc(h, &h->wb, wb * 2));
+  CONET_CUDA(cudaMemset(h->wb, 0, wb * 2));
+  CONET_TRY(dev_alloc_t(h, &h->d_err, 1));
+  CONET_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+  const int n = tc_n_convs(h);
+  h->tcmaps.resize(n);
+  for (int idx = 0; idx < n; ++idx) {
+    const int cin = idx == 0 ? TC_CIN0 : h->C;
+    const int kc = tc_chunk(kind, cin);
+    for (int b = 0; b < h->nb; ++b) {
+      CONET_TRY(make_act_map(&h->tcmaps[idx].a[b], kind, tc_conv_in(h, idx, b), cin, h->F, h->T, h->chunk, kc));
+      const void* w = static_cast<const uint16_t*>(h->wb) + h->wb_off.at((size_t)tc_conv_w(h, idx, b));
+      CONET_TRY(make_weight_map(&h->tcmaps[idx].w[b], kind, w, cin, h->C, kc));
+    }
+  }
+  return CONET_OK;
+}
+
+int tc_weights_changed(conet_s* h, cudaStream_t s) {
+  if (tc_kind(h) < 0) return CONET_OK;
+  for (const auto& c : h->L.convs) {
+    const int cin_dst = c.cin == h->cin ? TC_CIN0 : c.cin;
+    CONET_TRY(launch_weights_16(tc_kind(h), h->params + c.off, c.cout, c.cin, cin_dst,
+                                static_cast<uint16_t*>(h->wb) + h->wb_off.at(c.off), s));
+  }
+  return CONET_OK;
+}
+
+static int tc_conv(conet_s* h, int idx, TcConvArgs& a, int B, cudaStream_t s) {
+  a.T = h->T;
+  a.F = h->F;
+  a.nfb = (h->F + 127) / 128;
+  a.n_tiles = B * h->T * a.nfb;
+  a.Q = h->Q;
+  a.err = h->d_err;
+  const int cin = idx == 0 ? TC_CIN0 : h->C;
+  prof_begin(h, idx == 0 ? PK_CONV_IN : PK_CONV, s);
+  const int rc = launch_conv_tc(tc_kind(h), h->nb, cin, h->C, h->tcmaps[idx], a, s);
+  prof_end(h, s);
+  return rc;
+}
+
+static int net_forward_tc_chunk(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
+
+int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
+  for (int c0 = 0; c0 < B; c0 += h->chunk) {
+    const int Bc = B - c0 < h->chunk ? B - c0 : h->chunk;
+    CONET_TRY(net_forward_tc_chunk(h, Y + (size_t)c0 * h->N * h->T * h->F * 2, mask, Bc,
+                                   llr + (size_t)c0 * h->T * h->F * h->Q, s));
+  }
+  h->fwd_B = B;
+  return CONET_OK;
+}
+
+static int net_forward_tc_chunk(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
+  const Acts A{h};
+  const Layout& L = h->L;
+  const int nb = h->nb, depth = h->cfg.depth;
+  const bool train = h->cfg.train != 0;
+  if (train && h->cfg.residual) return fail(CONET_ERR_UNSUPPORTED, "BF16 training of residual networks");
+  prof_begin(h, PK_ASSEMBLE, s);
+  CONET_TRY(launch_assemble_16(tc_kind(h), Y, mask, h->psym, B, h->N, h->T, h->F, TC_CIN0, h->X0b, s));
+  if (train) CONET_TRY(launch_assemble(Y, mask, h->psym, B, h->N, h->T, h->F, h->c_pad, h->X0, s));
+  prof_end(h, s);
+  if (!h->cfg.residual) {
+    for (int l = 0; l < depth; ++l) {
+      TcConvArgs a = {};
+      for (int b = 0; b < nb; ++b) {
+        a.bias[b] = P(h, l == 0 ? L.in_b[b] : L.lb[b][l - 1]);
+        if (l + 1 < depth) a.nx_out[b] = h->nxb[l & 1][b];
+        if (train) a.a_out[b] = A.A(l, b);
+      }
+      if (train) a.xs_out[0] = A.XM(l);
+      a.pre = 1;
+      a.fuse = fused_at(h->cfg, l);
+      a.lnf_g = P(h, L.fg[l]);
+      a.lnf_b = P(h, L.fb[l]);
+      if (l == depth - 1) {
+        a.head_w = P(h, L.hw);
+        a.head_b = P(h, L.hb);
+        a.llr = llr;
+      }
+      CONET_TRY(tc_conv(h, l, a, B, s));
+    }
+  } else {
+    // input layer, then per block conv1 (LN2 + ReLU epilogue) and conv2 (residual add,
+    // Hadamard fusion + LN, next pre-activation or head)
+    for (int idx = 0; idx < 1 + 2 * depth; ++idx) {
+      TcConvArgs a = {};
+      const int k = (idx - 1) / 2;
+      const bool conv1 = idx > 0 && (idx - 1) % 2 == 0;
+      if (conv1) {
+        for (int b = 0; b < nb; ++b) {
+          a.bias[b] = P(h, L.blk[b][k].c1b);
+          a.ln2_g[b] = P(h, L.blk[b][k].ln2g);
+          a.ln2_b[b] = P(h, L.blk[b][k].ln2b);
+          a.nx_out[b] = h->nxb[1][b];
+        }
+        a.pre = 2;
+      } else {
+        const int point = idx == 0 ? 0 : k + 1;        // fusion point after this conv
+        for (int b = 0; b < nb; ++b) {
+          a.bias[b] = P(h, idx == 0 ? L.in_b[b] : L.blk[b][k].c2b);
+          if (idx > 0) a.resid[b] = h->act[(size_t)(k & 1) * nb + b];
+          a.xs_out[b] = h->act[(size_t)(point & 1) * nb + b];
+          if (point < depth) {
+            a.nx_out[b] = h->nxb[0][b];
+            const long g = L.blk[b][point].ln1g;
+            a.post[b] = g >= 0 ? 2 : 1;
+            a.ln1_g[b] = P(h, g);
+            a.ln1_b[b] = P(h, L.blk[b][point].ln1b);
+          }
+        }
+        a.pre = idx == 0 ? 1 : 0;
+        a.fuse = fused_at(h->cfg, point);
+        a.lnf_g = P(h, L.fg[point]);
+        a.lnf_b = P(h, L.fb[point]);
+        if (point == depth) {
+          a.head_w = P(h, L.hw);
+          a.head_b = P(h, L.hb);
+          a.llr = llr;
+        }
+      }
+      CONET_TRY(tc_conv(h, idx, a, B, s));
+    }
+  }
+  h->fwd_B = B;
+  return CONET_OK;
+}
+
+// ------------------------------------------------------------------ backward
+namespace {
+
+struct Bwd {
+  conet_s* h;
+  cudaStream_t s;
+  long long M;
+
+  int reduce_ew(int n, long off) {   // sum the elementwise kernels' partials into grads[off..off+n)
+    return launch_reduce_partials(h->ew_part, ew_grid(M), n, h->grads + off, 0, s);
+  }
+  int bias(const float* g, long off) {
+    CONET_TRY(launch_channel_sums(g, M, h->C, h->ew_part, s));
+    return reduce_ew(h->C, off);
+  }
+  // weight + bias gradients of one conv layer of every branch
+  int wgrad(const float* const* x, const float* const* g, bool input_layer, const long* w_off, const long* b_off) {
+    const int cin_pad = input_layer ? h->c_pad : h->C;
+    WgradArgs w = {};
+    for (int b = 0; b < h->nb; ++b) {
+      w.x[b] = x[b];
+      w.g[b] = g[b];
+      w.dW[b] = h->grads + w_off[b];
+      w.cin_src[b] = input_layer ? h->cin : h->C;
+    }
+    w.part = h->wg_part;
+    w.cin = cin_pad;
+    w.cout = h->C;
+    w.n_br = h->nb;
+    w.T = h->T;
+    w.F = h->F;
+    w.M = M;
+    prof_begin(h, PK_BACKWARD, s);
+    const int rc = launch_wgrad(w, s);
+    prof_end(h, s);
+    CONET_TRY(rc);
+    for (int b = 0; b < h->nb; ++b) CONET_TRY(bias(g[b], b_off[b]));
+    return CONET_OK;
+  }
+  // data gradient of a body conv of every branch: out = conv3x3(g, rotated W)
+  int dgrad(float* const* g, const long* w_off, float* const* out) {
+    ConvArgs c = {};
+    c.M = (int)M;
+    c.T = h->T;
+    c.F = h->F;
+    for (int b = 0; b < h->nb; ++b) {
+      c.in[b] = g[b];
+      c.w[b] = h->wd + h->wd_off.at((size_t)w_off[b]);
+      c.out0[b] = out[b];
+    }
+    prof_begin(h, PK_BACKWARD, s);
+    const int rc = launch_conv3x3_fp32(c, h->nb, h->C, h->C, s);
+    prof_end(h, s);
+    return rc;
+  }
+  int fuse(const float* const* u, const float* gx0, float* const* gxs, float* const* gu, int point, int relu_mask) {
+    FuseBwdArgs f = {};
+    for (int b = 0; b < h->nb; ++b) {
+      f.u[b] = u[b];
+      f.gu[b] = gu[b];
+      f.gxs[b] = b ? gxs[b] : nullptr;
+    }
+    f.gx0 = gx0;
+    f.ln_g = P(h, h->L.fg[point]);
+    f.part = f.ln_g ? h->ew_part : nullptr;
+    f.n_br = h->nb;
+    f.fuse = fused_at(h->cfg, point);
+    f.relu_mask = relu_mask;
+    f.C = h->C;
+    f.M = M;
+    CONET_TRY(launch_fuse_bwd(f, s));
+    if (f.ln_g) CONET_TRY(reduce_ew(2 * h->C, h->L.fg[point]));
+    return CONET_OK;
+  }
+  int ln_relu(const float* g, const float* x, long lng, long lnb, const float* add, float* out) {
+    LnReluBwdArgs a = {};
+    a.g = g;
+    a.x = x;
+    a.ln_g = P(h, lng);
+    a.ln_b = P(h, lnb);
+    a.add = add;
+    a.out = out;
+    a.part = a.ln_g ? h->ew_part : nullptr;
+    a.C = h->C;
+    a.M = M;
+    CONET_TRY(launch_ln_relu_bwd(a, s));
+    if (a.ln_g) CONET_TRY(reduce_ew(2 * h->C, lng));
+    return CONET_OK;
+  }
+};
+
+}  // namespace
+
 int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
-  (void)h; (void)dllr; (void)B; (void)s;
-  return fail(CONET_ERR_UNSUPPORTED, "backward not built yet");
+  if (h->prec != CONET_FP32 && ((h->prec != CONET_BF16 && h->prec != CONET_FP16) || h->cfg.residual))
+    return fail(CONET_ERR_UNSUPPORTED, "precision %d backward of this network not built yet", h->prec);
+  const Acts A{h};
+  const Layout& L = h->L;
+  const int nb = h->nb, depth = h->cfg.depth, C = h->C;
+  Bwd bw{h, s, (long long)B * h->T * h->F};
+  float* const* G0 = h->G[0];
+  float* const* G1 = h->G[1];
+  float* const* G2 = h->G[2];
+  float* nulw[MAX_BR] = {};
+  // head: grad wrt the head input, dW_h and db_h (stored contiguously)
+  HeadBwdArgs hb = {};
+  hb.dllr = dllr;
+  hb.x0 = h->cfg.residual ? A.RXM(depth) : A.XM(depth - 1);
+  hb.w = P(h, L.hw);
+  hb.gx0 = G0[0];
+  hb.part = h->ew_part;
+  hb.C = C;
+  hb.Q = h->Q;
+  hb.M = bw.M;
+  CONET_TRY(launch_head_bwd(hb, s));
+  CONET_TRY(bw.reduce_ew(h->Q * C + h->Q, L.hw));
+  long w_off[MAX_BR], b_off[MAX_BR];
+  if (!h->cfg.residual) {
+    float* const* gxs = nulw;   // support gradients entering the top layer: zero
+    for (int l = depth - 1; l >= 0; --l) {
+      const float* u[MAX_BR];
+      for (int b = 0; b < nb; ++b) u[b] = A.A(l, b);
+      CONET_TRY(bw.fuse(u, G0[0], gxs, G1, l, 1));
+      const float* x[MAX_BR];
+      for (int b = 0; b < nb; ++b) {
+        x[b] = l == 0 ? h->X0 : (b == 0 ? A.XM(l - 1) : A.A(l - 1, b));
+        w_off[b] = l == 0 ? L.in_w[b] : L.lw[b][l - 1];
+        b_off[b] = l == 0 ? L.in_b[b] : L.lb[b][l - 1];
+      }
+      CONET_TRY(bw.wgrad(x, G1, l == 0, w_off, b_off));
+      if (l > 0) {
+        CONET_TRY(bw.dgrad(G1, w_off, G0));
+        gxs = G0;
+      }
+    }
+  } else {
+    float* const* gxs = nulw;
+    for (int k = depth; k >= 1; --k) {
+      const int blk = k - 1;
+      const float* u[MAX_BR];
+      for (int b = 0; b < nb; ++b) u[b] = A.U(blk, b);
+      CONET_TRY(bw.fuse(u, G0[0], gxs, G1, k, 0));                       // G1 = d u
+      const float* x[MAX_BR];
+      // conv2: input h2, output gradient d u
+      for (int b = 0; b < nb; ++b) {
+        x[b] = A.H2(blk, b);
+        w_off[b] = L.blk[b][blk].c2w;
+        b_off[b] = L.blk[b][blk].c2b;
+      }
+      CONET_TRY(bw.wgrad(x, G1, false, w_off, b_off));
+      CONET_TRY(bw.dgrad(G1, w_off, G2));                               // G2 = d h2
+      for (int b = 0; b < nb; ++b)                                      // G0 = d t1
+        CONET_TRY(bw.ln_relu(G2[b], A.T1(blk, b), L.blk[b][blk].ln2g, L.blk[b][blk].ln2b, nullptr, G0[b]));
+      for (int b = 0; b < nb; ++b) {
+        x[b] = A.H1(blk, b);
+        w_off[b] = L.blk[b][blk].c1w;
+        b_off[b] = L.blk[b][blk].c1b;
+      }
+      CONET_TRY(bw.wgrad(x, G0, false, w_off, b_off));
+      CONET_TRY(bw.dgrad(G0, w_off, G2));                               // G2 = d h1
+      for (int b = 0; b < nb; ++b)                                      // G0 = d x (skip + pre-act)
+        CONET_TRY(bw.ln_relu(G2[b], A.XS(blk, b), L.blk[b][blk].ln1g, L.blk[b][blk].ln1b, G1[b], G0[b]));
+      gxs = G0;
+    }
+    const float* u[MAX_BR];
+    for (int b = 0; b < nb; ++b) u[b] = A.A0(b);
+    CONET_TRY(bw.fuse(u, G0[0], gxs, G1, 0, 1));
+    const float* x[MAX_BR];
+    for (int b = 0; b < nb; ++b) {
+      x[b] = h->X0;
+      w_off[b] = L.in_w[b];
+      b_off[b] = L.in_b[b];
+    }
+    CONET_TRY(bw.wgrad(x, G1, true, w_off, b_off));
+  }
+  return CONET_OK;
 }
 
 int net_adam(conet_s* h, float lr, int step, cudaStream_t s) {
-  (void)h; (void)lr; (void)step; (void)s;
-  return fail(CONET_ERR_UNSUPPORTED, "Adam not built yet");
+  const double b1 = 0.9, b2 = 0.999;
+  const float bc1 = (float)(1.0 - pow(b1, step)), bc2 = (float)(1.0 - pow(b2, step));
+  prof_begin(h, PK_ADAM, s);
+  const int rc = launch_adam(h->params, h->grads, h->adam_m, h->adam_v, h->L.total, lr, (float)b1, (float)b2, 1e-8f,
+                             bc1, bc2, s);
+  prof_end(h, s);
+  CONET_TRY(rc);
+  return net_weights_changed(h, s);
 }
 
-int net_train_step(conet_s* h, const SimArgs& a, uint64_t step, int B, float lr, double* loss_out, cudaStream_t s) {
-  (void)h; (void)a; (void)step; (void)B; (void)lr; (void)loss_out; (void)s;
-  return fail(CONET_ERR_UNSUPPORTED, "train step not built yet");
+int net_train_step(conet_s* h, const SimArgs& a0, uint64_t step, int B, float lr, double* loss_out, cudaStream_t s) {
+  SimArgs a = a0;
+  a.Y = h->sim_Y;
+  a.bits = h->sim_bits;
+  a.H = nullptr;
+  a.noise_var = h->sim_nv;
+  a.interf_var = nullptr;
+  CONET_TRY(launch_sim(a, B, s));
+  CONET_TRY(net_forward(h, h->sim_Y, h->mask, B, h->llr, s));
+  const double count = (double)B * ((double)h->T * h->F - h->n_pilot_re) * h->Q;
+  CONET_CUDA(cudaMemsetAsync(h->d_loss, 0, sizeof(double), s));
+  CONET_TRY(launch_loss_ber(h->llr, h->sim_bits, h->mask, B, h->T, h->F, h->Q, (float)(1.0 / count), h->dllr,
+                            h->d_loss, nullptr, nullptr, s));
+  CONET_TRY(net_backward(h, h->dllr, B, s));
+  CONET_TRY(net_adam(h, lr, (int)(step + 1), s));
+  if (loss_out) {
+    double v = 0.0;
+    CONET_CUDA(cudaMemcpyAsync(&v, h->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CONET_CUDA(cudaStreamSynchronize(s));
+    *loss_out = v / count;
+    if (!isfinite(*loss_out)) return fail(CONET_ERR_NONFINITE, "training loss is not finite");
+  }
+  return CONET_OK;
 }
 
 }  // namespace conet

@@ -59,6 +59,19 @@ struct conet_s {
   float* psym = nullptr;                     // pilot symbols [T][F][2]
   float* X0 = nullptr;                       // assembled input [B][T][F][c_pad]
   std::vector<float*> act;                   // activation buffers, max_batch*T*F*C floats each
+  float* wd = nullptr;                       // body conv weights for dgrad: [9][Cout][Cin], rotated
+  std::map<size_t, size_t> wd_off;
+  float* G[3][conet::MAX_BR] = {};           // gradient buffers (train), max_batch*T*F*C each
+  float* ew_part = nullptr;                  // partial sums of the elementwise backward kernels
+  float* wg_part = nullptr;                  // split partials of the weight gradient
+  int n_pilot_re = 0;
+  // tensor-core (BF16) path
+  void* X0b = nullptr;                       // assembled input, BF16 [B][T][F][16]
+  void* nxb[2][conet::MAX_BR] = {};          // BF16 conv inputs (ping-pong / H1, H2)
+  void* wb = nullptr;                        // BF16 weights [9][Cout][Cin_pad] per conv
+  std::map<size_t, size_t> wb_off;
+  std::vector<conet::TcMaps> tcmaps;         // tensor maps per conv launch
+  int* d_err = nullptr;                      // device error word of the tensor-core kernels
   float* sim_Y = nullptr;                    // training-step slots
   uint8_t* sim_bits = nullptr;
   float* sim_nv = nullptr;
@@ -67,6 +80,7 @@ struct conet_s {
   double* d_loss = nullptr;
   unsigned long long* d_cnt = nullptr;
   int fwd_B = 0;
+  int chunk = 1;                             // slots per pass (activation buffers hold this many)
   std::vector<void*> allocs;
   bool prof_on = false;                      // CUDA-event timing of launches by kind
   std::vector<cudaEvent_t> prof_ev;          // 2 events per recorded launch

@@ -2,6 +2,7 @@
 // receiver with exact / max-log demapping (Sec. I, Sec. IV baselines), and the fused
 // BCE-loss / bit-error counter over data REs.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -46,9 +47,9 @@ __global__ void assemble_kernel(const float2* __restrict__ Y, const uint8_t* __r
       }
     } else {
       for (int c = 0; c < c_pad; c += 8) {
-        __align__(16) __nv_bfloat16 h[8];
+        __align__(16) Out h[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(v[c + j]);
+        for (int j = 0; j < 8; ++j) h[j] = Out(v[c + j]);
         *reinterpret_cast<uint4*>(o + c) = *reinterpret_cast<uint4*>(h);
       }
     }
@@ -64,13 +65,18 @@ int launch_assemble(const float* Y, const uint8_t* mask, const float* psym, int 
   return check_launch("assemble_kernel");
 }
 
-int launch_assemble_bf16(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
-                         int c_pad, void* X0, cudaStream_t s) {
+int launch_assemble_16(int kind, const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
+                       int c_pad, void* X0, cudaStream_t s) {
   const long long n = (long long)B * T * F;
-  assemble_kernel<__nv_bfloat16><<<grid_for(n, 256), 256, 0, s>>>(
-      reinterpret_cast<const float2*>(Y), mask, reinterpret_cast<const float2*>(psym), B, N, T, F, c_pad,
-      reinterpret_cast<__nv_bfloat16*>(X0));
-  return check_launch("assemble_kernel_bf16");
+  if (kind == 3)
+    assemble_kernel<__half><<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const float2*>(Y), mask,
+                                                             reinterpret_cast<const float2*>(psym), B, N, T, F, c_pad,
+                                                             reinterpret_cast<__half*>(X0));
+  else
+    assemble_kernel<__nv_bfloat16><<<grid_for(n, 256), 256, 0, s>>>(
+        reinterpret_cast<const float2*>(Y), mask, reinterpret_cast<const float2*>(psym), B, N, T, F, c_pad,
+        reinterpret_cast<__nv_bfloat16*>(X0));
+  return check_launch("assemble_kernel_16");
 }
 
 // ------------------------------------------------------------------ LS-LMMSE

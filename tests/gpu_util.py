@@ -25,6 +25,25 @@ def oracle_inputs(net, sim, seed, slot0, B, **kw):
     return s
 
 
+def receptive_radius(net):
+    """Subcarriers on each side that one output RE depends on (one per 3x3 conv)."""
+    return 1 + (2 * net.depth if net.residual else net.depth - 1)
+
+
+def oracle_llr_at(net, params64, Y32_slot, pilot_sym, pilot_mask, f):
+    """Exact oracle LLRs of one slot at subcarrier f (all symbols), computed on the crop
+    f - R .. f + R of the grid: positions farther than R from the crop edge see exactly
+    the receptive field they see in the full grid."""
+    from oracle import pipeline
+    from workloads import replace
+    R = receptive_radius(net)
+    F = Y32_slot.shape[-2]
+    lo, hi = max(0, f - R), min(F, f + R + 1)
+    Yc = Y32_slot[None, :, :, lo:hi, 0].astype(np.float64) + 1j * Y32_slot[None, :, :, lo:hi, 1]
+    L = pipeline.receive(replace(net, n_sc=hi - lo), params64, Yc, pilot_sym[:, lo:hi], pilot_mask[:, lo:hi])
+    return L[0, :, f - lo, :]
+
+
 def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
