@@ -172,6 +172,22 @@ int conet_forward(conet_t h, const float* Y, const uint8_t* pilot_mask, const fl
  */
 int conet_backward(conet_t h, const float* dllr, int B, void* stream);
 
+/*
+ * Weight and bias gradient of one 3x3 'same' convolution layer (zero padding 1 on the
+ * symbol and subcarrier axes, as every CoNet conv of Sec. III), the weight-gradient step of
+ * conet_backward exposed for callers that run their own backward pass:
+ *   dW[co][kh][kw][ci] = sum_{b,t,f} dz[b][t][f][co] x[b][t+kh-1][f+kw-1][ci]   (0 outside)
+ *   db[co]             = sum_{b,t,f} dz[b][t][f][co]
+ *   x  dev float [B][T][F][cin]     layer input, channels last
+ *   dz dev float [B][T][F][cout]    gradient w.r.t. the layer output (pre-activation)
+ *   dW dev float [cout][3][3][cin]  overwritten;  db dev float [cout] or NULL
+ * cin and cout are multiples of 4 in 4..128.  The split partial sums live in scratch that
+ * this call allocates and frees stream-ordered (cudaMallocAsync / cudaFreeAsync on `stream`);
+ * the sum over splits runs in a fixed order, so results are deterministic.
+ */
+int conet_conv3x3_wgrad(const float* x, const float* dz, int B, int T, int F, int cin, int cout, float* dW,
+                        float* db, void* stream);
+
 /* One bias-corrected Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the master
  * parameters with the current gradient; `step` counts from 1. */
 int conet_adam_step(conet_t h, float lr, int step, void* stream);

@@ -197,6 +197,16 @@ def loss_ber(llr, bits, pilot_mask, grad_scale: float = 0.0, want_grad=False, st
     return loss, cnt, dllr
 
 
+def conv3x3_wgrad(x, dz, want_bias=True, stream=None):
+    """(dW [Cout][3][3][Cin], db [Cout]) of one 3x3 'same' conv: x [B,T,F,Cin], dz [B,T,F,Cout]."""
+    B, T, F, cin = x.shape
+    cout = dz.shape[-1]
+    dW = torch.empty((cout, 3, 3, cin), dtype=torch.float32, device=x.device)
+    db = torch.empty(cout, dtype=torch.float32, device=x.device) if want_bias else None
+    check(lib().conet_conv3x3_wgrad(_ptr(x), _ptr(dz), B, T, F, cin, cout, _ptr(dW), _ptr(db), _stream(stream)))
+    return dW, db
+
+
 def launch_count() -> int:
     return int(lib().conet_launch_count())
 

@@ -196,3 +196,22 @@ def test_param_counts_of_named_networks():
     r2 = onet.param_count(WORKLOADS["resnet_14x624_b256_fp32"].net)
     assert abs(n2 - r2) / r2 < 0.02          # matched model size (Sec. III, last paragraph)
     assert onet.param_count(WORKLOADS["plain_14x72_b16_fp32"].net) == 2 * (9 * 5 * 32 + 32 + 3 * (9 * 32 * 32 + 32)) + 32 * 4 + 4
+
+
+@pytest.mark.parametrize("name,kw", [("plain_14x72_b16_fp32", {}), ("resid_14x624_b256_fp32", dict(n_sc=60, depth=2))])
+def test_cropped_receptive_field_is_exact(name, kw):
+    """A depth-L stack of 3x3 convs (LayerNorm and fusion act per RE) sees L subcarriers on
+    each side: the oracle on the crop f-L..f+L reproduces the full-grid LLR at f.  The GPU
+    tests use this to check full-size grids RE by RE."""
+    from gpu_util import oracle_inputs, oracle_llr_at
+    from oracle import pipeline
+    from workloads import WORKLOADS
+    w = WORKLOADS[name]
+    net = replace(w.net, **kw)
+    ref = oracle_inputs(net, w.sim, 1, 0, 1)
+    p = onet.init_params(net, 3)
+    Yd = ref["Y32"][..., 0].astype(np.float64) + 1j * ref["Y32"][..., 1]
+    full = pipeline.receive(net, p, Yd, ref["pilot_sym"], ref["pilot_mask"])
+    for f in (0, 1, net.n_sc // 2, net.n_sc - 1):
+        crop = oracle_llr_at(net, p, ref["Y32"][0], ref["pilot_sym"], ref["pilot_mask"], f)
+        assert np.max(np.abs(crop - full[0, :, f, :])) < 1e-12
