@@ -188,6 +188,23 @@ int conet_backward(conet_t h, const float* dllr, int B, void* stream);
 int conet_conv3x3_wgrad(const float* x, const float* dz, int B, int T, int F, int cin, int cout, float* dW,
                         float* db, void* stream);
 
+/*
+ * The same weight and bias gradient for callers that cannot allocate device memory when
+ * they need it: a real-time receiver or training loop that plans all memory at start-up, code
+ * running inside a CUDA graph capture, or an embedding that only owns its own buffers.  The
+ * paper has no counterpart: this is a deployment variant of the library's own op.
+ * Arguments, layouts and results are those of conet_conv3x3_wgrad; the call allocates and
+ * frees nothing.  Its partial sums live in one array compiled into the library (about
+ * 4.25 MiB, held by every GPU that loads the library until the process exits); a size whose
+ * partials would not fit returns CONET_ERR_SHAPE (never the case for cin, cout <= 128 with
+ * the library's split rule).  The first call on each device, with that device current,
+ * looks up the array's device address once (cudaGetSymbolAddress): make that first call
+ * before any stream capture.  All calls share the array, so calls that overlap on the GPU
+ * (other streams, other host threads) race; serialise them.
+ */
+int conet_conv3x3_wgrad_noalloc(const float* x, const float* dz, int B, int T, int F, int cin, int cout,
+                                float* dW, float* db, void* stream);
+
 /* One bias-corrected Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the master
  * parameters with the current gradient; `step` counts from 1. */
 int conet_adam_step(conet_t h, float lr, int step, void* stream);

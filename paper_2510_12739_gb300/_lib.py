@@ -51,6 +51,7 @@ SIGNATURES = {
     "conet_backward": (I, [P, P, I, P]),
     "conet_adam_step": (I, [P, F32, I, P]),
     "conet_conv3x3_wgrad": (I, [P, P, I, I, I, I, I, P, P, P]),
+    "conet_conv3x3_wgrad_noalloc": (I, [P, P, I, I, I, I, I, P, P, P]),
     "conet_train_step": (I, [P, SIM, U64, U64, I, F32, C.POINTER(C.c_double), P]),
     "conet_pilots": (I, [CFG, P, P, P]),
     "conet_sim_generate": (I, [CFG, SIM, U64, U64, I, F32, P, P, P, P, P, P]),
