@@ -3,6 +3,11 @@
 // N = Cout, K = 9*Cin (tap-major, input channel fastest).  One launch covers every
 // branch of a layer (blockIdx.y).  A CTA owns 128 consecutive REs x all Cout channels, so
 // the epilogue can apply bias, residual add, ReLU and a per-RE LayerNorm in place.
+//
+// Each thread accumulates an 8 x 8 register tile: REs {4r..4r+3, 64+4r..64+4r+3} and
+// channels {4c..4c+3, Cout/2+4c..Cout/2+4c+3}.  Splitting both sets in halves makes every
+// 8-thread shared-memory phase read one contiguous 128-byte row (no bank conflicts) while
+// one k step costs four 128-bit loads for 64 FFMAs.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -11,18 +16,20 @@ namespace conet {
 namespace {
 
 constexpr int TM = 128;   // REs per CTA
-constexpr int RM = 8;     // REs per thread
+constexpr int HM = TM / 2;
 
 template <int CIN, int COUT, int KC>
-__global__ void __launch_bounds__(COUT * 4) conv3x3_fp32_kernel(ConvArgs a) {
-  constexpr int NT = COUT * 4;            // (COUT/4) channel groups x 16 RE groups
-  constexpr int CG = COUT / 4;
+__global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_kernel(ConvArgs a) {
+  constexpr int NT = COUT * 2;            // (COUT/8) channel groups x 16 RE groups
+  constexpr int CG = COUT / 8;
+  constexpr int HC = COUT / 2;
   constexpr int NCH = 9 * (CIN / KC);     // K chunks
   constexpr int A_F4 = TM * KC / 4;
   constexpr int A_PER_T = (A_F4 + NT - 1) / NT;
   constexpr int B_F4 = KC * COUT / 4;
   constexpr int B_PER_T = (B_F4 + NT - 1) / NT;
   constexpr int CS = COUT + 4;            // padded row of the epilogue tile
+  static_assert(COUT % 8 == 0 && CIN % KC == 0 && KC % 4 == 0, "tile shape");
 
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -90,9 +97,11 @@ __global__ void __launch_bounds__(COUT * 4) conv3x3_fp32_kernel(ConvArgs a) {
     }
   };
 
-  float acc[RM][4];
+  float acc[8][8];
 #pragma unroll
-  for (int i = 0; i < RM; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
   load_chunk(0);
   store_chunk(0);
@@ -104,55 +113,59 @@ __global__ void __launch_bounds__(COUT * 4) conv3x3_fp32_kernel(ConvArgs a) {
     const float* Bb = Bs + buf * KC * COUT;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
-      const float4 a0 = *reinterpret_cast<const float4*>(Ab + k * TM + rg * RM);
-      const float4 a1 = *reinterpret_cast<const float4*>(Ab + k * TM + rg * RM + 4);
-      const float4 b = *reinterpret_cast<const float4*>(Bb + k * COUT + cg * 4);
-      const float av[RM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float4 a0 = *reinterpret_cast<const float4*>(Ab + k * TM + rg * 4);
+      const float4 a1 = *reinterpret_cast<const float4*>(Ab + k * TM + HM + rg * 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(Bb + k * COUT + cg * 4);
+      const float4 b1 = *reinterpret_cast<const float4*>(Bb + k * COUT + HC + cg * 4);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int i = 0; i < RM; ++i) {
-        acc[i][0] = fmaf(av[i], b.x, acc[i][0]);
-        acc[i][1] = fmaf(av[i], b.y, acc[i][1]);
-        acc[i][2] = fmaf(av[i], b.z, acc[i][2]);
-        acc[i][3] = fmaf(av[i], b.w, acc[i][3]);
-      }
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     if (c + 1 < NCH) store_chunk(buf ^ 1);
     __syncthreads();
   }
 
   // ---------------------------------------------------------------- epilogue
-  const float4 bv = a.bias[br] ? __ldg(reinterpret_cast<const float4*>(a.bias[br]) + cg)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* __restrict__ bias = a.bias[br];
   const float* __restrict__ resid = a.resid[br];
   float* __restrict__ out0 = a.out0[br];
   const bool ln = a.ln_g[br] != nullptr;
   float* Cs = smem;   // [TM][CS], reuses the mainloop buffers (all reads done)
 #pragma unroll
-  for (int i = 0; i < RM; ++i) {
-    const int re = rg * RM + i;
-    const long long m = m0 + re;
-    if (m >= a.M) continue;
-    float4 v = make_float4(acc[i][0] + bv.x, acc[i][1] + bv.y, acc[i][2] + bv.z, acc[i][3] + bv.w);
-    if (resid) {
-      const float4 r = __ldg(reinterpret_cast<const float4*>(resid + m * COUT) + cg);
-      v.x += r.x;
-      v.y += r.y;
-      v.z += r.z;
-      v.w += r.w;
+  for (int h = 0; h < 2; ++h) {
+    const int c0 = h * HC + cg * 4;
+    const float4 bv = bias ? __ldg(reinterpret_cast<const float4*>(bias + c0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int re = (i < 4 ? 0 : HM) + rg * 4 + (i & 3);
+      const long long m = m0 + re;
+      if (m >= a.M) continue;
+      float4 v = make_float4(acc[i][4 * h] + bv.x, acc[i][4 * h + 1] + bv.y, acc[i][4 * h + 2] + bv.z,
+                             acc[i][4 * h + 3] + bv.w);
+      if (resid) {
+        const float4 r = __ldg(reinterpret_cast<const float4*>(resid + m * COUT + c0));
+        v.x += r.x;
+        v.y += r.y;
+        v.z += r.z;
+        v.w += r.w;
+      }
+      if (out0) {
+        float4 o = v;
+        if (a.relu0) o = make_float4(fmaxf(o.x, 0.f), fmaxf(o.y, 0.f), fmaxf(o.z, 0.f), fmaxf(o.w, 0.f));
+        *reinterpret_cast<float4*>(out0 + m * COUT + c0) = o;
+      }
+      if (ln) *reinterpret_cast<float4*>(Cs + re * CS + c0) = v;
     }
-    if (out0) {
-      float4 o = v;
-      if (a.relu0) o = make_float4(fmaxf(o.x, 0.f), fmaxf(o.y, 0.f), fmaxf(o.z, 0.f), fmaxf(o.w, 0.f));
-      reinterpret_cast<float4*>(out0 + m * COUT)[cg] = o;
-    }
-    if (ln) *reinterpret_cast<float4*>(Cs + re * CS + cg * 4) = v;
   }
   if (!ln) return;
   __syncthreads();
   const float* __restrict__ g = a.ln_g[br];
   const float* __restrict__ be = a.ln_b[br];
   float* __restrict__ out1 = a.out1[br];
-  constexpr int NW = NT / 32;
+  constexpr int NW = NT / 32 > 0 ? NT / 32 : 1;
   constexpr int CPL = (COUT + 31) / 32;
   const int lane = tid & 31, warp = tid >> 5;
   for (int re = warp; re < TM; re += NW) {
@@ -195,7 +208,7 @@ int launch_t(const ConvArgs& a, int n_br, cudaStream_t s) {
     attr = true;
   }
   dim3 grid((unsigned)((a.M + TM - 1) / TM), n_br);
-  conv3x3_fp32_kernel<CIN, COUT, KC><<<grid, COUT * 4, smem, s>>>(a);
+  conv3x3_fp32_kernel<CIN, COUT, KC><<<grid, COUT * 2, smem, s>>>(a);
   return check_launch("conv3x3_fp32_kernel");
 }
 

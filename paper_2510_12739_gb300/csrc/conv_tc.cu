@@ -28,9 +28,16 @@ namespace conet {
 namespace {
 
 constexpr int TILE_M = 128;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_PARTS = 2;                      // epilogue warps per TMEM lane quarter
+constexpr int EPI_WARPS = 4 * EPI_PARTS;
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr size_t SMEM_LIMIT = 227 * 1024;
+constexpr int HEAD_QMAX = 8;
+
+// Shared memory the epilogue parts use to merge LayerNorm moments and head partial sums.
+__host__ __device__ constexpr size_t xch_floats(int nb) {
+  return (size_t)4 * EPI_PARTS * 32 * (nb + 1) * 2 + (size_t)4 * 32 * HEAD_QMAX;
+}
 
 __host__ __device__ constexpr int pow2_ceil(int x) {
   int p = 32;
@@ -52,9 +59,10 @@ struct Cfg {
   static constexpr int COLS = pow2_ceil(NB * COUT);
   static constexpr int N_ACC = 2 * COLS <= 512 ? 2 : 1;
   static constexpr int TMEM_COLS = N_ACC * COLS;
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256) / STAGE);
+  static constexpr size_t XCH = xch_floats(NB) * sizeof(float);
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - XCH) / STAGE);
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + XCH;
   static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT);   // BF16 / TF32 / F16, E4M3
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
   static_assert(COUT % 16 == 0 && COUT <= 256, "MMA N");
@@ -62,7 +70,8 @@ struct Cfg {
   static_assert(CIN % KC == 0, "K chunking");
 };
 
-// Shifted first and second moments of one channel vector (shift = its first element).
+// Shifted first and second moments of part of a channel vector (shift = the part's first
+// element), reduced to (mean, M2) and merged across parts by Chan et al.'s pairwise rule.
 struct Moments {
   float k = 0.f, s1 = 0.f, s2 = 0.f;
   __device__ __forceinline__ void add(float x, bool first) {
@@ -71,20 +80,60 @@ struct Moments {
     s1 += d;
     s2 += d * d;
   }
-  __device__ __forceinline__ void finish(int C, float& mean, float& rstd) const {
-    const float m1 = s1 / (float)C;
+  __device__ __forceinline__ void partial(int n, float& mean, float& m2) const {
+    if (n == 0) {
+      mean = 0.f;
+      m2 = 0.f;
+      return;
+    }
+    const float m1 = s1 / (float)n;
     mean = k + m1;
-    rstd = rsqrtf(fmaxf(s2 / (float)C - m1 * m1, 0.f) + 1e-5f);
+    m2 = fmaxf(s2 - s1 * m1, 0.f);
   }
 };
 
-// v_b = acc_b + bias_b (+ resid_b) for the 16 channels of chunk j of every branch.
+// (na, ma, Ma) + (nb, mb, Mb) -> mean and 1/sqrt(var + eps) of the union (n = na + nb).
+__device__ __forceinline__ void merge_moments(int na, float ma, float Ma, int nb, float mb, float Mb, float& mean,
+                                             float& rstd) {
+  const float n = (float)(na + nb);
+  const float d = mb - ma;
+  mean = ma + d * ((float)nb / n);
+  const float m2 = Ma + Mb + d * d * ((float)na * (float)nb / n);
+  rstd = rsqrtf(m2 / n + 1e-5f);
+}
+
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Barrier over `threads` threads that also returns whether `ok` held in all of them, so the
+// warps of an epilogue pair always take the same branch (a lone warp would otherwise wait at
+// the next named barrier for a partner that already left).
+__device__ __forceinline__ bool barrier_all(int id, int threads, bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)ok), "r"(id), "r"(threads)
+      : "memory");
+  return r != 0;
+}
+
+// v_b = acc_b + bias_b (+ resid_b) for the 16 channels of chunk j of every branch
+// (add = false: the raw TMEM columns, when an earlier pass already wrote v back).
 template <int NB, int COUT>
 __device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, int j, bool valid, long long m,
-                                           float (&v)[NB][16]) {
+                                           float (&v)[NB][16], bool add = true) {
+  uint32_t r[NB][16];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) tc::tmem_ld16(tacc + (uint32_t)(b * COUT + 16 * j), v[b]);
-  if (!valid) return;
+  for (int b = 0; b < NB; ++b) tc::tmem_ld16_nowait(tacc + (uint32_t)(b * COUT + 16 * j), r[b]);
+  tc::tmem_wait_ld();
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[b][c] = __uint_as_float(r[b][c]);
+  if (!valid || !add) return;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const float4* bp = reinterpret_cast<const float4*>(a.bias[b] + 16 * j);
@@ -134,12 +183,19 @@ __device__ __forceinline__ void store16_bf16(__nv_bfloat16* p, const float (&x)[
   q[1] = reinterpret_cast<const uint4*>(h)[1];
 }
 
-// The fused epilogue for one RE (this thread's TMEM lane): two passes over the
-// accumulator columns -- statistics of every LayerNorm it applies, then the outputs.
+// The fused epilogue for one RE (this thread's TMEM lane) and one part of its channels:
+// two passes over the part's accumulator columns -- statistics of every LayerNorm it
+// applies (merged with the other part through shared memory), then the outputs; the head's
+// partial sums are merged the same way and written by part 0.
 template <int KIND, int NB, int COUT>
-__device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, bool valid, long long m) {
+__device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, bool valid, long long m, int part,
+                                            int quarter, int lane, float* xstat, float* xhead) {
   constexpr int CH = COUT / 16;
-  constexpr int QMAX = 8;
+  constexpr int CHP = (CH + EPI_PARTS - 1) / EPI_PARTS;   // chunks of the first part
+  constexpr int QMAX = HEAD_QMAX;
+  const int j_lo = part == 0 ? 0 : CHP;
+  const int j_hi = part == 0 ? CHP : CH;
+  const int n_part = 16 * (j_hi - j_lo);
   const bool pre_ln = a.pre == 2;
   const bool fuse_ln = a.fuse && a.lnf_g != nullptr;
   bool need_ln1[NB];
@@ -149,15 +205,26 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
     need_ln1[b] = a.post[b] == 2;
     any_ln1 = any_ln1 || need_ln1[b];
   }
+  bool has_resid = false;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) has_resid = has_resid || a.resid[b] != nullptr;
   Moments mb[NB], mp;
-  if (pre_ln || fuse_ln || any_ln1) {
-    for (int j = 0; j < CH; ++j) {
+  // With a statistics pass and a residual input, the statistics pass writes v (bias and
+  // residual added) back into TMEM so that the output pass reads no global memory again.
+  const bool stats = pre_ln || fuse_ln || any_ln1;
+  const bool write_back = stats && has_resid;
+  if (stats) {
+    for (int j = j_lo; j < j_hi; ++j) {
       float v[NB][16];
       __syncwarp();
       load_chunk<NB, COUT>(a, tacc, j, valid, m, v);
+      if (write_back) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) tc::tmem_st16(tacc + (uint32_t)(b * COUT + 16 * j), v[b]);
+      }
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        const bool first = (j == 0 && c == 0);
+        const bool first = (j == j_lo && c == 0);
         float p = 1.f;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -171,18 +238,42 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
       }
     }
   }
+  // merge the parts' moments (the barrier runs every tile, statistics or not, so that the
+  // head exchange below never overtakes a reader of the previous tile)
   float mean_b[NB], rstd_b[NB], mean_p = 0.f, rstd_p = 1.f;
+  {
+    float* mine = xstat + (((size_t)(quarter * EPI_PARTS + part) * 32 + lane) * (NB + 1)) * 2;
+    float* other = xstat + (((size_t)(quarter * EPI_PARTS + (part ^ 1)) * 32 + lane) * (NB + 1)) * 2;
+    if (stats) {
 #pragma unroll
-  for (int b = 0; b < NB; ++b) mb[b].finish(COUT, mean_b[b], rstd_b[b]);
-  if (fuse_ln) mp.finish(COUT, mean_p, rstd_p);
+      for (int b = 0; b < NB; ++b) mb[b].partial(n_part, mine[2 * b], mine[2 * b + 1]);
+      mp.partial(n_part, mine[2 * NB], mine[2 * NB + 1]);
+    }
+    named_barrier(1 + quarter, 32 * EPI_PARTS);
+    if (stats) {
+      const int n_other = COUT - n_part;
+#pragma unroll
+      for (int b = 0; b <= NB; ++b) {
+        float mm, rr;
+        merge_moments(n_part, mine[2 * b], mine[2 * b + 1], n_other, other[2 * b], other[2 * b + 1], mm, rr);
+        if (b < NB) {
+          mean_b[b] = mm;
+          rstd_b[b] = rr;
+        } else {
+          mean_p = mm;
+          rstd_p = rr;
+        }
+      }
+    }
+  }
 
   float hq[QMAX];
 #pragma unroll
   for (int qq = 0; qq < QMAX; ++qq) hq[qq] = 0.f;
-  for (int j = 0; j < CH; ++j) {
+  for (int j = j_lo; j < j_hi; ++j) {
     float v[NB][16];
     __syncwarp();
-    load_chunk<NB, COUT>(a, tacc, j, valid, m, v);
+    load_chunk<NB, COUT>(a, tacc, j, valid, m, v, !write_back);
     const int c0 = 16 * j;
     // rows past the grid edge compute on don't-care values and store nothing
 #pragma unroll
@@ -241,8 +332,16 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
       }
     }
   }
-  if (a.head_w && valid) {
-    for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) a.llr[m * a.Q + qq] = hq[qq] + __ldg(a.head_b + qq);
+  if (a.head_w) {
+    float* slot = xhead + ((size_t)quarter * 32 + lane) * QMAX;
+    if (part == 1) {
+#pragma unroll
+      for (int qq = 0; qq < QMAX; ++qq) slot[qq] = hq[qq];
+    }
+    named_barrier(1 + 4 + quarter, 32 * EPI_PARTS);
+    if (part == 0 && valid) {
+      for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) a.llr[m * a.Q + qq] = hq[qq] + slot[qq] + __ldg(a.head_b + qq);
+    }
   }
 }
 
@@ -263,6 +362,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   uint64_t* tfull = empty + K::STAGES;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  float* xstat = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256);
+  float* xhead = xstat + (size_t)4 * EPI_PARTS * 32 * (NB + 1) * 2;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -366,12 +467,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   } else if (warp >= 2) {
     // ------------------------------------------------------------ fused epilogue
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int part = (warp - 2) / 4;        // which share of the channels this warp handles
     const int row = 32 * q + lane;
     int it = 0;
     for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
-      if (!tc::mbar_wait(&tfull[acc], aph, err, 4)) break;
+      const bool got = tc::mbar_wait(&tfull[acc], aph, err, 4);
+      if (!barrier_all(1 + q, 32 * EPI_PARTS, got)) break;
       tc::fence_after_sync();
       int slot, t, fb;
       decode_tile(tile, a.T, a.nfb, slot, t, fb);
@@ -379,7 +482,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       const bool valid = f < a.F;
       const long long m = ((long long)slot * a.T + t) * a.F + f;
       const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + ((uint32_t)(32 * q) << 16);
-      tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m);
+      tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m, part, q, lane, xstat, xhead);
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[acc]);
@@ -420,11 +523,11 @@ int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, cons
   TC_CASE(0, 2, 16, 32, 16)
   TC_CASE(0, 2, 32, 32, 32)
   TC_CASE(0, 3, 16, 64, 16)
-  TC_CASE(0, 3, 64, 64, 32)
+  TC_CASE(0, 3, 64, 64, 64)
   TC_CASE(0, 4, 16, 96, 16)
   TC_CASE(0, 4, 96, 96, 32)
   TC_CASE(0, 1, 16, 64, 16)
-  TC_CASE(0, 1, 64, 64, 32)
+  TC_CASE(0, 1, 64, 64, 64)
   TC_CASE(0, 3, 16, 16, 16)
   TC_CASE(0, 3, 16, 32, 16)
   TC_CASE(0, 3, 32, 32, 32)
@@ -432,7 +535,7 @@ int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, cons
   TC_CASE(3, 2, 16, 32, 16)
   TC_CASE(3, 2, 32, 32, 32)
   TC_CASE(3, 3, 16, 64, 16)
-  TC_CASE(3, 3, 64, 64, 32)
+  TC_CASE(3, 3, 64, 64, 64)
   TC_CASE(3, 4, 16, 96, 16)
   TC_CASE(3, 4, 96, 96, 32)
   TC_CASE(3, 3, 16, 32, 16)
@@ -500,9 +603,12 @@ int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int c
   return CONET_OK;
 }
 
+// Channels per K chunk (one TMA box row): 128-byte rows where the width allows it, so each
+// box moves the fewest, longest rows.
 int tc_chunk(int kind, int cin) {
   (void)kind;
-  return cin <= 16 ? 16 : 32;
+  if (cin <= 16) return 16;
+  return cin % 64 == 0 ? 64 : 32;
 }
 
 // [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] BF16, zero padded input channels
