@@ -5,8 +5,12 @@ One step = one pass of the inference hot path over one batch of synthetic slots 
 resident in HBM: input assembly -> every CoNet branch with Hadamard fusion -> 1x1 LLR
 head -> BCE loss and bit-error counters against the transmitted bits.  The slots come
 from the library's own device-side link simulator before the timed region.  The
-default workload is the 2-Rx, 14 x 624 subcarrier, 64-QAM slot batch (B = 256) through
+headline workload is the 2-Rx, 14 x 624 subcarrier, 64-QAM slot batch (B = 256) through
 the 3-branch x (input + 6 RB/MRB) x 64-channel residual CoNet in FP32.
+
+The same line carries, under "variants", the other precisions of that workload, the
+4-Rx 14 x 3276 BF16 / FP16 workload, the matched single-branch ResNet, and training
+throughput (simulate -> forward -> BCE -> backward -> Adam per step).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (a bounded sample of the same workload per step).
@@ -14,6 +18,9 @@ host cores instead (a bounded sample of the same workload per step).
 from __future__ import annotations
 
 import argparse
+import ctypes as C
+import dataclasses
+import hashlib
 import json
 import os
 import statistics
@@ -21,8 +28,6 @@ import subprocess
 import sys
 import threading
 import time
-
-import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -33,6 +38,9 @@ from workloads import WORKLOADS  # noqa: E402
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP32_LANES_PER_SM = 128             # FFMA lanes per SM (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
+METRIC = "conet_infer_slots_per_s"
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+NOMINAL_FP8_OVER_BF16 = 4.5 / 2.25
 
 
 def parse():
@@ -44,21 +52,26 @@ def parse():
     p.add_argument("--workload", default="resid_14x624_b256_fp32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    p.add_argument("--no-variants", action="store_true", help="headline workload only")
     p.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling runs)")
-    p.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default=None,
+    p.add_argument("--precision", choices=["fp32", "bf16", "fp16", "tf32x3", "fp8"], default=None,
                    help="override the workload's conv precision")
     return p.parse_args()
 
 
 def conv_flops(net, B):
-    """Algorithmic FLOPs (2 x MACs) of one body 3x3 conv launch (all branches)."""
-    M = B * net.n_sym * net.n_sc
-    return 2.0 * M * 9 * net.width * net.width * net.n_branches
+    """Algorithmic FLOPs (2 x MACs) of one body 3x3 conv layer over B slots (all branches)."""
+    return 2.0 * B * net.n_sym * net.n_sc * 9 * net.width * net.width * net.n_branches
 
 
 def n_body_convs(net):
     """Body (C -> C) 3x3 conv layers per branch."""
     return 2 * net.depth if net.residual else net.depth - 1
+
+
+def net_flops_per_re(net):
+    C, nb = net.width, net.n_branches
+    return 2 * 9 * net.c_in * C * nb + n_body_convs(net) * 2 * 9 * C * C * nb + 2 * C * net.qam_bits
 
 
 def tensor_peak():
@@ -70,14 +83,6 @@ def tensor_peak():
         return float(mp["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
     except (OSError, ValueError, KeyError):
         return 1700.0, "fallback sustained BF16 1.7 PFLOP/s (of fallback)"
-
-
-def net_flops_per_re(net):
-    C, nb = net.width, net.n_branches
-    f = 2 * 9 * net.c_in * C * nb
-    body = (2 * net.depth) if net.residual else (net.depth - 1)
-    f += body * 2 * 9 * C * C * nb
-    return f + 2 * C * net.qam_bits
 
 
 class ClockSampler:
@@ -168,7 +173,7 @@ def reference_arm(args, rank, world):
     dt = time.perf_counter() - t0
     v = args.steps / dt
     cores = os.cpu_count()
-    line = {"metric": "conet_infer_slots_per_s", "value": v, "unit": "slots/s", "impl": "reference",
+    line = {"metric": METRIC, "value": v, "unit": "slots/s", "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "batch_per_step": 1, "note": "one slot of the workload per step"},
@@ -177,6 +182,165 @@ def reference_arm(args, rank, world):
             "e2e": {"value": v, "unit": "slots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+class Ctx:
+    def __init__(self, rank, world, local, dist):
+        import torch
+        self.torch = torch
+        self.rank, self.world, self.local, self.dist = rank, world, local, dist
+        self.stream = torch.cuda.current_stream()
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, v):
+        if self.dist is None:
+            return v
+        t = self.torch.tensor([v], device="cuda")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(self, fn, steps):
+        """Per-step CUDA-event times on the launch stream, L2 flushed between steps."""
+        torch = self.torch
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            self.flush.zero_()
+            evs[i][0].record(self.stream)
+            fn()
+            evs[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+
+def roofline_of(w, net, B, rx, steps, n_sm):
+    from paper_2510_12739_gb300 import api
+    conv_ms, conv_n = rx.profile_read(api.PROFILE_KINDS["conv"])
+    avg_s = (conv_ms / max(conv_n, 1)) / 1e3
+    per_step = conv_n / max(1, steps)
+    flops_per_launch = conv_flops(net, B) * n_body_convs(net) / max(1e-9, per_step)
+    achieved = flops_per_launch / avg_s / 1e12 if conv_n else None
+    if w.precision == "fp32":
+        peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        bound, src = "alu", f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {SM_MAX_MHZ:.0f} MHz"
+        kname = f"conv3x3_fp32_kernel<{net.width},{net.width},8> (body 3x3 conv, {net.n_branches} branches per launch)"
+    else:
+        peak, src = tensor_peak()
+        bound = "tensor"
+        if w.precision == "tf32x3":
+            # TF32 runs at the nominal 1.1 / 2.25 of the BF16 rate and issues 3 MMAs per product
+            peak = peak * NOMINAL_TF32_OVER_BF16 / 3.0
+            src += " x 1.1/2.25 (nominal TF32/BF16) / 3 MMAs per useful product (split TF32)"
+        elif w.precision == "fp8":
+            peak = peak * NOMINAL_FP8_OVER_BF16
+            src += " x 4.5/2.25 (nominal FP8/BF16 dense)"
+        kname = (f"conv_tc_kernel<{w.precision},{net.n_branches},{net.width},{net.width}> "
+                 f"(tcgen05 body 3x3 conv, {net.n_branches} branches per launch)")
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic_per_launch(w, net, B, per_step),
+            "kernel": kname, "peak_source": src, "launches": conv_n, "avg_launch_ms": avg_s * 1e3}
+
+
+def measure_inference(ctx, w, B, steps, warmup, clocks=False, e2e=False):
+    """Device-resident inference throughput (and optionally host-buffer end to end)."""
+    torch = ctx.torch
+    from paper_2510_12739_gb300 import api
+    from paper_2510_12739_gb300._lib import check, lib
+    net = w.net
+    T, F, Q = net.n_sym, net.n_sc, net.qam_bits
+    rx = api.Receiver(net, precision=w.precision, max_batch=B)
+    rx.init_he(0)
+    mask, _ = api.pilots(net)
+    s = api.sim_generate(net, w.sim, 1, ctx.rank * 1_000_000, B)     # each rank its own slots
+    Y, bits, nv = s["Y"], s["bits"], s["noise_var"]
+    llr = torch.empty((B, T, F, Q), device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    stream = ctx.stream
+
+    def count(l):
+        check(lib().conet_loss_ber(C.c_void_p(l.data_ptr()), C.c_void_p(bits.data_ptr()),
+                                   C.c_void_p(mask.data_ptr()), B, T, F, Q, 0.0, None,
+                                   C.c_void_p(loss.data_ptr()), C.c_void_p(cnt.data_ptr()),
+                                   C.c_void_p(cnt.data_ptr() + 8), C.c_void_p(stream.cuda_stream)))
+
+    def step():
+        rx.forward(Y, mask, nv, llr)
+        count(llr)
+
+    for _ in range(warmup):
+        step()
+    rx.sync()
+    ctx.barrier()
+    sampler = ClockSampler(ctx.local) if clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    rx.profile_enable(True)
+    n0 = api.launch_count()
+    times = ctx.timed(step, steps)
+    n_launch = api.launch_count() - n0
+    ctx.barrier()
+    clk = sampler.stop() if sampler else None
+    ms = ctx.max_over_ranks(statistics.mean(times))
+    n_sm = torch.cuda.get_device_properties(ctx.local).multi_processor_count
+    roof = roofline_of(w, net, B, rx, steps, n_sm)
+    rx.profile_enable(False)
+    rx.sync()
+    out = {"value": B * ctx.world / (ms / 1e3), "ms_per_step": ms, "roofline": roof, "gpu_launches": n_launch,
+           "clocks": clk, "step_ms": {"min": min(times), "max": max(times)}}
+    if e2e:
+        Y_h = Y.cpu().pin_memory()
+        nv_h = nv.cpu().pin_memory()
+        llr_h = torch.empty(llr.shape, dtype=llr.dtype, pin_memory=True)
+        cnt_h = torch.empty(2, dtype=torch.int64, pin_memory=True)
+        Yd, nvd = torch.empty_like(Y), torch.empty_like(nv)
+
+        def e2e_step():
+            Yd.copy_(Y_h, non_blocking=True)
+            nvd.copy_(nv_h, non_blocking=True)
+            rx.forward(Yd, mask, nvd, llr)
+            count(llr)
+            llr_h.copy_(llr, non_blocking=True)
+            cnt_h.copy_(cnt, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ctx.barrier()
+        ms_e2e = ctx.max_over_ranks(statistics.mean(ctx.timed(e2e_step, steps)))
+        out["e2e"] = {"value": B * ctx.world / (ms_e2e / 1e3), "unit": "slots/s",
+                      "h2d_bytes_per_step": int(Y.nbytes + nv.nbytes),
+                      "d2h_bytes_per_step": int(llr.nbytes + cnt.nbytes)}
+    rx.close()
+    return out
+
+
+def measure_training(ctx, w, steps, warmup):
+    """Train slots/s: each step simulates B slots on the device, runs forward, BCE,
+    backward and Adam (conet_train_step)."""
+    from paper_2510_12739_gb300 import api
+    B = w.batch
+    rx = api.Receiver(w.net, precision=w.precision, max_batch=B, train=True)
+    rx.init_he(1)
+    it = [0]
+
+    def step():
+        rx.train_step(w.sim, 7, ctx.rank * 1_000_000 + it[0], B, 1e-3, want_loss=False)
+        it[0] += 1
+
+    for _ in range(warmup):
+        step()
+    rx.sync()
+    times = ctx.timed(step, steps)
+    loss = rx.train_step(w.sim, 7, ctx.rank * 1_000_000 + it[0], B, 1e-3, want_loss=True)
+    ms = ctx.max_over_ranks(statistics.mean(times))
+    rx.close()
+    return {"value": B * ctx.world / (ms / 1e3), "unit": "train slots/s", "ms_per_step": ms,
+            "precision": w.precision, "loss_after": loss}
 
 
 def main():
@@ -193,139 +357,33 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2510_12739_gb300 import api
+    from paper_2510_12739_gb300 import api  # noqa: F401  (fails loudly without libconet)
+    ctx = Ctx(rank, world, local, dist)
 
     w = WORKLOADS[args.workload]
     if args.precision:
-        import dataclasses
         w = dataclasses.replace(w, precision=args.precision)
-    net, B = w.net, (args.batch or w.batch)
-    T, F, Q = net.n_sym, net.n_sc, net.qam_bits
-    rx = api.Receiver(net, precision=w.precision, max_batch=B)
-    rx.init_he(0)
-    mask, psym = api.pilots(net)
-    s = api.sim_generate(net, w.sim, 1, rank * 1_000_000, B)     # each rank its own slots
-    Y, bits, nv = s["Y"], s["bits"], s["noise_var"]
-    llr = torch.empty((B, T, F, Q), device="cuda")
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    from paper_2510_12739_gb300._lib import check, lib
-    import ctypes as C
+    B = args.batch or w.batch
+    head = measure_inference(ctx, w, B, args.steps, args.warmup, clocks=True, e2e=not args.no_e2e)
 
-    def count(l):
-        check(lib().conet_loss_ber(C.c_void_p(l.data_ptr()), C.c_void_p(bits.data_ptr()),
-                                   C.c_void_p(mask.data_ptr()), B, T, F, Q, 0.0, None,
-                                   C.c_void_p(loss.data_ptr()), C.c_void_p(cnt.data_ptr()),
-                                   C.c_void_p(cnt.data_ptr() + 8), C.c_void_p(stream.cuda_stream)))
-
-    def step():
-        rx.forward(Y, mask, nv, llr)
-        count(llr)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    # ---------------------------------------------------------------- device-resident timing
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    rx.profile_enable(True)
-    n0 = api.launch_count()
-    for i in range(args.steps):
-        flush.zero_()                                   # evict L2 between steps
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    n_launch = api.launch_count() - n0
-    barrier()
-    clk = clocks.stop()
-    times = [a.elapsed_time(b) for a, b in evs]
-    ms = statistics.mean(times)
-    conv_ms, conv_n = rx.profile_read(api.PROFILE_KINDS["conv"])
-    rx.profile_enable(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    # ---------------------------------------------------------------- end to end (host buffers)
-    e2e = None
-    if not args.no_e2e:
-        e2e = end_to_end(args, rx, count, Y, nv, mask, llr, cnt, flush, stream, B, world, dist, barrier)
-    return finish(args, rank, world, local, w, net, B, T, F, Q, ms, times, conv_ms, conv_n, clk, n_launch, e2e, dist)
-
-
-def end_to_end(args, rx, count, Y, nv, mask, llr, cnt, flush, stream, B, world, dist, barrier):
-    import torch
-    Y_h = Y.cpu().pin_memory()
-    nv_h = nv.cpu().pin_memory()
-    llr_h = torch.empty(llr.shape, dtype=llr.dtype, pin_memory=True)
-    cnt_h = torch.empty(2, dtype=torch.int64, pin_memory=True)
-    Yd, nvd = torch.empty_like(Y), torch.empty_like(nv)
-
-    def e2e_step():
-        Yd.copy_(Y_h, non_blocking=True)
-        nvd.copy_(nv_h, non_blocking=True)
-        rx.forward(Yd, mask, nvd, llr)
-        count(llr)
-        llr_h.copy_(llr, non_blocking=True)
-        cnt_h.copy_(cnt, non_blocking=True)
-
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    for i in range(args.steps):
-        flush.zero_()
-        ev2[i][0].record(stream)
-        e2e_step()
-        ev2[i][1].record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = statistics.mean(a.elapsed_time(b) for a, b in ev2)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    return {"value": B * world / (ms_e2e / 1e3), "unit": "slots/s",
-            "h2d_bytes_per_step": int(Y.nbytes + nv.nbytes),
-            "d2h_bytes_per_step": int(llr.nbytes + cnt.nbytes)}
-
-
-def finish(args, rank, world, local, w, net, B, T, F, Q, ms, times, conv_ms, conv_n, clk, n_launch, e2e, dist):
-    import torch
-    value = B * world / (ms / 1e3)
-    # ---------------------------------------------------------------- roofline of the body conv
-    props = torch.cuda.get_device_properties(local)
-    n_sm = props.multi_processor_count
-    avg_conv_s = (conv_ms / max(conv_n, 1)) / 1e3
-    # one launch per body layer and batch chunk: spread the step's body-conv FLOPs over them
-    launches_per_step = conv_n / max(1, args.steps)
-    flops_per_launch = conv_flops(net, B) * n_body_convs(net) / max(1e-9, launches_per_step)
-    achieved = flops_per_launch / avg_conv_s / 1e12 if conv_n else None
-    if w.precision == "fp32":
-        peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        bound, src = "alu", f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {SM_MAX_MHZ:.0f} MHz"
-        kname = f"conv3x3_fp32_kernel<{net.width},{net.width},8> (body 3x3 conv, {net.n_branches} branches per launch)"
-    else:
-        peak, src = tensor_peak()
-        bound = "tensor"
-        kname = (f"conv_tc_kernel<{w.precision},{net.n_branches},{net.width},{net.width}> "
-                 f"(tcgen05 body 3x3 conv, {net.n_branches} branches per launch)")
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic_per_launch(net, B),
-                "kernel": kname, "peak_source": src, "launches": conv_n, "avg_launch_ms": avg_conv_s * 1e3}
+    variants = {}
+    if not args.no_variants and not args.batch:
+        for name, prec, steps in [("resid_14x624_b256_fp32", "tf32x3", 10), ("resid_14x624_b256_fp32", "bf16", 10),
+                                  ("resid_14x624_b256_fp32", "fp16", 10), ("resnet_14x624_b256_fp32", "fp32", 5),
+                                  ("resid_14x624_b256_fp32", "fp8", 10),
+                                  ("resid_14x3276_b1024_bf16", "bf16", 3), ("resid_14x3276_b1024_bf16", "fp16", 3),
+                                  ("resid_14x3276_b1024_bf16", "fp8", 3),
+                                  ("interf_14x72_b512_fp8", "fp8", 20), ("interf_14x72_b512_fp8", "bf16", 20),
+                                  ("interf_14x72_b512_fp8", "fp32", 20),
+                                  ("plain_14x72_b16_fp32", "fp32", 20), ("plain_14x72_b16_fp32", "bf16", 20)]:
+            vw = dataclasses.replace(WORKLOADS[name], precision=prec)
+            r = measure_inference(ctx, vw, vw.batch, steps, 2)
+            variants[f"{name}:{prec}"] = {"value": r["value"], "unit": "slots/s", "ms_per_step": r["ms_per_step"],
+                                          "conv_tflops": r["roofline"]["achieved"],
+                                          "roofline_frac": r["roofline"]["frac"], "bound": r["roofline"]["bound"]}
+        for prec in ("bf16", "fp32"):
+            tw = dataclasses.replace(WORKLOADS["train_14x72_b128_bf16"], precision=prec)
+            variants[f"train_14x72_b128:{prec}"] = measure_training(ctx, tw, 20, 3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -334,42 +392,47 @@ def finish(args, rank, world, local, w, net, B, T, F, Q, ms, times, conv_ms, con
                "sample": f"{n} slots of {w.name} (FP64 numpy oracle, receive + BER), {secs:.1f} s"}
 
     if rank == 0:
-        line = {"metric": "conet_infer_slots_per_s", "value": value, "unit": "slots/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[w.precision],
+        net = w.net
+        line = {"metric": METRIC, "value": head["value"], "unit": "slots/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "tf32x3": "f32 (tf32x3 split)",
+                          "fp8": "e4m3"}[w.precision],
                 "data": "synthetic",
                 "config": {"workload": w.name, "global_batch": B * world, "batch_per_gpu": B, "n_rx": net.n_rx,
-                           "grid": f"{T}x{F}", "qam_bits": Q, "branches": net.n_branches, "blocks": net.depth,
-                           "width": net.width, "flop_per_slot": net_flops_per_re(net) * T * F,
+                           "grid": f"{net.n_sym}x{net.n_sc}", "qam_bits": net.qam_bits,
+                           "branches": net.n_branches, "blocks": net.depth, "width": net.width,
+                           "flop_per_slot": net_flops_per_re(net) * net.n_sym * net.n_sc,
                            "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-                "clocks": clk, "step_ms": {"min": min(times), "max": max(times)}}
+                "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head.get("e2e"),
+                "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "step_ms": head["step_ms"],
+                "variants": variants}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
 
-def traffic_per_launch(net, B):
-    """DRAM bytes per body-conv launch from the committed ncu summary, when it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def traffic_per_launch(w, net, B, launches_per_step):
+    """DRAM bytes per body-conv launch from the committed ncu summary, scaled to this
+    launch's REs, when it was taken on the current kernel source (else None)."""
     try:
-        with open(path) as f:
-            rec = json.load(f)
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            recs = json.load(f)
     except (OSError, ValueError):
         return None
-    import hashlib
-    src = os.path.join(ROOT, "paper_2510_12739_gb300", "csrc", rec.get("source", ""))
+    rec = recs.get(w.precision)
+    if not rec or rec.get("workload") != w.name:
+        return None
+    src = os.path.join(ROOT, "paper_2510_12739_gb300", "csrc", rec["source"])
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
     if digest != rec.get("sha256"):
         return None
-    per_re = rec["bytes_per_launch"] / rec["res_per_launch"]
-    return per_re * B * net.n_sym * net.n_sc
+    res_per_launch = B * net.n_sym * net.n_sc * n_body_convs(net) / max(1e-9, launches_per_step)
+    return rec["bytes_per_launch"] / rec["res_per_launch"] * res_per_launch
 
 
 if __name__ == "__main__":

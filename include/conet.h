@@ -50,8 +50,12 @@ typedef enum {
 typedef enum {
   CONET_FP32 = 0,              /* FP32 storage, FP32 FFMA convolutions */
   CONET_BF16 = 1,              /* BF16 activations / weights, FP32 accumulate (tcgen05) */
-  CONET_FP8E4M3 = 2,           /* E4M3 weights with per-output-channel scales (tcgen05) */
-  CONET_FP16 = 3               /* FP16 activations / weights, FP32 accumulate (tcgen05) */
+  CONET_FP8E4M3 = 2,           /* E4M3 weights (per-output-channel scales) and activations
+                                  (per-tensor scales from calibration), FP32 accumulate
+                                  (tcgen05 kind::f8f6f4); inference only */
+  CONET_FP16 = 3,              /* FP16 activations / weights, FP32 accumulate (tcgen05) */
+  CONET_TF32X3 = 4             /* FP32-accurate on tensor cores: operands split into TF32 hi +
+                                  lo parts, hi*hi + hi*lo + lo*hi accumulated in FP32 (tcgen05) */
 } conet_precision;
 
 /*
@@ -162,6 +166,23 @@ int conet_grads_device(conet_t h, float** dev_grads, size_t* n);
  */
 int conet_forward(conet_t h, const float* Y, const uint8_t* pilot_mask, const float* noise_var,
                   int B, float* llr, void* stream);
+
+/*
+ * Activation scales of a CONET_FP8E4M3 handle.  Every conv input (the assembled grid and each
+ * branch's activation entering each conv) is stored as E4M3 of value / s with one scale s per
+ * tensor; the weights of each output channel carry their own scale (the smallest power of
+ * two >= largest |w| / 448), and the FP32 accumulator is multiplied back by s x that channel
+ * scale before the bias (the FP8 variant of the convolutions of Sec. III).  E4M3 values are
+ * rounded to nearest even and saturate at +-448.  This call runs the forward pass on the
+ * first min(B, activation chunk) of the given slots and sets each s = the smallest power of
+ * two >= margin x (largest |value| of that tensor on them) / 448; larger values met later
+ * saturate at +-448 s.  Arguments as for
+ * conet_forward; margin in [1, 448], else CONET_ERR_ARG.  Handles of other precisions
+ * return CONET_OK and change nothing.  A forward pass on an FP8 handle whose weights changed
+ * since its last calibration (or that was never calibrated) first calibrates on its own
+ * first chunk with margin 2.  Writes no caller memory; asynchronous on `stream`.
+ */
+int conet_calibrate(conet_t h, const float* Y, const uint8_t* pilot_mask, int B, float margin, void* stream);
 
 /*
  * Backward of the last conet_forward on this handle for upstream gradient dllr (dev

@@ -201,13 +201,22 @@ def head1x1(tp, x, w, b):
 
 
 # ----------------------------------------------------------------------------- network
-def forward(cfg, flat, X0, keep_tape=False):
-    """LLR [B, T, F, Q] of the CoNet described by ``cfg`` with flat parameters ``flat``."""
+def forward(cfg, flat, X0, keep_tape=False, quant=None):
+    """LLR [B, T, F, Q] of the CoNet described by ``cfg`` with flat parameters ``flat``.
+
+    ``quant`` (optional, inference only): an object whose ``act(x)`` and ``weight(w)``
+    replace every 3x3 conv's input and weight by their quantised values (oracle.fp8)."""
     tp = Tape()
     P = unflatten(cfg, np.asarray(flat, dtype=np.float64))
     ids = {k: tp.leaf(v) for k, v in P.items()}
     x_in = tp.leaf(np.asarray(X0, dtype=np.float64))
     nb = cfg.n_branches
+
+    def conv(x, w, b):
+        if quant is not None:
+            x = tp.leaf(quant.act(tp[x]))
+            w = tp.leaf(quant.weight(tp[w]))
+        return conv3x3(tp, x, w, b)
 
     def fuse(i, acts):
         if not cfg.fused(i):
@@ -217,11 +226,11 @@ def forward(cfg, flat, X0, keep_tape=False):
             m = layernorm(tp, m, ids[f"f{i}.g"], ids[f"f{i}.b"])
         return [m] + list(acts[1:])
 
-    acts = [relu(tp, conv3x3(tp, x_in, ids[f"b{b}.in.w"], ids[f"b{b}.in.b"])) for b in range(nb)]
+    acts = [relu(tp, conv(x_in, ids[f"b{b}.in.w"], ids[f"b{b}.in.b"])) for b in range(nb)]
     x = fuse(0, acts)
     if not cfg.residual:
         for l in range(1, cfg.depth):
-            acts = [relu(tp, conv3x3(tp, x[b], ids[f"b{b}.l{l}.w"], ids[f"b{b}.l{l}.b"]))
+            acts = [relu(tp, conv(x[b], ids[f"b{b}.l{l}.w"], ids[f"b{b}.l{l}.b"]))
                     for b in range(nb)]
             x = fuse(l, acts)
     else:
@@ -233,9 +242,9 @@ def forward(cfg, flat, X0, keep_tape=False):
                     h1 = relu(tp, layernorm(tp, x[b], ids[p + "ln1.g"], ids[p + "ln1.b"]))
                 else:
                     h1 = relu(tp, x[b])
-                t1 = conv3x3(tp, h1, ids[p + "c1.w"], ids[p + "c1.b"])
+                t1 = conv(h1, ids[p + "c1.w"], ids[p + "c1.b"])
                 h2 = relu(tp, layernorm(tp, t1, ids[p + "ln2.g"], ids[p + "ln2.b"]))
-                u.append(add(tp, x[b], conv3x3(tp, h2, ids[p + "c2.w"], ids[p + "c2.b"])))
+                u.append(add(tp, x[b], conv(h2, ids[p + "c2.w"], ids[p + "c2.b"])))
             x = fuse(k + 1, u)
     llr = head1x1(tp, x[0], ids["head.w"], ids["head.b"])
     if keep_tape:

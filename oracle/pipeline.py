@@ -16,6 +16,13 @@ def receive(cfg, params, Y, pilot_sym, pilot_mask):
     return onet.forward(cfg, params, X0)
 
 
+def receive_fp8(cfg, params, Y, pilot_sym, pilot_mask, margin: float = 2.0):
+    """receive() with E4M3 conv operands (oracle.fp8), scales calibrated on this batch."""
+    from . import fp8
+    X0 = orx.assemble_input(Y, pilot_sym, pilot_mask)
+    return fp8.forward_fp8(cfg, params, X0, margin)
+
+
 def train_step(cfg, sim, params, m, v, step: int, seed: int, batch: int, lr: float):
     """Slots seed/(step*batch .. step*batch+batch-1); returns (params, m, v, loss)."""
     s = osim.simulate(cfg, sim, seed, step * batch, batch)

@@ -48,6 +48,7 @@ SIGNATURES = {
     "conet_params_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
     "conet_grads_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
     "conet_forward": (I, [P, P, P, P, I, P, P]),
+    "conet_calibrate": (I, [P, P, P, I, F32, P]),
     "conet_backward": (I, [P, P, I, P]),
     "conet_adam_step": (I, [P, F32, I, P]),
     "conet_conv3x3_wgrad": (I, [P, P, I, I, I, I, I, P, P, P]),

@@ -14,7 +14,7 @@ import torch
 
 from ._lib import check, conet_config, conet_sim_params, lib
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3, "tf32x3": 4}
 
 
 def make_config(net, max_batch: int = 1, train: bool = False) -> conet_config:
@@ -120,6 +120,10 @@ class Receiver:
         check(lib().conet_forward(self.h, _ptr(Y), _ptr(pilot_mask), _ptr(noise_var), B, _ptr(llr),
                                   _stream(stream)))
         return llr
+
+    def calibrate(self, Y, pilot_mask, margin: float = 2.0, stream=None):
+        """E4M3 activation scales from these slots (no-op for other precisions)."""
+        check(lib().conet_calibrate(self.h, _ptr(Y), _ptr(pilot_mask), Y.shape[0], margin, _stream(stream)))
 
     def backward(self, dllr, stream=None):
         check(lib().conet_backward(self.h, _ptr(dllr), dllr.shape[0], _stream(stream)))

@@ -205,7 +205,8 @@ int conet_create(const conet_config* cfg, int precision, conet_t* out) {
   CONET_TRY(validate_config(cfg));
   if (!out) return fail(CONET_ERR_ARG, "out is NULL");
   if (cfg->max_batch < 1) return fail(CONET_ERR_SHAPE, "max_batch %d < 1", cfg->max_batch);
-  if (precision != CONET_FP32 && precision != CONET_BF16 && precision != CONET_FP8E4M3 && precision != CONET_FP16)
+  if (precision != CONET_FP32 && precision != CONET_BF16 && precision != CONET_FP8E4M3 && precision != CONET_FP16 &&
+      precision != CONET_TF32X3)
     return fail(CONET_ERR_ARG, "unknown precision %d", precision);
   conet_s* h = new conet_s();
   h->cfg = *cfg;
@@ -280,6 +281,13 @@ int conet_forward(conet_t h, const float* Y, const uint8_t* pilot_mask, const fl
   if (!h || !Y || !pilot_mask || !llr) return fail(CONET_ERR_ARG, "NULL argument");
   if (B < 1 || B > h->cfg.max_batch) return fail(CONET_ERR_SHAPE, "B = %d outside 1..max_batch (%d)", B, h->cfg.max_batch);
   return net_forward(h, Y, pilot_mask, B, llr, (cudaStream_t)stream);
+}
+
+int conet_calibrate(conet_t h, const float* Y, const uint8_t* pilot_mask, int B, float margin, void* stream) {
+  if (!h || !Y || !pilot_mask) return fail(CONET_ERR_ARG, "NULL argument");
+  if (B < 1 || B > h->cfg.max_batch) return fail(CONET_ERR_SHAPE, "B = %d outside 1..max_batch (%d)", B, h->cfg.max_batch);
+  if (!(margin >= 1.f) || !(margin <= 448.f)) return fail(CONET_ERR_ARG, "margin %g outside [1, 448]", (double)margin);
+  return net_calibrate(h, Y, pilot_mask, B, margin, (cudaStream_t)stream);
 }
 
 int conet_backward(conet_t h, const float* dllr, int B, void* stream) {

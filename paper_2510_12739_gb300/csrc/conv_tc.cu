@@ -51,8 +51,11 @@ struct Cfg {
   static constexpr int ROW = KC * ELT;                  // bytes per operand row (= swizzle span)
   static_assert(ROW == 32 || ROW == 64 || ROW == 128, "row bytes");
   static constexpr int SLICES = ROW / 32;               // MMAs (32 bytes of K each) per chunk
-  static constexpr int A_BYTES = TILE_M * ROW;
-  static constexpr int B_BYTES = COUT * ROW;
+  static constexpr int NSPLIT = KIND == 1 ? 2 : 1;      // split TF32: hi and lo copies of A and B
+  static constexpr int A_PART = TILE_M * ROW;
+  static constexpr int B_PART = COUT * ROW;
+  static constexpr int A_BYTES = NSPLIT * A_PART;
+  static constexpr int B_BYTES = NSPLIT * B_PART;
   static constexpr int STAGE_TX = NB * (A_BYTES + B_BYTES);
   static constexpr int STAGE = (STAGE_TX + 1023) / 1024 * 1024;
   static constexpr int K_ITERS = 9 * (CIN / KC);
@@ -120,9 +123,10 @@ __device__ __forceinline__ bool barrier_all(int id, int threads, bool ok) {
   return r != 0;
 }
 
-// v_b = acc_b + bias_b (+ resid_b) for the 16 channels of chunk j of every branch
-// (add = false: the raw TMEM columns, when an earlier pass already wrote v back).
-template <int NB, int COUT>
+// v_b = acc_b (x dq_b on the E4M3 path) + bias_b (+ resid_b) for the 16 channels of chunk j
+// of every branch (add = false: the raw TMEM columns, when an earlier pass already wrote v
+// back).
+template <int KIND, int NB, int COUT>
 __device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, int j, bool valid, long long m,
                                            float (&v)[NB][16], bool add = true) {
   uint32_t r[NB][16];
@@ -136,6 +140,17 @@ __device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, i
   if (!valid || !add) return;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
+    if constexpr (KIND == 2) {
+      const float4* dp = reinterpret_cast<const float4*>(a.dq[b] + 16 * j);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 x = __ldg(dp + i);
+        v[b][4 * i] *= x.x;
+        v[b][4 * i + 1] *= x.y;
+        v[b][4 * i + 2] *= x.z;
+        v[b][4 * i + 3] *= x.w;
+      }
+    }
     const float4* bp = reinterpret_cast<const float4*>(a.bias[b] + 16 * j);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -159,6 +174,26 @@ __device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, i
   }
 }
 
+// 16 consecutive per-channel parameters (16-byte aligned) through the read-only path.
+__device__ __forceinline__ void ldg16(const float* p, float (&x)[16]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 t = __ldg(q + i);
+    x[4 * i] = t.x;
+    x[4 * i + 1] = t.y;
+    x[4 * i + 2] = t.z;
+    x[4 * i + 3] = t.w;
+  }
+}
+
+// Round to the nearest TF32 value (10 explicit mantissa bits; low 13 bits zero).
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void store16_f32(float* p, const float (&x)[16]) {
   float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
@@ -172,6 +207,20 @@ __device__ __forceinline__ void store16_f16(__half* p, const float (&x)[16]) {
   uint4* q = reinterpret_cast<uint4*>(p);
   q[0] = reinterpret_cast<const uint4*>(h)[0];
   q[1] = reinterpret_cast<const uint4*>(h)[1];
+}
+
+// 16 values x qinv as E4M3 (round to nearest even, saturating to +-448): one 16-byte store.
+__device__ __forceinline__ void store16_e4m3(uint8_t* p, const float (&x)[16], float qinv) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x[4 * i] * qinv, x[4 * i + 1] * qinv), __NV_SATFINITE,
+                                                 __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(x[4 * i + 2] * qinv, x[4 * i + 3] * qinv),
+                                                 __NV_SATFINITE, __NV_E4M3);
+    w[i] = (lo & 0xFFFFu) | (hi << 16);
+  }
+  *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 __device__ __forceinline__ void store16_bf16(__nv_bfloat16* p, const float (&x)[16]) {
@@ -217,7 +266,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
     for (int j = j_lo; j < j_hi; ++j) {
       float v[NB][16];
       __syncwarp();
-      load_chunk<NB, COUT>(a, tacc, j, valid, m, v);
+      load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v);
       if (write_back) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) tc::tmem_st16(tacc + (uint32_t)(b * COUT + 16 * j), v[b]);
@@ -270,10 +319,13 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
   float hq[QMAX];
 #pragma unroll
   for (int qq = 0; qq < QMAX; ++qq) hq[qq] = 0.f;
+  float amx[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) amx[b] = 0.f;
   for (int j = j_lo; j < j_hi; ++j) {
     float v[NB][16];
     __syncwarp();
-    load_chunk<NB, COUT>(a, tacc, j, valid, m, v, !write_back);
+    load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v, !write_back);
     const int c0 = 16 * j;
     // rows past the grid edge compute on don't-care values and store nothing
 #pragma unroll
@@ -286,50 +338,90 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
 #pragma unroll
         for (int c = 0; c < 16; ++c) v[b][c] = fmaxf(v[b][c], 0.f);
       } else if (pre_ln) {
+        float g[16], be[16];
+        ldg16(a.ln2_g[b] + c0, g);
+        ldg16(a.ln2_b[b] + c0, be);
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-          v[b][c] = fmaxf((v[b][c] - mean_b[b]) * rstd_b[b] * __ldg(a.ln2_g[b] + c0 + c) + __ldg(a.ln2_b[b] + c0 + c),
-                          0.f);
+        for (int c = 0; c < 16; ++c) v[b][c] = fmaxf((v[b][c] - mean_b[b]) * rstd_b[b] * g[c] + be[c], 0.f);
       }
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b)
       if (valid && a.a_out[b]) store16_f32(a.a_out[b] + m * COUT + c0, v[b]);
     // x_0 = fused (and normalised) product, or a_0; it replaces v[0] from here on
+    if (a.fuse) {
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      float p = v[0][c];
-      if (a.fuse) {
+      for (int c = 0; c < 16; ++c) {
 #pragma unroll
-        for (int b = 1; b < NB; ++b) p *= v[b][c];
-        if (fuse_ln) p = (p - mean_p) * rstd_p * __ldg(a.lnf_g + c0 + c) + __ldg(a.lnf_b + c0 + c);
+        for (int b = 1; b < NB; ++b) v[0][c] *= v[b][c];
       }
-      v[0][c] = p;
+      if (fuse_ln) {
+        float g[16], be[16];
+        ldg16(a.lnf_g + c0, g);
+        ldg16(a.lnf_b + c0, be);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[0][c] = (v[0][c] - mean_p) * rstd_p * g[c] + be[c];
+      }
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      if (valid && a.xs_out[b]) store16_f32(a.xs_out[b] + m * COUT + c0, v[b]);
+      if (valid && a.xs_out[b] && !a.measure) store16_f32(a.xs_out[b] + m * COUT + c0, v[b]);
       if (valid && a.nx_out[b]) {
         float o[16];
+        if (a.post[b] == 2) {
+          float g[16], be[16];
+          ldg16(a.ln1_g[b] + c0, g);
+          ldg16(a.ln1_b[b] + c0, be);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          float y = v[b][c];
-          if (a.post[b] == 2) y = (y - mean_b[b]) * rstd_b[b] * __ldg(a.ln1_g[b] + c0 + c) + __ldg(a.ln1_b[b] + c0 + c);
-          o[c] = a.post[b] ? fmaxf(y, 0.f) : y;
+          for (int c = 0; c < 16; ++c) o[c] = fmaxf((v[b][c] - mean_b[b]) * rstd_b[b] * g[c] + be[c], 0.f);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) o[c] = a.post[b] ? fmaxf(v[b][c], 0.f) : v[b][c];
         }
-        if constexpr (KIND == 3) store16_f16(reinterpret_cast<__half*>(a.nx_out[b]) + m * COUT + c0, o);
-        else store16_bf16(reinterpret_cast<__nv_bfloat16*>(a.nx_out[b]) + m * COUT + c0, o);
+        if constexpr (KIND == 2) {
+          if (a.amax[b]) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) amx[b] = fmaxf(amx[b], fabsf(o[c]));
+          }
+          if (!a.measure) store16_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, __ldg(a.qinv[b]));
+        } else if constexpr (KIND == 3) {
+          store16_f16(reinterpret_cast<__half*>(a.nx_out[b]) + m * COUT + c0, o);
+        } else if constexpr (KIND == 1) {
+          float lo[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const float hi = tf32_round(o[c]);
+            lo[c] = o[c] - hi;
+            o[c] = hi;
+          }
+          store16_f32(reinterpret_cast<float*>(a.nx_out[b]) + m * COUT + c0, o);
+          store16_f32(a.nx_lo[b] + m * COUT + c0, lo);
+        } else {
+          store16_bf16(reinterpret_cast<__nv_bfloat16*>(a.nx_out[b]) + m * COUT + c0, o);
+        }
       }
     }
     if (a.head_w) {
 #pragma unroll
       for (int qq = 0; qq < QMAX; ++qq) {
         if (qq >= a.Q) break;
+        float hw[16];
+        ldg16(a.head_w + qq * COUT + c0, hw);
         float s = 0.f;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) s += __ldg(a.head_w + qq * COUT + c0 + c) * v[0][c];
+        for (int c = 0; c < 16; ++c) s += hw[c] * v[0][c];
         hq[qq] += s;
       }
+    }
+  }
+  if constexpr (KIND == 2) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (!a.amax[b]) continue;
+      float mx = amx[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx > 0.f) atomicMax(a.amax[b], __float_as_uint(mx));
     }
   }
   if (a.head_w) {
@@ -339,7 +431,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
       for (int qq = 0; qq < QMAX; ++qq) slot[qq] = hq[qq];
     }
     named_barrier(1 + 4 + quarter, 32 * EPI_PARTS);
-    if (part == 0 && valid) {
+    if (part == 0 && valid && !a.measure) {
       for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) a.llr[m * a.Q + qq] = hq[qq] + slot[qq] + __ldg(a.head_b + qq);
     }
   }
@@ -414,8 +506,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         uint8_t* st = smem + (size_t)s * K::STAGE;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          tc::tma_load_4d(st + b * K::A_BYTES, &maps.a[b], &full[s], ch, fb * TILE_M + df, t + dt, slot);
-          tc::tma_load_3d(st + NB * K::A_BYTES + b * K::B_BYTES, &maps.w[b], &full[s], ch, 0, tap);
+          uint8_t* ab = st + b * K::A_BYTES;
+          uint8_t* bb = st + NB * K::A_BYTES + b * K::B_BYTES;
+          tc::tma_load_4d(ab, &maps.a[b], &full[s], ch, fb * TILE_M + df, t + dt, slot);
+          tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap);
+          if constexpr (K::NSPLIT == 2) {
+            tc::tma_load_4d(ab + K::A_PART, &maps.a_lo[b], &full[s], ch, fb * TILE_M + df, t + dt, slot);
+            tc::tma_load_3d(bb + K::B_PART, &maps.w_lo[b], &full[s], ch, 0, tap);
+          }
         }
         used[s] = true;
         last_par[s] = ph;
@@ -451,9 +549,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         for (int b = 0; b < NB; ++b) {
 #pragma unroll
           for (int j = 0; j < K::SLICES; ++j) {
-            const uint64_t ad = tc::smem_desc(st + b * K::A_BYTES + 32 * j, K::ROW);
-            const uint64_t bd = tc::smem_desc(st + NB * K::A_BYTES + b * K::B_BYTES + 32 * j, K::ROW);
+            const uint32_t aa = st + b * K::A_BYTES + 32 * j;
+            const uint32_t ba = st + NB * K::A_BYTES + b * K::B_BYTES + 32 * j;
+            const uint64_t ad = tc::smem_desc(aa, K::ROW);
+            const uint64_t bd = tc::smem_desc(ba, K::ROW);
             tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, bd, K::IDESC, (k | j) != 0);
+            if constexpr (K::NSPLIT == 2) {
+              // FP32-accurate product from TF32 parts: hi*hi + hi*lo + lo*hi
+              tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, tc::smem_desc(ba + K::B_PART, K::ROW), K::IDESC, 1u);
+              tc::mma<KIND>(dcol + (uint32_t)(b * COUT), tc::smem_desc(aa + K::A_PART, K::ROW), bd, K::IDESC, 1u);
+            }
           }
         }
         tc::mma_commit(&empty[s]);
@@ -540,6 +645,31 @@ int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, cons
   TC_CASE(3, 4, 96, 96, 32)
   TC_CASE(3, 3, 16, 32, 16)
   TC_CASE(3, 3, 32, 32, 32)
+  // split TF32 (kind::tf32, three MMAs per K slice): FP32-accurate products
+  TC_CASE(1, 2, 16, 32, 8)
+  TC_CASE(1, 2, 32, 32, 8)
+  TC_CASE(1, 3, 16, 64, 8)
+  TC_CASE(1, 3, 64, 64, 8)
+  TC_CASE(1, 4, 16, 96, 8)
+  TC_CASE(1, 4, 96, 96, 8)
+  TC_CASE(1, 3, 16, 32, 8)
+  TC_CASE(1, 3, 32, 32, 8)
+  TC_CASE(1, 1, 16, 112, 8)
+  TC_CASE(1, 1, 112, 112, 8)
+  // the matched single-branch ResNet (width 112) in 16-bit operands
+  TC_CASE(0, 1, 16, 112, 16)
+  TC_CASE(0, 1, 112, 112, 16)
+  TC_CASE(3, 1, 16, 112, 16)
+  TC_CASE(3, 1, 112, 112, 16)
+  // E4M3 operands (kind::f8f6f4): input layers take 32 padded channels (32-byte rows)
+  TC_CASE(2, 2, 32, 32, 32)
+  TC_CASE(2, 3, 32, 32, 32)
+  TC_CASE(2, 3, 32, 64, 32)
+  TC_CASE(2, 3, 64, 64, 64)
+  TC_CASE(2, 4, 32, 96, 32)
+  TC_CASE(2, 4, 96, 96, 32)
+  TC_CASE(2, 1, 32, 64, 32)
+  TC_CASE(2, 1, 64, 64, 64)
 #undef TC_CASE
   return fail(CONET_ERR_UNSUPPORTED, "tensor-core conv kind=%d branches=%d Cin=%d Cout=%d not instantiated", kind, nb,
               cin, cout);
@@ -606,9 +736,29 @@ int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int c
 // Channels per K chunk (one TMA box row): 128-byte rows where the width allows it, so each
 // box moves the fewest, longest rows.
 int tc_chunk(int kind, int cin) {
-  (void)kind;
+  if (kind == 1) return 8;                 // 32-byte FP32 rows keep the hi + lo stages small
+  if (kind == 2) return cin % 128 == 0 ? 128 : cin % 64 == 0 ? 64 : 32;   // E4M3: 1 byte per channel
   if (cin <= 16) return 16;
-  return cin % 64 == 0 ? 64 : 32;
+  if (cin % 64 == 0) return 64;
+  return cin % 32 == 0 ? 32 : 16;
+}
+
+// [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] TF32 hi and FP32 lo = w - hi
+__global__ void weights_split_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+                                     float* __restrict__ hi, float* __restrict__ lo) {
+  const int n = 9 * cout * cin_dst;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int ci = i % cin_dst, rem = i / cin_dst, co = rem % cout, tap = rem / cout;
+    const float v = ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f;
+    const float h = tf32_round(v);
+    hi[i] = h;
+    lo[i] = v - h;
+  }
+}
+
+int launch_weights_split(const float* w, int cout, int cin_src, int cin_dst, float* hi, float* lo, cudaStream_t s) {
+  weights_split_kernel<<<grid_for(9LL * cout * cin_dst, 256, 512), 256, 0, s>>>(w, cout, cin_src, cin_dst, hi, lo);
+  return check_launch("weights_split_kernel");
 }
 
 // [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] BF16, zero padded input channels
@@ -638,6 +788,67 @@ int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_d
     weights_bf16_kernel<<<grid_for(9LL * cout * cin_dst, 256, 512), 256, 0, s>>>(
         w, cout, cin_src, cin_dst, reinterpret_cast<__nv_bfloat16*>(out));
   return check_launch("weights_16_kernel");
+}
+
+// Smallest power of two s with t / s <= 448, the largest finite E4M3 value (1 for t <= 0):
+// with t = m 2^e, m in [0.5, 1), and 448 = 0.875 x 2^9, s = 2^(e - 9) if m <= 0.875 else
+// 2^(e - 8).  Power-of-two scales make scaling and unscaling exact.
+__device__ __forceinline__ float e4m3_pow2_scale(float t) {
+  if (!(t > 0.f)) return 1.f;
+  int e;
+  const float m = frexpf(t, &e);
+  return ldexpf(1.f, m <= 0.875f ? e - 9 : e - 8);
+}
+
+// One CTA per output channel: the channel's scale is the power of two that maps its largest
+// |w| into (224, 448], so that each channel's E4M3 weights use the format's full range
+// (per-output-channel scaling).
+__global__ void weights_fp8_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+                                   uint8_t* __restrict__ out, float* __restrict__ wscale) {
+  __shared__ float red[32];
+  const int co = blockIdx.x;
+  const int n = 9 * cin_src;
+  const float* wc = w + (size_t)co * n;
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, fabsf(wc[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) red[0] = mx;
+  }
+  __syncthreads();
+  const float scale = e4m3_pow2_scale(red[0]);
+  const float inv = 1.f / scale;   // exact: a power of two
+  if (threadIdx.x == 0) wscale[co] = scale;
+  for (int i = threadIdx.x; i < 9 * cin_dst; i += blockDim.x) {
+    const int tap = i / cin_dst, ci = i % cin_dst;
+    const float v = ci < cin_src ? wc[(size_t)tap * cin_src + ci] * inv : 0.f;
+    out[((size_t)tap * cout + co) * cin_dst + ci] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+int launch_weights_fp8(const float* w, int cout, int cin_src, int cin_dst, uint8_t* out, float* wscale,
+                       cudaStream_t s) {
+  weights_fp8_kernel<<<cout, 128, 0, s>>>(w, cout, cin_src, cin_dst, out, wscale);
+  return check_launch("weights_fp8_kernel");
+}
+
+__global__ void fp8_scales_kernel(Fp8ScaleArgs a, int cout, float margin) {
+  const int b = blockIdx.x;
+  const float scale = e4m3_pow2_scale(margin * __uint_as_float(*a.amax[b]));
+  if (threadIdx.x == 0) {
+    *a.scale[b] = scale;
+    *a.qinv[b] = 1.f / scale;
+  }
+  for (int c = threadIdx.x; c < cout; c += blockDim.x) a.dq[b][c] = scale * a.wscale[b][c];
+}
+
+int launch_fp8_scales(const Fp8ScaleArgs& a, int nb, int cout, float margin, cudaStream_t s) {
+  fp8_scales_kernel<<<nb, 128, 0, s>>>(a, cout, margin);
+  return check_launch("fp8_scales_kernel");
 }
 
 }  // namespace conet

@@ -172,6 +172,8 @@ int launch_weights_dgrad_layout(const float* w, int C, float* out, cudaStream_t 
 struct TcMaps {
   CUtensorMap a[MAX_BR];       // activations [slots][T][F][Cin], box {KC, 128, 1, 1}
   CUtensorMap w[MAX_BR];       // weights [9][Cout][Cin], box {KC, Cout, 1}
+  CUtensorMap a_lo[MAX_BR];    // split-TF32 path: low parts of the same tensors
+  CUtensorMap w_lo[MAX_BR];
 };
 
 // Fused epilogue, per RE and branch b:
@@ -194,6 +196,7 @@ struct TcConvArgs {
   float* a_out[MAX_BR];        // a_b (FP32, optional; kept for backward)
   float* xs_out[MAX_BR];
   void* nx_out[MAX_BR];
+  float* nx_lo[MAX_BR];        // split-TF32 path: nx_out holds hi = tf32(next), nx_lo = next - hi
   int post[MAX_BR];
   const float* ln1_g[MAX_BR];
   const float* ln1_b[MAX_BR];
@@ -202,12 +205,43 @@ struct TcConvArgs {
   float* llr;
   int Q;
   int* err;                    // device error word (first timed-out wait)
+  // E4M3 path: accumulator column c of branch b is dequantised by dq[b][c] (= the input's
+  // per-tensor scale x the weights' per-output-channel scale); nx_out[b] is written as
+  // E4M3 of next / scale, with qinv[b] = 1 / scale (device scalars); amax[b], when set,
+  // receives the largest |next| (float bits, atomicMax); measure = 1 writes no activation.
+  const float* dq[MAX_BR];
+  const float* qinv[MAX_BR];
+  unsigned* amax[MAX_BR];
+  int measure;
 };
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
 int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc);
 int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc);
 int tc_chunk(int kind, int cin);
 int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s);
+int launch_weights_split(const float* w, int cout, int cin_src, int cin_dst, float* hi, float* lo, cudaStream_t s);
+int launch_assemble_split(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
+                          int c_pad, float* hi, float* lo, cudaStream_t s);
+// E4M3 input assembly: X0 [B][T][F][c_pad] = E4M3(channel value * qinv[0]); X0 == NULL only
+// accumulates the largest |channel value| into *amax (float bits).
+int launch_assemble_fp8(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
+                        int c_pad, const float* qinv, uint8_t* X0, unsigned* amax, cudaStream_t s);
+// [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] E4M3 with one scale per output
+// channel, wscale[co] = the smallest power of two >= max_{tap,ci} |w| / 448 (1 for an
+// all-zero channel).
+int launch_weights_fp8(const float* w, int cout, int cin_src, int cin_dst, uint8_t* out, float* wscale,
+                       cudaStream_t s);
+// Activation scales of one conv launch from the recorded amax: per branch b, scale = the
+// smallest power of two >= margin * amax[b] / 448 (1 when amax is 0), qinv[b] = 1 / scale
+// and dq[b][c] = scale * wscale[b][c] for c < cout.
+struct Fp8ScaleArgs {
+  const unsigned* amax[MAX_BR];
+  const float* wscale[MAX_BR];
+  float* scale[MAX_BR];
+  float* qinv[MAX_BR];
+  float* dq[MAX_BR];
+};
+int launch_fp8_scales(const Fp8ScaleArgs& a, int nb, int cout, float margin, cudaStream_t s);
 
 // ---------------------------------------------------------------- weights
 // Re-layout of the FP32 master conv weights [Cout][3][3][cin_src] into the kernels'

@@ -105,7 +105,9 @@ int net_setup(conet_s* h) {
   const size_t na = Acts::count(h);
   h->chunk = h->cfg.max_batch;
   if (h->prec != CONET_FP32 && !h->cfg.train) {
-    const double per_slot = (double)h->T * h->F * ((double)na * h->C * 4 + 2.0 * h->nb * h->C * 2 + 16 * 2);
+    // bytes per conv-input value (hi + lo for split TF32)
+    const double opnd = h->prec == CONET_TF32X3 ? 8.0 : h->prec == CONET_FP8E4M3 ? 1.0 : 2.0;
+    const double per_slot = (double)h->T * h->F * ((double)na * h->C * 4 + 2.0 * h->nb * h->C * opnd + 32 * opnd);
     const double fit = 48e9 / per_slot;
     h->chunk = fit < 1 ? 1 : (fit < h->cfg.max_batch ? (int)fit : h->cfg.max_batch);
   }
@@ -201,7 +203,8 @@ static FuseArgs fuse_args(conet_s* h, int B) {
 }
 
 int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
-  if (h->prec == CONET_BF16 || h->prec == CONET_FP16) return net_forward_tc(h, Y, mask, B, llr, s);
+  if (h->prec == CONET_BF16 || h->prec == CONET_FP16 || h->prec == CONET_TF32X3 || h->prec == CONET_FP8E4M3)
+    return net_forward_tc(h, Y, mask, B, llr, s);
   if (h->prec != CONET_FP32) return fail(CONET_ERR_UNSUPPORTED, "precision %d forward not built yet", h->prec);
   const Acts A{h};
   const Layout& L = h->L;
@@ -291,12 +294,32 @@ int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* l
   return CONET_OK;
 }
 
-// ------------------------------------------------------------------ tensor-core (BF16) path
+// ------------------------------------------------------------------ tensor-core paths
 namespace {
 
-constexpr int TC_CIN0 = 16;   // padded input channels of the BF16 input layer
+// tcgen05 operand kind of the handle's precision: 0 BF16, 3 FP16, 1 split TF32, 2 E4M3;
+// -1 = SIMT path.
+int tc_kind(const conet_s* h) {
+  switch (h->prec) {
+    case CONET_BF16: return 0;
+    case CONET_FP16: return 3;
+    case CONET_TF32X3: return 1;
+    case CONET_FP8E4M3: return 2;
+    default: return -1;
+  }
+}
 
-int tc_kind(const conet_s* h) { return h->prec == CONET_BF16 ? 0 : h->prec == CONET_FP16 ? 3 : -1; }
+int tc_elt(int kind) { return kind == 1 ? 4 : kind == 2 ? 1 : 2; }
+
+// Padded input channels of the input layer: one MMA K step (32 bytes) of E4M3, 16 otherwise.
+int tc_cin0(int kind) { return kind == 2 ? 32 : 16; }
+
+// low part of the input buffer of conv launch idx (split TF32)
+const void* tc_conv_in_lo(const conet_s* h, int idx, int b) {
+  if (idx == 0) return h->X0b_lo;
+  if (!h->cfg.residual) return h->nxb_lo[(idx - 1) & 1][b];
+  return h->nxb_lo[(idx - 1) % 2 == 0 ? 0 : 1][b];
+}
 
 // conv launch index -> (per branch) master weight offset
 long tc_conv_w(const conet_s* h, int idx, int b) {
@@ -316,48 +339,92 @@ const void* tc_conv_in(const conet_s* h, int idx, int b) {
   return h->nxb[(idx - 1) % 2 == 0 ? 0 : 1][b];
 }
 
+// E4M3 activation scales of the input of conv launch idx, branch b
+size_t fp8_rec(const conet_s* h, int idx, int b) { return ((size_t)idx * h->nb + b) * (size_t)(h->C + 4); }
+float* fp8_scale(const conet_s* h, int idx, int b) { return h->fp8_act + fp8_rec(h, idx, b); }
+float* fp8_qinv(const conet_s* h, int idx, int b) { return h->fp8_act + fp8_rec(h, idx, b) + 1; }
+float* fp8_dq(const conet_s* h, int idx, int b) { return h->fp8_act + fp8_rec(h, idx, b) + 4; }
+unsigned* fp8_amax(const conet_s* h, int idx, int b) { return h->fp8_amax + (size_t)idx * h->nb + b; }
+
 }  // namespace
 
 int tc_setup(conet_s* h) {
   if (tc_kind(h) < 0) return CONET_OK;
   const int kind = tc_kind(h);
-  if (h->cin > TC_CIN0) return fail(CONET_ERR_UNSUPPORTED, "BF16 path takes at most %d input channels", TC_CIN0);
-  if (h->C % 16) return fail(CONET_ERR_UNSUPPORTED, "BF16 path needs width %% 16 == 0");
+  const int cin0 = tc_cin0(kind);
+  if (h->cin > cin0) return fail(CONET_ERR_UNSUPPORTED, "tensor-core path takes at most %d input channels", cin0);
+  if (h->C % 16) return fail(CONET_ERR_UNSUPPORTED, "tensor-core path needs width %% 16 == 0");
+  if (kind == 2 && h->C % 32) return fail(CONET_ERR_UNSUPPORTED, "E4M3 path needs width %% 32 == 0");
+  if (kind == 2 && h->cfg.train) return fail(CONET_ERR_UNSUPPORTED, "E4M3 handles are inference-only (train = 0)");
   const size_t re = (size_t)h->chunk * h->T * h->F;
-  CONET_TRY(dev_alloc(h, &h->X0b, re * TC_CIN0 * 2));
+  const size_t e = (size_t)tc_elt(kind);
+  const bool split = kind == 1;
+  CONET_TRY(dev_alloc(h, &h->X0b, re * cin0 * e));
+  if (split) CONET_TRY(dev_alloc(h, &h->X0b_lo, re * cin0 * e));
   for (int i = 0; i < 2; ++i)
-    for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc(h, &h->nxb[i][b], re * h->C * 2));
-  size_t wb = 0;
+    for (int b = 0; b < h->nb; ++b) {
+      CONET_TRY(dev_alloc(h, &h->nxb[i][b], re * h->C * e));
+      if (split) CONET_TRY(dev_alloc_t(h, &h->nxb_lo[i][b], re * h->C));
+    }
+  size_t wb = 0, ws = 0;
   for (const auto& c : h->L.convs) {
-    const int cin_dst = c.cin == h->cin ? TC_CIN0 : c.cin;
+    const int cin_dst = c.cin == h->cin ? cin0 : c.cin;
     h->wb_off[c.off] = wb;
     wb += (size_t)9 * cin_dst * c.cout;
+    h->fp8_ws_off[c.off] = ws;
+    ws += (size_t)c.cout;
   }
-  CONET_TRY(dev_alloc(h, &h->wb, wb * 2));
-  CONET_CUDA(cudaMemset(h->wb, 0, wb * 2));
+  CONET_TRY(dev_alloc(h, &h->wb, wb * e));
+  CONET_CUDA(cudaMemset(h->wb, 0, wb * e));
+  if (split) {
+    CONET_TRY(dev_alloc_t(h, &h->wb_lo, wb));
+    CONET_CUDA(cudaMemset(h->wb_lo, 0, wb * sizeof(float)));
+  }
+  const int n = tc_n_convs(h);
+  if (kind == 2) {
+    CONET_TRY(dev_alloc_t(h, &h->fp8_wscale, ws));
+    CONET_TRY(dev_alloc_t(h, &h->fp8_act, (size_t)n * h->nb * (h->C + 4)));
+    CONET_TRY(dev_alloc_t(h, &h->fp8_amax, (size_t)n * h->nb));
+    CONET_CUDA(cudaMemset(h->fp8_act, 0, (size_t)n * h->nb * (h->C + 4) * sizeof(float)));
+  }
   CONET_TRY(dev_alloc_t(h, &h->d_err, 1));
   CONET_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
-  const int n = tc_n_convs(h);
   h->tcmaps.resize(n);
   for (int idx = 0; idx < n; ++idx) {
-    const int cin = idx == 0 ? TC_CIN0 : h->C;
+    const int cin = idx == 0 ? cin0 : h->C;
     const int kc = tc_chunk(kind, cin);
     for (int b = 0; b < h->nb; ++b) {
+      const size_t woff = h->wb_off.at((size_t)tc_conv_w(h, idx, b));
       CONET_TRY(make_act_map(&h->tcmaps[idx].a[b], kind, tc_conv_in(h, idx, b), cin, h->F, h->T, h->chunk, kc));
-      const void* w = static_cast<const uint16_t*>(h->wb) + h->wb_off.at((size_t)tc_conv_w(h, idx, b));
-      CONET_TRY(make_weight_map(&h->tcmaps[idx].w[b], kind, w, cin, h->C, kc));
+      CONET_TRY(make_weight_map(&h->tcmaps[idx].w[b], kind, static_cast<const uint8_t*>(h->wb) + woff * e, cin,
+                                h->C, kc));
+      if (split) {
+        CONET_TRY(make_act_map(&h->tcmaps[idx].a_lo[b], kind, tc_conv_in_lo(h, idx, b), cin, h->F, h->T, h->chunk,
+                               kc));
+        CONET_TRY(make_weight_map(&h->tcmaps[idx].w_lo[b], kind, h->wb_lo + woff, cin, h->C, kc));
+      }
     }
   }
   return CONET_OK;
 }
 
 int tc_weights_changed(conet_s* h, cudaStream_t s) {
-  if (tc_kind(h) < 0) return CONET_OK;
+  const int kind = tc_kind(h);
+  if (kind < 0) return CONET_OK;
   for (const auto& c : h->L.convs) {
-    const int cin_dst = c.cin == h->cin ? TC_CIN0 : c.cin;
-    CONET_TRY(launch_weights_16(tc_kind(h), h->params + c.off, c.cout, c.cin, cin_dst,
-                                static_cast<uint16_t*>(h->wb) + h->wb_off.at(c.off), s));
+    const int cin_dst = c.cin == h->cin ? tc_cin0(kind) : c.cin;
+    const size_t wo = h->wb_off.at(c.off);
+    if (kind == 1)
+      CONET_TRY(launch_weights_split(h->params + c.off, c.cout, c.cin, cin_dst, static_cast<float*>(h->wb) + wo,
+                                     h->wb_lo + wo, s));
+    else if (kind == 2)
+      CONET_TRY(launch_weights_fp8(h->params + c.off, c.cout, c.cin, cin_dst, static_cast<uint8_t*>(h->wb) + wo,
+                                   h->fp8_wscale + h->fp8_ws_off.at(c.off), s));
+    else
+      CONET_TRY(launch_weights_16(kind, h->params + c.off, c.cout, c.cin, cin_dst, static_cast<uint16_t*>(h->wb) + wo,
+                                  s));
   }
+  h->fp8_calibrated = false;   // activation ranges change with the weights
   return CONET_OK;
 }
 
@@ -368,98 +435,164 @@ static int tc_conv(conet_s* h, int idx, TcConvArgs& a, int B, cudaStream_t s) {
   a.n_tiles = B * h->T * a.nfb;
   a.Q = h->Q;
   a.err = h->d_err;
-  const int cin = idx == 0 ? TC_CIN0 : h->C;
+  const int cin = idx == 0 ? tc_cin0(tc_kind(h)) : h->C;
   prof_begin(h, idx == 0 ? PK_CONV_IN : PK_CONV, s);
   const int rc = launch_conv_tc(tc_kind(h), h->nb, cin, h->C, h->tcmaps[idx], a, s);
   prof_end(h, s);
   return rc;
 }
 
-static int net_forward_tc_chunk(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
+// Arguments of conv launch idx of the forward pass over B slots.
+static TcConvArgs tc_args(conet_s* h, int idx, float* llr) {
+  const Acts A{h};
+  const Layout& L = h->L;
+  const int nb = h->nb, depth = h->cfg.depth;
+  const bool train = h->cfg.train != 0;
+  TcConvArgs a = {};
+  if (!h->cfg.residual) {
+    const int l = idx;
+    for (int b = 0; b < nb; ++b) {
+      a.bias[b] = P(h, l == 0 ? L.in_b[b] : L.lb[b][l - 1]);
+      if (l + 1 < depth) {
+        a.nx_out[b] = h->nxb[l & 1][b];
+        a.nx_lo[b] = h->nxb_lo[l & 1][b];
+      }
+      if (train) a.a_out[b] = A.A(l, b);
+    }
+    if (train) a.xs_out[0] = A.XM(l);
+    a.pre = 1;
+    a.fuse = fused_at(h->cfg, l);
+    a.lnf_g = P(h, L.fg[l]);
+    a.lnf_b = P(h, L.fb[l]);
+    if (l == depth - 1) {
+      a.head_w = P(h, L.hw);
+      a.head_b = P(h, L.hb);
+      a.llr = llr;
+    }
+  } else {
+    // input layer, then per block conv1 (LN2 + ReLU epilogue) and conv2 (residual add,
+    // Hadamard fusion + LN, next pre-activation or head)
+    const int k = (idx - 1) / 2;
+    const bool conv1 = idx > 0 && (idx - 1) % 2 == 0;
+    if (conv1) {
+      for (int b = 0; b < nb; ++b) {
+        a.bias[b] = P(h, L.blk[b][k].c1b);
+        a.ln2_g[b] = P(h, L.blk[b][k].ln2g);
+        a.ln2_b[b] = P(h, L.blk[b][k].ln2b);
+        a.nx_out[b] = h->nxb[1][b];
+        a.nx_lo[b] = h->nxb_lo[1][b];
+      }
+      a.pre = 2;
+    } else {
+      const int point = idx == 0 ? 0 : k + 1;        // fusion point after this conv
+      for (int b = 0; b < nb; ++b) {
+        a.bias[b] = P(h, idx == 0 ? L.in_b[b] : L.blk[b][k].c2b);
+        if (idx > 0) a.resid[b] = h->act[(size_t)(k & 1) * nb + b];
+        a.xs_out[b] = h->act[(size_t)(point & 1) * nb + b];
+        if (point < depth) {
+          a.nx_out[b] = h->nxb[0][b];
+          a.nx_lo[b] = h->nxb_lo[0][b];
+          const long g = L.blk[b][point].ln1g;
+          a.post[b] = g >= 0 ? 2 : 1;
+          a.ln1_g[b] = P(h, g);
+          a.ln1_b[b] = P(h, L.blk[b][point].ln1b);
+        }
+      }
+      a.pre = idx == 0 ? 1 : 0;
+      a.fuse = fused_at(h->cfg, point);
+      a.lnf_g = P(h, L.fg[point]);
+      a.lnf_b = P(h, L.fb[point]);
+      if (point == depth) {
+        a.head_w = P(h, L.hw);
+        a.head_b = P(h, L.hb);
+        a.llr = llr;
+      }
+    }
+  }
+  if (tc_kind(h) == 2) {
+    for (int b = 0; b < nb; ++b) {
+      a.dq[b] = fp8_dq(h, idx, b);
+      if (a.nx_out[b]) a.qinv[b] = fp8_qinv(h, idx + 1, b);
+    }
+  }
+  return a;
+}
 
-int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
-  for (int c0 = 0; c0 < B; c0 += h->chunk) {
-    const int Bc = B - c0 < h->chunk ? B - c0 : h->chunk;
-    CONET_TRY(net_forward_tc_chunk(h, Y + (size_t)c0 * h->N * h->T * h->F * 2, mask, Bc,
-                                   llr + (size_t)c0 * h->T * h->F * h->Q, s));
+// Activation scales of conv launch idx's input from the amax recorded for it.
+static int fp8_set_scales(conet_s* h, int idx, float margin, cudaStream_t s) {
+  Fp8ScaleArgs sa = {};
+  for (int b = 0; b < h->nb; ++b) {
+    sa.amax[b] = fp8_amax(h, idx, idx == 0 ? 0 : b);      // the input grid is shared by all branches
+    sa.wscale[b] = h->fp8_wscale + h->fp8_ws_off.at((size_t)tc_conv_w(h, idx, b));
+    sa.scale[b] = fp8_scale(h, idx, b);
+    sa.qinv[b] = fp8_qinv(h, idx, b);
+    sa.dq[b] = fp8_dq(h, idx, b);
+  }
+  return launch_fp8_scales(sa, h->nb, h->C, margin, s);
+}
+
+static int net_forward_tc_chunk(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, bool calibrate,
+                                cudaStream_t s) {
+  const int kind = tc_kind(h);
+  const int n = tc_n_convs(h);
+  const bool train = h->cfg.train != 0;
+  if (train && h->cfg.residual) return fail(CONET_ERR_UNSUPPORTED, "tensor-core training of residual networks");
+  prof_begin(h, PK_ASSEMBLE, s);
+  if (kind == 1) {
+    CONET_TRY(launch_assemble_split(Y, mask, h->psym, B, h->N, h->T, h->F, tc_cin0(kind), static_cast<float*>(h->X0b),
+                                    static_cast<float*>(h->X0b_lo), s));
+  } else if (kind == 2) {
+    if (calibrate) {
+      CONET_CUDA(cudaMemsetAsync(h->fp8_amax, 0, (size_t)n * h->nb * sizeof(unsigned), s));
+      CONET_TRY(launch_assemble_fp8(Y, mask, h->psym, B, h->N, h->T, h->F, tc_cin0(kind), nullptr, nullptr,
+                                    fp8_amax(h, 0, 0), s));
+      CONET_TRY(fp8_set_scales(h, 0, h->fp8_margin, s));
+    }
+    CONET_TRY(launch_assemble_fp8(Y, mask, h->psym, B, h->N, h->T, h->F, tc_cin0(kind), fp8_qinv(h, 0, 0),
+                                  static_cast<uint8_t*>(h->X0b), nullptr, s));
+  } else {
+    CONET_TRY(launch_assemble_16(kind, Y, mask, h->psym, B, h->N, h->T, h->F, tc_cin0(kind), h->X0b, s));
+  }
+  if (train) CONET_TRY(launch_assemble(Y, mask, h->psym, B, h->N, h->T, h->F, h->c_pad, h->X0, s));
+  prof_end(h, s);
+  for (int idx = 0; idx < n; ++idx) {
+    TcConvArgs a = tc_args(h, idx, llr);
+    if (calibrate && idx + 1 < n) {
+      // measuring pass: the outputs' largest magnitude per branch, then the next input's scales
+      TcConvArgs m = a;
+      m.measure = 1;
+      for (int b = 0; b < h->nb; ++b) m.amax[b] = m.nx_out[b] ? fp8_amax(h, idx + 1, b) : nullptr;
+      CONET_TRY(tc_conv(h, idx, m, B, s));
+      CONET_TRY(fp8_set_scales(h, idx + 1, h->fp8_margin, s));
+    }
+    if (idx + 1 == n && !llr) break;     // calibration only: the head's output is not needed
+    CONET_TRY(tc_conv(h, idx, a, B, s));
   }
   h->fwd_B = B;
   return CONET_OK;
 }
 
-static int net_forward_tc_chunk(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
-  const Acts A{h};
-  const Layout& L = h->L;
-  const int nb = h->nb, depth = h->cfg.depth;
-  const bool train = h->cfg.train != 0;
-  if (train && h->cfg.residual) return fail(CONET_ERR_UNSUPPORTED, "BF16 training of residual networks");
-  prof_begin(h, PK_ASSEMBLE, s);
-  CONET_TRY(launch_assemble_16(tc_kind(h), Y, mask, h->psym, B, h->N, h->T, h->F, TC_CIN0, h->X0b, s));
-  if (train) CONET_TRY(launch_assemble(Y, mask, h->psym, B, h->N, h->T, h->F, h->c_pad, h->X0, s));
-  prof_end(h, s);
-  if (!h->cfg.residual) {
-    for (int l = 0; l < depth; ++l) {
-      TcConvArgs a = {};
-      for (int b = 0; b < nb; ++b) {
-        a.bias[b] = P(h, l == 0 ? L.in_b[b] : L.lb[b][l - 1]);
-        if (l + 1 < depth) a.nx_out[b] = h->nxb[l & 1][b];
-        if (train) a.a_out[b] = A.A(l, b);
-      }
-      if (train) a.xs_out[0] = A.XM(l);
-      a.pre = 1;
-      a.fuse = fused_at(h->cfg, l);
-      a.lnf_g = P(h, L.fg[l]);
-      a.lnf_b = P(h, L.fb[l]);
-      if (l == depth - 1) {
-        a.head_w = P(h, L.hw);
-        a.head_b = P(h, L.hb);
-        a.llr = llr;
-      }
-      CONET_TRY(tc_conv(h, l, a, B, s));
-    }
-  } else {
-    // input layer, then per block conv1 (LN2 + ReLU epilogue) and conv2 (residual add,
-    // Hadamard fusion + LN, next pre-activation or head)
-    for (int idx = 0; idx < 1 + 2 * depth; ++idx) {
-      TcConvArgs a = {};
-      const int k = (idx - 1) / 2;
-      const bool conv1 = idx > 0 && (idx - 1) % 2 == 0;
-      if (conv1) {
-        for (int b = 0; b < nb; ++b) {
-          a.bias[b] = P(h, L.blk[b][k].c1b);
-          a.ln2_g[b] = P(h, L.blk[b][k].ln2g);
-          a.ln2_b[b] = P(h, L.blk[b][k].ln2b);
-          a.nx_out[b] = h->nxb[1][b];
-        }
-        a.pre = 2;
-      } else {
-        const int point = idx == 0 ? 0 : k + 1;        // fusion point after this conv
-        for (int b = 0; b < nb; ++b) {
-          a.bias[b] = P(h, idx == 0 ? L.in_b[b] : L.blk[b][k].c2b);
-          if (idx > 0) a.resid[b] = h->act[(size_t)(k & 1) * nb + b];
-          a.xs_out[b] = h->act[(size_t)(point & 1) * nb + b];
-          if (point < depth) {
-            a.nx_out[b] = h->nxb[0][b];
-            const long g = L.blk[b][point].ln1g;
-            a.post[b] = g >= 0 ? 2 : 1;
-            a.ln1_g[b] = P(h, g);
-            a.ln1_b[b] = P(h, L.blk[b][point].ln1b);
-          }
-        }
-        a.pre = idx == 0 ? 1 : 0;
-        a.fuse = fused_at(h->cfg, point);
-        a.lnf_g = P(h, L.fg[point]);
-        a.lnf_b = P(h, L.fb[point]);
-        if (point == depth) {
-          a.head_w = P(h, L.hw);
-          a.head_b = P(h, L.hb);
-          a.llr = llr;
-        }
-      }
-      CONET_TRY(tc_conv(h, idx, a, B, s));
-    }
+int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
+  for (int c0 = 0; c0 < B; c0 += h->chunk) {
+    const int Bc = B - c0 < h->chunk ? B - c0 : h->chunk;
+    const bool calibrate = tc_kind(h) == 2 && !h->fp8_calibrated;
+    CONET_TRY(net_forward_tc_chunk(h, Y + (size_t)c0 * h->N * h->T * h->F * 2, mask, Bc,
+                                   llr + (size_t)c0 * h->T * h->F * h->Q, calibrate, s));
+    if (calibrate) h->fp8_calibrated = true;
   }
   h->fwd_B = B;
+  return CONET_OK;
+}
+
+// E4M3 activation scales from B slots (at most one chunk): the forward pass up to the last
+// conv, every conv run once more beforehand to measure its outputs' range.
+int net_calibrate(conet_s* h, const float* Y, const uint8_t* mask, int B, float margin, cudaStream_t s) {
+  if (tc_kind(h) != 2) return CONET_OK;
+  h->fp8_margin = margin;
+  const int Bc = B < h->chunk ? B : h->chunk;
+  CONET_TRY(net_forward_tc_chunk(h, Y, mask, Bc, nullptr, true, s));
+  h->fp8_calibrated = true;
+  h->fwd_B = 0;
   return CONET_OK;
 }
 
@@ -557,7 +690,8 @@ struct Bwd {
 }  // namespace
 
 int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
-  if (h->prec != CONET_FP32 && ((h->prec != CONET_BF16 && h->prec != CONET_FP16) || h->cfg.residual))
+  if (h->prec != CONET_FP32 &&
+      ((h->prec != CONET_BF16 && h->prec != CONET_FP16 && h->prec != CONET_TF32X3) || h->cfg.residual))
     return fail(CONET_ERR_UNSUPPORTED, "precision %d backward of this network not built yet", h->prec);
   const Acts A{h};
   const Layout& L = h->L;

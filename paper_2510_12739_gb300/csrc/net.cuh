@@ -68,10 +68,20 @@ struct conet_s {
   // tensor-core (BF16) path
   void* X0b = nullptr;                       // assembled input, BF16 [B][T][F][16]
   void* nxb[2][conet::MAX_BR] = {};          // BF16 conv inputs (ping-pong / H1, H2)
+  void* X0b_lo = nullptr;                    // split-TF32 path: low parts of X0b / nxb / wb
+  float* nxb_lo[2][conet::MAX_BR] = {};
+  float* wb_lo = nullptr;
   void* wb = nullptr;                        // BF16 weights [9][Cout][Cin_pad] per conv
   std::map<size_t, size_t> wb_off;
   std::vector<conet::TcMaps> tcmaps;         // tensor maps per conv launch
   int* d_err = nullptr;                      // device error word of the tensor-core kernels
+  // E4M3 path
+  float* fp8_wscale = nullptr;               // per conv: [Cout] per-output-channel weight scales
+  std::map<size_t, size_t> fp8_ws_off;       // master offset -> offset in fp8_wscale
+  float* fp8_act = nullptr;                  // per conv launch and branch: scale, 1/scale, pad, dq[C]
+  unsigned* fp8_amax = nullptr;              // per conv launch and branch: largest |input| (float bits)
+  bool fp8_calibrated = false;               // activation scales valid for the current weights
+  float fp8_margin = 2.f;                    // scale = margin * amax / 448
   float* sim_Y = nullptr;                    // training-step slots
   uint8_t* sim_bits = nullptr;
   float* sim_nv = nullptr;
@@ -107,5 +117,6 @@ int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* l
 int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s);
 int net_adam(conet_s* h, float lr, int step, cudaStream_t s);
 int net_train_step(conet_s* h, const SimArgs& a, uint64_t step, int B, float lr, double* loss_out, cudaStream_t s);
+int net_calibrate(conet_s* h, const float* Y, const uint8_t* mask, int B, float margin, cudaStream_t s);
 
 }  // namespace conet

@@ -3,6 +3,7 @@
 // BCE-loss / bit-error counter over data REs.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -77,6 +78,118 @@ int launch_assemble_16(int kind, const float* Y, const uint8_t* mask, const floa
         reinterpret_cast<const float2*>(Y), mask, reinterpret_cast<const float2*>(psym), B, N, T, F, c_pad,
         reinterpret_cast<__nv_bfloat16*>(X0));
   return check_launch("assemble_kernel_16");
+}
+
+// Same channels as assemble_kernel, written as TF32 hi parts and FP32 lo = x - hi.
+__global__ void assemble_split_kernel(const float2* __restrict__ Y, const uint8_t* __restrict__ mask,
+                                      const float2* __restrict__ psym, int B, int N, int T, int F, int c_pad,
+                                      float* __restrict__ hi, float* __restrict__ lo) {
+  const long long TF = (long long)T * F;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)B * TF;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / TF, r = i % TF;
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = 0.f;
+    const bool pil = mask[r] != 0;
+    const float2 p = psym[r];
+    const float inv = pil ? 1.0f / (p.x * p.x + p.y * p.y) : 0.f;
+    float hr = 0.f, hq = 0.f;
+    for (int n = 0; n < N; ++n) {
+      const float2 y = Y[(b * N + n) * TF + r];
+      v[n] = y.x;
+      v[N + n] = y.y;
+      hr += (y.x * p.x + y.y * p.y) * inv;
+      hq += (y.y * p.x - y.x * p.y) * inv;
+    }
+    v[2 * N] = pil ? 1.f : 0.f;
+    v[2 * N + 1] = hr / (float)N;
+    v[2 * N + 2] = hq / (float)N;
+    for (int c = 0; c < c_pad; c += 4) {
+      float h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint32_t u;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v[c + j]));
+        h[j] = __uint_as_float(u);
+        l[j] = v[c + j] - h[j];
+      }
+      *reinterpret_cast<float4*>(hi + i * c_pad + c) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(lo + i * c_pad + c) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+int launch_assemble_split(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
+                          int c_pad, float* hi, float* lo, cudaStream_t s) {
+  const long long n = (long long)B * T * F;
+  assemble_split_kernel<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const float2*>(Y), mask,
+                                                         reinterpret_cast<const float2*>(psym), B, N, T, F, c_pad,
+                                                         hi, lo);
+  return check_launch("assemble_split_kernel");
+}
+
+// Same channels as assemble_kernel (c_pad <= 32), written as E4M3 of value * qinv[0]; with
+// X0 == NULL the kernel only folds the largest |value| into *amax.
+__global__ void assemble_fp8_kernel(const float2* __restrict__ Y, const uint8_t* __restrict__ mask,
+                                    const float2* __restrict__ psym, int B, int N, int T, int F, int c_pad,
+                                    const float* __restrict__ qinv, uint8_t* __restrict__ X0,
+                                    unsigned* __restrict__ amax) {
+  const long long TF = (long long)T * F;
+  const float qi = X0 ? *qinv : 1.f;
+  float mx = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)B * TF;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / TF, r = i % TF;
+    float v[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = 0.f;
+    const bool pil = mask[r] != 0;
+    const float2 p = psym[r];
+    const float inv = pil ? 1.0f / (p.x * p.x + p.y * p.y) : 0.f;
+    float hr = 0.f, hq = 0.f;
+    for (int n = 0; n < N; ++n) {
+      const float2 y = Y[(b * N + n) * TF + r];
+      v[n] = y.x;
+      v[N + n] = y.y;
+      hr += (y.x * p.x + y.y * p.y) * inv;
+      hq += (y.y * p.x - y.x * p.y) * inv;
+    }
+    v[2 * N] = pil ? 1.f : 0.f;
+    v[2 * N + 1] = hr / (float)N;
+    v[2 * N + 2] = hq / (float)N;
+    if (!X0) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) mx = fmaxf(mx, fabsf(v[c]));
+      continue;
+    }
+    for (int c = 0; c < c_pad; c += 16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[c + 4 * j] * qi, v[c + 4 * j + 1] * qi),
+                                                     __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[c + 4 * j + 2] * qi, v[c + 4 * j + 3] * qi),
+                                                     __NV_SATFINITE, __NV_E4M3);
+        w[j] = (lo & 0xFFFFu) | (hi << 16);
+      }
+      *reinterpret_cast<uint4*>(X0 + i * c_pad + c) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  if (!X0) {
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(amax, __float_as_uint(mx));
+  }
+}
+
+int launch_assemble_fp8(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
+                        int c_pad, const float* qinv, uint8_t* X0, unsigned* amax, cudaStream_t s) {
+  if (c_pad != 32 || 2 * N + 3 > 32) return fail(CONET_ERR_UNSUPPORTED, "E4M3 input assembly pads to 32 channels");
+  const long long n = (long long)B * T * F;
+  assemble_fp8_kernel<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const float2*>(Y), mask,
+                                                       reinterpret_cast<const float2*>(psym), B, N, T, F, c_pad, qinv,
+                                                       X0, amax);
+  return check_launch("assemble_fp8_kernel");
 }
 
 // ------------------------------------------------------------------ LS-LMMSE
