@@ -45,20 +45,63 @@ __host__ __device__ constexpr int pow2_ceil(int x) {
   return p;
 }
 
-template <int KIND, int NB, int CIN, int COUT, int KC>
+__host__ __device__ constexpr int elt_of(int kind) { return kind == 1 ? 4 : kind == 2 ? 1 : 2; }
+__host__ __device__ constexpr int nsplit_of(int kind) { return kind == 1 ? 2 : 1; }
+
+// Shared-memory bytes of one pipeline stage: per branch (and split part) an A box of
+// a_rows rows and `taps` weight slices of cout rows, rows of `row` bytes; 1 KB aligned.
+__host__ __device__ constexpr size_t stage_bytes(int kind, int nb, int cout, int row, int a_rows, int taps) {
+  return ((size_t)nb * nsplit_of(kind) * ((size_t)a_rows * row + (size_t)taps * cout * row) + 1023) / 1024 * 1024;
+}
+
+__host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row, int a_rows, int taps) {
+  return (int)((SMEM_LIMIT - 1024 - 256 - xch_floats(nb) * sizeof(float)) /
+               stage_bytes(kind, nb, cout, row, a_rows, taps));
+}
+
+// K chunk (channels per operand row) and stage shape of an instantiation.  Preferred: the
+// "halo" stage -- one TMA box of TILE_M + 2 subcarriers serves the three subcarrier taps of
+// one symbol row through descriptors shifted by 0, 1, 2 rows, with the three taps' weights
+// -- at the longest operand row (128, 64, 32 bytes) that divides Cin and leaves >= 3
+// stages.  Else one tap per stage at the longest row that leaves >= 2 stages.
+constexpr int HALO_ROWS = TILE_M + 8;   // smem rows reserved for a halo box (a whole swizzle atom)
+__host__ __device__ constexpr int kc_min(int kind) { return 32 / elt_of(kind); }   // one MMA K step
+
+__host__ __device__ constexpr int tc_plan(int kind, int nb, int cin, int cout, bool want_halo) {
+  // returns KC for the requested stage shape, 0 if none fits
+  for (int row = 128; row >= 32; row >>= 1) {
+    const int kc = row / elt_of(kind);
+    if (kc < kc_min(kind) || cin % kc) continue;
+    if (want_halo ? stages_fit(kind, nb, cout, row, HALO_ROWS, 3) >= 3 : stages_fit(kind, nb, cout, row, TILE_M, 1) >= 2)
+      return kc;
+  }
+  return 0;
+}
+
+__host__ __device__ constexpr int tc_halo(int kind, int nb, int cin, int cout) {
+  return tc_plan(kind, nb, cin, cout, true) > 0 ? 1 : 0;
+}
+
+__host__ __device__ constexpr int tc_kc(int kind, int nb, int cin, int cout) {
+  return tc_halo(kind, nb, cin, cout) ? tc_plan(kind, nb, cin, cout, true) : tc_plan(kind, nb, cin, cout, false);
+}
+
+template <int KIND, int NB, int CIN, int COUT, int KC, int HALO>
 struct Cfg {
-  static constexpr int ELT = (KIND == 0 || KIND == 3) ? 2 : KIND == 1 ? 4 : 1;
+  static constexpr int ELT = elt_of(KIND);
   static constexpr int ROW = KC * ELT;                  // bytes per operand row (= swizzle span)
   static_assert(ROW == 32 || ROW == 64 || ROW == 128, "row bytes");
   static constexpr int SLICES = ROW / 32;               // MMAs (32 bytes of K each) per chunk
-  static constexpr int NSPLIT = KIND == 1 ? 2 : 1;      // split TF32: hi and lo copies of A and B
-  static constexpr int A_PART = TILE_M * ROW;
-  static constexpr int B_PART = COUT * ROW;
+  static constexpr int NSPLIT = nsplit_of(KIND);        // split TF32: hi and lo copies of A and B
+  static constexpr int TAPS = HALO ? 3 : 1;             // weight taps (subcarrier shifts) per stage
+  static constexpr int A_BOX = HALO ? TILE_M + 2 : TILE_M;
+  static constexpr int A_PART = (HALO ? HALO_ROWS : TILE_M) * ROW;
+  static constexpr int B_PART = TAPS * COUT * ROW;
   static constexpr int A_BYTES = NSPLIT * A_PART;
   static constexpr int B_BYTES = NSPLIT * B_PART;
-  static constexpr int STAGE_TX = NB * (A_BYTES + B_BYTES);
-  static constexpr int STAGE = (STAGE_TX + 1023) / 1024 * 1024;
-  static constexpr int K_ITERS = 9 * (CIN / KC);
+  static constexpr int STAGE_TX = NB * NSPLIT * (A_BOX * ROW + B_PART);
+  static constexpr int STAGE = (int)stage_bytes(KIND, NB, COUT, ROW, HALO ? HALO_ROWS : TILE_M, TAPS);
+  static constexpr int K_ITERS = (9 / TAPS) * (CIN / KC);
   static constexpr int COLS = pow2_ceil(NB * COUT);
   static constexpr int N_ACC = 2 * COLS <= 512 ? 2 : 1;
   static constexpr int TMEM_COLS = N_ACC * COLS;
@@ -71,6 +114,8 @@ struct Cfg {
   static_assert(COUT % 16 == 0 && COUT <= 256, "MMA N");
   static_assert(NB * COUT <= 512, "TMEM columns");
   static_assert(CIN % KC == 0, "K chunking");
+  static_assert(A_PART % 1024 == 0 || (A_PART % 512 == 0 && ROW <= 64) || (A_PART % 256 == 0 && ROW == 32),
+                "A part must hold whole swizzle atoms");
 };
 
 // Shifted first and second moments of part of a channel vector (shift = the part's first
@@ -444,9 +489,23 @@ __device__ __forceinline__ void decode_tile(int tile, int T, int nfb, int& slot,
   slot = st / T;
 }
 
-template <int KIND, int NB, int CIN, int COUT, int KC>
+// Start moving a tile's residual rows (contiguous: consecutive subcarriers of one symbol)
+// from HBM into L2, so that the epilogue's loads of them wait on L2 rather than on DRAM.
+template <int NB, int COUT>
+__device__ __forceinline__ void prefetch_resid(const TcConvArgs& a, int tile) {
+  if (tile >= a.n_tiles) return;
+  int slot, t, fb;
+  decode_tile(tile, a.T, a.nfb, slot, t, fb);
+  const int rows = a.F - fb * TILE_M < TILE_M ? a.F - fb * TILE_M : TILE_M;
+  const long long m0 = ((long long)slot * a.T + t) * a.F + (long long)fb * TILE_M;
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    if (a.resid[b]) tc::prefetch_l2(a.resid[b] + m0 * COUT, (uint32_t)(rows * COUT * sizeof(float)));
+}
+
+template <int KIND, int NB, int CIN, int COUT, int KC, int HALO>
 __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ TcMaps maps, TcConvArgs a) {
-  using K = Cfg<KIND, NB, CIN, COUT, KC>;
+  using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)K::STAGES * K::STAGE);
@@ -501,18 +560,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
           break;
         }
         tc::mbar_arrive_expect_tx(&full[s], K::STAGE_TX);
-        const int tap = k / (CIN / KC), ch = (k % (CIN / KC)) * KC;
-        const int dt = tap / 3 - 1, df = tap % 3 - 1;
+        // halo stage: symbol row t + dt, subcarriers from one before the tile, taps
+        // (dt, -1..1); else one tap (dt, df) with the tile's rows shifted by df
+        const int grp = k / (CIN / KC), ch = (k % (CIN / KC)) * KC;
+        const int dt = HALO ? grp - 1 : grp / 3 - 1;
+        const int f0 = HALO ? fb * TILE_M - 1 : fb * TILE_M + grp % 3 - 1;
+        const int tap0 = HALO ? 3 * grp : grp;
         uint8_t* st = smem + (size_t)s * K::STAGE;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
           uint8_t* ab = st + b * K::A_BYTES;
           uint8_t* bb = st + NB * K::A_BYTES + b * K::B_BYTES;
-          tc::tma_load_4d(ab, &maps.a[b], &full[s], ch, fb * TILE_M + df, t + dt, slot);
-          tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap);
+          tc::tma_load_4d(ab, &maps.a[b], &full[s], ch, f0, t + dt, slot);
+          tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap0);
           if constexpr (K::NSPLIT == 2) {
-            tc::tma_load_4d(ab + K::A_PART, &maps.a_lo[b], &full[s], ch, fb * TILE_M + df, t + dt, slot);
-            tc::tma_load_3d(bb + K::B_PART, &maps.w_lo[b], &full[s], ch, 0, tap);
+            tc::tma_load_4d(ab + K::A_PART, &maps.a_lo[b], &full[s], ch, f0, t + dt, slot);
+            tc::tma_load_3d(bb + K::B_PART, &maps.w_lo[b], &full[s], ch, 0, tap0);
           }
         }
         used[s] = true;
@@ -548,16 +611,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
 #pragma unroll
-          for (int j = 0; j < K::SLICES; ++j) {
-            const uint32_t aa = st + b * K::A_BYTES + 32 * j;
-            const uint32_t ba = st + NB * K::A_BYTES + b * K::B_BYTES + 32 * j;
-            const uint64_t ad = tc::smem_desc(aa, K::ROW);
-            const uint64_t bd = tc::smem_desc(ba, K::ROW);
-            tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, bd, K::IDESC, (k | j) != 0);
-            if constexpr (K::NSPLIT == 2) {
-              // FP32-accurate product from TF32 parts: hi*hi + hi*lo + lo*hi
-              tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, tc::smem_desc(ba + K::B_PART, K::ROW), K::IDESC, 1u);
-              tc::mma<KIND>(dcol + (uint32_t)(b * COUT), tc::smem_desc(aa + K::A_PART, K::ROW), bd, K::IDESC, 1u);
+          for (int d = 0; d < K::TAPS; ++d) {
+#pragma unroll
+            for (int j = 0; j < K::SLICES; ++j) {
+              // tap d of a halo stage reads the box from row d: the swizzle pattern is a
+              // function of the shared-memory address, so a whole-row shift of the
+              // descriptor's start selects the shifted rows
+              const uint32_t aa = st + b * K::A_BYTES + d * K::ROW + 32 * j;
+              const uint32_t ba = st + NB * K::A_BYTES + b * K::B_BYTES + d * COUT * K::ROW + 32 * j;
+              const uint64_t ad = tc::smem_desc(aa, K::ROW);
+              const uint64_t bd = tc::smem_desc(ba, K::ROW);
+              tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, bd, K::IDESC, (k | d | j) != 0);
+              if constexpr (K::NSPLIT == 2) {
+                // FP32-accurate product from TF32 parts: hi*hi + hi*lo + lo*hi
+                tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, tc::smem_desc(ba + K::B_PART, K::ROW), K::IDESC, 1u);
+                tc::mma<KIND>(dcol + (uint32_t)(b * COUT), tc::smem_desc(aa + K::A_PART, K::ROW), bd, K::IDESC, 1u);
+              }
             }
           }
         }
@@ -574,10 +643,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
     const int part = (warp - 2) / 4;        // which share of the channels this warp handles
     const int row = 32 * q + lane;
+    const bool prefetcher = warp == 2 && lane == 0;
+    if (prefetcher) prefetch_resid<NB, COUT>(a, blockIdx.x);
     int it = 0;
     for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
+      if (prefetcher) prefetch_resid<NB, COUT>(a, tile + gridDim.x);
       const bool got = tc::mbar_wait(&tfull[acc], aph, err, 4);
       if (!barrier_all(1 + q, 32 * EPI_PARTS, got)) break;
       tc::fence_after_sync();
@@ -602,12 +674,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   }
 }
 
-template <int KIND, int NB, int CIN, int COUT, int KC>
+template <int KIND, int NB, int CIN, int COUT, int KC, int HALO>
 int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
-  using K = Cfg<KIND, NB, CIN, COUT, KC>;
+  using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
   static int attr_done = 0;
   if (!attr_done) {
-    CONET_CUDA(cudaFuncSetAttribute(conv_tc_kernel<KIND, NB, CIN, COUT, KC>,
+    CONET_CUDA(cudaFuncSetAttribute(conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM));
     attr_done = 1;
   }
@@ -615,61 +687,62 @@ int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
   CONET_CUDA(cudaGetDevice(&dev));
   CONET_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = a.n_tiles < n_sm ? a.n_tiles : n_sm;
-  conv_tc_kernel<KIND, NB, CIN, COUT, KC><<<grid, TC_THREADS, K::SMEM, s>>>(maps, a);
+  conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO><<<grid, TC_THREADS, K::SMEM, s>>>(maps, a);
   return check_launch("conv_tc_kernel");
 }
 
 }  // namespace
 
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
-#define TC_CASE(KI, NBV, CI, CO, KCV) \
-  if (kind == KI && nb == NBV && cin == CI && cout == CO) return launch_tc_t<KI, NBV, CI, CO, KCV>(maps, a, s);
+#define TC_CASE(KI, NBV, CI, CO)                                                                          \
+  if (kind == KI && nb == NBV && cin == CI && cout == CO)                                                  \
+    return launch_tc_t<KI, NBV, CI, CO, tc_kc(KI, NBV, CI, CO), tc_halo(KI, NBV, CI, CO)>(maps, a, s);
   // BF16 (kind::f16): input layers take 16 padded channels (32-byte rows)
-  TC_CASE(0, 2, 16, 32, 16)
-  TC_CASE(0, 2, 32, 32, 32)
-  TC_CASE(0, 3, 16, 64, 16)
-  TC_CASE(0, 3, 64, 64, 64)
-  TC_CASE(0, 4, 16, 96, 16)
-  TC_CASE(0, 4, 96, 96, 32)
-  TC_CASE(0, 1, 16, 64, 16)
-  TC_CASE(0, 1, 64, 64, 64)
-  TC_CASE(0, 3, 16, 16, 16)
-  TC_CASE(0, 3, 16, 32, 16)
-  TC_CASE(0, 3, 32, 32, 32)
+  TC_CASE(0, 2, 16, 32)
+  TC_CASE(0, 2, 32, 32)
+  TC_CASE(0, 3, 16, 64)
+  TC_CASE(0, 3, 64, 64)
+  TC_CASE(0, 4, 16, 96)
+  TC_CASE(0, 4, 96, 96)
+  TC_CASE(0, 1, 16, 64)
+  TC_CASE(0, 1, 64, 64)
+  TC_CASE(0, 3, 16, 16)
+  TC_CASE(0, 3, 16, 32)
+  TC_CASE(0, 3, 32, 32)
   // FP16 operands (kind::f16, same rate, 11-bit significands)
-  TC_CASE(3, 2, 16, 32, 16)
-  TC_CASE(3, 2, 32, 32, 32)
-  TC_CASE(3, 3, 16, 64, 16)
-  TC_CASE(3, 3, 64, 64, 64)
-  TC_CASE(3, 4, 16, 96, 16)
-  TC_CASE(3, 4, 96, 96, 32)
-  TC_CASE(3, 3, 16, 32, 16)
-  TC_CASE(3, 3, 32, 32, 32)
+  TC_CASE(3, 2, 16, 32)
+  TC_CASE(3, 2, 32, 32)
+  TC_CASE(3, 3, 16, 64)
+  TC_CASE(3, 3, 64, 64)
+  TC_CASE(3, 4, 16, 96)
+  TC_CASE(3, 4, 96, 96)
+  TC_CASE(3, 3, 16, 32)
+  TC_CASE(3, 3, 32, 32)
   // split TF32 (kind::tf32, three MMAs per K slice): FP32-accurate products
-  TC_CASE(1, 2, 16, 32, 8)
-  TC_CASE(1, 2, 32, 32, 8)
-  TC_CASE(1, 3, 16, 64, 8)
-  TC_CASE(1, 3, 64, 64, 8)
-  TC_CASE(1, 4, 16, 96, 8)
-  TC_CASE(1, 4, 96, 96, 8)
-  TC_CASE(1, 3, 16, 32, 8)
-  TC_CASE(1, 3, 32, 32, 8)
-  TC_CASE(1, 1, 16, 112, 8)
-  TC_CASE(1, 1, 112, 112, 8)
+  TC_CASE(1, 2, 16, 32)
+  TC_CASE(1, 2, 32, 32)
+  TC_CASE(1, 3, 16, 64)
+  TC_CASE(1, 3, 64, 64)
+  TC_CASE(1, 4, 16, 96)
+  TC_CASE(1, 4, 96, 96)
+  TC_CASE(1, 3, 16, 32)
+  TC_CASE(1, 3, 32, 32)
+  TC_CASE(1, 1, 16, 112)
+  TC_CASE(1, 1, 112, 112)
   // the matched single-branch ResNet (width 112) in 16-bit operands
-  TC_CASE(0, 1, 16, 112, 16)
-  TC_CASE(0, 1, 112, 112, 16)
-  TC_CASE(3, 1, 16, 112, 16)
-  TC_CASE(3, 1, 112, 112, 16)
+  TC_CASE(0, 1, 16, 112)
+  TC_CASE(0, 1, 112, 112)
+  TC_CASE(3, 1, 16, 112)
+  TC_CASE(3, 1, 112, 112)
   // E4M3 operands (kind::f8f6f4): input layers take 32 padded channels (32-byte rows)
-  TC_CASE(2, 2, 32, 32, 32)
-  TC_CASE(2, 3, 32, 32, 32)
-  TC_CASE(2, 3, 32, 64, 32)
-  TC_CASE(2, 3, 64, 64, 64)
-  TC_CASE(2, 4, 32, 96, 32)
-  TC_CASE(2, 4, 96, 96, 32)
-  TC_CASE(2, 1, 32, 64, 32)
-  TC_CASE(2, 1, 64, 64, 64)
+  TC_CASE(2, 2, 32, 32)
+  TC_CASE(2, 3, 32, 32)
+  TC_CASE(2, 3, 32, 64)
+  TC_CASE(2, 3, 64, 64)
+  TC_CASE(2, 4, 32, 96)
+  TC_CASE(2, 4, 96, 96)
+  TC_CASE(2, 1, 32, 64)
+  TC_CASE(2, 1, 64, 64)
 #undef TC_CASE
   return fail(CONET_ERR_UNSUPPORTED, "tensor-core conv kind=%d branches=%d Cin=%d Cout=%d not instantiated", kind, nb,
               cin, cout);
@@ -703,13 +776,13 @@ static CUtensorMapDataType dtype_of(int kind) {
                    : kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
 }
 
-int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc) {
+int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc, int taps) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CONET_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const int e = (kind == 0 || kind == 3) ? 2 : kind == 1 ? 4 : 1;
   const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)F, (cuuint64_t)T, (cuuint64_t)slots};
   const cuuint64_t strides[3] = {(cuuint64_t)C * e, (cuuint64_t)F * C * e, (cuuint64_t)T * F * C * e};
-  const cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)TILE_M, 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)(taps == 3 ? TILE_M + 2 : TILE_M), 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUresult r = enc(map, dtype_of(kind), 4, const_cast<void*>(base), dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(kc * e), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -718,13 +791,13 @@ int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int
   return CONET_OK;
 }
 
-int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc) {
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int taps) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CONET_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const int e = (kind == 0 || kind == 3) ? 2 : kind == 1 ? 4 : 1;
   const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)cout, 9};
   const cuuint64_t strides[2] = {(cuuint64_t)cin * e, (cuuint64_t)cout * cin * e};
-  const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)cout, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)cout, (cuuint32_t)taps};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(map, dtype_of(kind), 3, const_cast<void*>(base), dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(kc * e), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -733,15 +806,9 @@ int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int c
   return CONET_OK;
 }
 
-// Channels per K chunk (one TMA box row): 128-byte rows where the width allows it, so each
-// box moves the fewest, longest rows.
-int tc_chunk(int kind, int cin) {
-  if (kind == 1) return 8;                 // 32-byte FP32 rows keep the hi + lo stages small
-  if (kind == 2) return cin % 128 == 0 ? 128 : cin % 64 == 0 ? 64 : 32;   // E4M3: 1 byte per channel
-  if (cin <= 16) return 16;
-  if (cin % 64 == 0) return 64;
-  return cin % 32 == 0 ? 32 : 16;
-}
+// Channels per K chunk and taps per stage of the instantiation for (kind, nb, cin, cout).
+int tc_chunk(int kind, int nb, int cin, int cout) { return tc_kc(kind, nb, cin, cout); }
+int tc_taps(int kind, int nb, int cin, int cout) { return tc_halo(kind, nb, cin, cout) ? 3 : 1; }
 
 // [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] TF32 hi and FP32 lo = w - hi
 __global__ void weights_split_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,

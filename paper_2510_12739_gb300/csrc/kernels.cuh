@@ -215,9 +215,13 @@ struct TcConvArgs {
   int measure;
 };
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
-int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc);
-int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc);
-int tc_chunk(int kind, int cin);
+// TMA maps of one conv operand: activations [slots][T][F][C] read in boxes of kc channels x
+// (TILE_M, or TILE_M + 2 when taps == 3) subcarriers; weights [9][cout][cin] in boxes of
+// kc x cout x taps.
+int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc, int taps);
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int taps);
+int tc_chunk(int kind, int nb, int cin, int cout);
+int tc_taps(int kind, int nb, int cin, int cout);
 int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s);
 int launch_weights_split(const float* w, int cout, int cin_src, int cin_dst, float* hi, float* lo, cudaStream_t s);
 int launch_assemble_split(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
