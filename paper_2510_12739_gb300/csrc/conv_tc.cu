@@ -19,6 +19,8 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -28,16 +30,17 @@ namespace conet {
 namespace {
 
 constexpr int TILE_M = 128;
-constexpr int EPI_PARTS = 2;                      // epilogue warps per TMEM lane quarter
+constexpr int EPI_PARTS = 3;                      // epilogue warps per TMEM lane quarter (channel parts)
 constexpr int EPI_WARPS = 4 * EPI_PARTS;
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int CW = 8;                             // accumulator columns per epilogue chunk
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 constexpr int HEAD_QMAX = 8;
-
-// Shared memory the epilogue parts use to merge LayerNorm moments and head partial sums.
-__host__ __device__ constexpr size_t xch_floats(int nb) {
-  return (size_t)4 * EPI_PARTS * 32 * (nb + 1) * 2 + (size_t)4 * 32 * HEAD_QMAX;
-}
+// Per epilogue warp: shared scratch used in turn for the LayerNorm moment exchange
+// ((NB + 1) x 2 x 32 floats) and the head's partial sums (HEAD_QMAX x 32 floats).
+constexpr int SCR_WARP_FLOATS = 320;
+constexpr size_t SCR_BYTES = (size_t)EPI_WARPS * SCR_WARP_FLOATS * sizeof(float);
+static_assert((4 + 1) * 2 * 32 <= SCR_WARP_FLOATS && HEAD_QMAX * 32 <= SCR_WARP_FLOATS, "epilogue scratch");
 
 __host__ __device__ constexpr int pow2_ceil(int x) {
   int p = 32;
@@ -55,7 +58,7 @@ __host__ __device__ constexpr size_t stage_bytes(int kind, int nb, int cout, int
 }
 
 __host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row, int a_rows, int taps) {
-  return (int)((SMEM_LIMIT - 1024 - 256 - xch_floats(nb) * sizeof(float)) /
+  return (int)((SMEM_LIMIT - 1024 - 256 - SCR_BYTES) /
                stage_bytes(kind, nb, cout, row, a_rows, taps));
 }
 
@@ -105,49 +108,27 @@ struct Cfg {
   static constexpr int COLS = pow2_ceil(NB * COUT);
   static constexpr int N_ACC = 2 * COLS <= 512 ? 2 : 1;
   static constexpr int TMEM_COLS = N_ACC * COLS;
-  static constexpr size_t XCH = xch_floats(NB) * sizeof(float);
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - XCH) / STAGE);
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR_BYTES) / STAGE);
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + XCH;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR_BYTES;
   static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT);   // BF16 / TF32 / F16, E4M3
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
-  static_assert(COUT % 16 == 0 && COUT <= 256, "MMA N");
+  static_assert(COUT % 16 == 0 && COUT <= 256 && COUT % CW == 0, "MMA N");
   static_assert(NB * COUT <= 512, "TMEM columns");
   static_assert(CIN % KC == 0, "K chunking");
   static_assert(A_PART % 1024 == 0 || (A_PART % 512 == 0 && ROW <= 64) || (A_PART % 256 == 0 && ROW == 32),
                 "A part must hold whole swizzle atoms");
 };
 
-// Shifted first and second moments of part of a channel vector (shift = the part's first
-// element), reduced to (mean, M2) and merged across parts by Chan et al.'s pairwise rule.
-struct Moments {
-  float k = 0.f, s1 = 0.f, s2 = 0.f;
-  __device__ __forceinline__ void add(float x, bool first) {
-    if (first) k = x;
-    const float d = x - k;
-    s1 += d;
-    s2 += d * d;
-  }
-  __device__ __forceinline__ void partial(int n, float& mean, float& m2) const {
-    if (n == 0) {
-      mean = 0.f;
-      m2 = 0.f;
-      return;
-    }
-    const float m1 = s1 / (float)n;
-    mean = k + m1;
-    m2 = fmaxf(s2 - s1 * m1, 0.f);
-  }
-};
-
-// (na, ma, Ma) + (nb, mb, Mb) -> mean and 1/sqrt(var + eps) of the union (n = na + nb).
-__device__ __forceinline__ void merge_moments(int na, float ma, float Ma, int nb, float mb, float Mb, float& mean,
-                                             float& rstd) {
-  const float n = (float)(na + nb);
+// Chan et al.'s pairwise rule: fold the part (nb, mb, Mb) -- count, mean and sum of
+// squared deviations -- into the running (na, ma, Ma).
+__device__ __forceinline__ void chan_fold(float& na, float& ma, float& Ma, float nb, float mb, float Mb) {
+  if (nb == 0.f) return;
+  const float n = na + nb;
   const float d = mb - ma;
-  mean = ma + d * ((float)nb / n);
-  const float m2 = Ma + Mb + d * d * ((float)na * (float)nb / n);
-  rstd = rsqrtf(m2 / n + 1e-5f);
+  ma += d * (nb / n);
+  Ma += Mb + d * d * (na * nb / n);
+  na = n;
 }
 
 __device__ __forceinline__ void named_barrier(int id, int threads) {
@@ -155,8 +136,8 @@ __device__ __forceinline__ void named_barrier(int id, int threads) {
 }
 
 // Barrier over `threads` threads that also returns whether `ok` held in all of them, so the
-// warps of an epilogue pair always take the same branch (a lone warp would otherwise wait at
-// the next named barrier for a partner that already left).
+// warps of an epilogue quarter always take the same branch (a lone warp would otherwise wait
+// at the next named barrier for partners that already left).
 __device__ __forceinline__ bool barrier_all(int id, int threads, bool ok) {
   uint32_t r;
   asm volatile(
@@ -168,67 +149,50 @@ __device__ __forceinline__ bool barrier_all(int id, int threads, bool ok) {
   return r != 0;
 }
 
-// v_b = acc_b (x dq_b on the E4M3 path) + bias_b (+ resid_b) for the 16 channels of chunk j
-// of every branch (add = false: the raw TMEM columns, when an earlier pass already wrote v
-// back).
+// 8 consecutive floats (32-byte aligned: one whole sector) in one 256-bit access: read-only
+// loads of per-channel parameters and residual rows, and stores of FP32 output rows.
+__device__ __forceinline__ void ldg8(const float* p, float (&x)[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+      : "l"(p));
+}
+
+__device__ __forceinline__ void stg8(float* p, const float (&x)[8]) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(x[0]), "f"(x[1]), "f"(x[2]),
+               "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
+               : "memory");
+}
+
+// v_b = acc_b (x dq_b on the E4M3 path) + bias_b (+ resid_b) for the 8 channels of chunk j
+// of every branch (add = false: the raw TMEM columns, when an earlier pass wrote v back).
 template <int KIND, int NB, int COUT>
 __device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, int j, bool valid, long long m,
-                                           float (&v)[NB][16], bool add = true) {
-  uint32_t r[NB][16];
+                                           float (&v)[NB][CW], bool add) {
+  uint32_t r[NB][CW];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) tc::tmem_ld16_nowait(tacc + (uint32_t)(b * COUT + 16 * j), r[b]);
+  for (int b = 0; b < NB; ++b) tc::tmem_ld8_nowait(tacc + (uint32_t)(b * COUT + CW * j), r[b]);
   tc::tmem_wait_ld();
 #pragma unroll
   for (int b = 0; b < NB; ++b)
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[b][c] = __uint_as_float(r[b][c]);
-  if (!valid || !add) return;
+    for (int c = 0; c < CW; ++c) v[b][c] = __uint_as_float(r[b][c]);
+  if (!add) return;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
+    float x[CW];
     if constexpr (KIND == 2) {
-      const float4* dp = reinterpret_cast<const float4*>(a.dq[b] + 16 * j);
+      ldg8(a.dq[b] + CW * j, x);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float4 x = __ldg(dp + i);
-        v[b][4 * i] *= x.x;
-        v[b][4 * i + 1] *= x.y;
-        v[b][4 * i + 2] *= x.z;
-        v[b][4 * i + 3] *= x.w;
-      }
+      for (int c = 0; c < CW; ++c) v[b][c] *= x[c];
     }
-    const float4* bp = reinterpret_cast<const float4*>(a.bias[b] + 16 * j);
+    ldg8(a.bias[b] + CW * j, x);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float4 x = __ldg(bp + i);
-      v[b][4 * i] += x.x;
-      v[b][4 * i + 1] += x.y;
-      v[b][4 * i + 2] += x.z;
-      v[b][4 * i + 3] += x.w;
+    for (int c = 0; c < CW; ++c) v[b][c] += x[c];
+    if (a.resid[b] && valid) {
+      ldg8(a.resid[b] + m * COUT + CW * j, x);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) v[b][c] += x[c];
     }
-    if (a.resid[b]) {
-      const float4* rp = reinterpret_cast<const float4*>(a.resid[b] + m * COUT + 16 * j);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float4 x = __ldg(rp + i);
-        v[b][4 * i] += x.x;
-        v[b][4 * i + 1] += x.y;
-        v[b][4 * i + 2] += x.z;
-        v[b][4 * i + 3] += x.w;
-      }
-    }
-  }
-}
-
-// 16 consecutive per-channel parameters (16-byte aligned) through the read-only path.
-__device__ __forceinline__ void ldg16(const float* p, float (&x)[16]) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float4 t = __ldg(q + i);
-    x[4 * i] = t.x;
-    x[4 * i + 1] = t.y;
-    x[4 * i + 2] = t.z;
-    x[4 * i + 3] = t.w;
   }
 }
 
@@ -239,126 +203,148 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ void store16_f32(float* p, const float (&x)[16]) {
-  float4* q = reinterpret_cast<float4*>(p);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) q[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
-}
-
-__device__ __forceinline__ void store16_f16(__half* p, const float (&x)[16]) {
-  __align__(16) __half2 h[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) h[i] = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
-  uint4* q = reinterpret_cast<uint4*>(p);
-  q[0] = reinterpret_cast<const uint4*>(h)[0];
-  q[1] = reinterpret_cast<const uint4*>(h)[1];
-}
-
-// 16 values x qinv as E4M3 (round to nearest even, saturating to +-448): one 16-byte store.
-__device__ __forceinline__ void store16_e4m3(uint8_t* p, const float (&x)[16], float qinv) {
+// 8 values as 16-bit floats (one 16-byte store) or as E4M3 of value x qinv (one 8-byte store).
+template <typename H>
+__device__ __forceinline__ void store8_h(H* p, const float (&x)[8]) {
   uint32_t w[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
+    if constexpr (std::is_same<H, __half>::value) {
+      const __half2 h = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  }
+  *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ void store8_e4m3(uint8_t* p, const float (&x)[8], float qinv) {
+  uint32_t w[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
     const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x[4 * i] * qinv, x[4 * i + 1] * qinv), __NV_SATFINITE,
                                                  __NV_E4M3);
     const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(x[4 * i + 2] * qinv, x[4 * i + 3] * qinv),
                                                  __NV_SATFINITE, __NV_E4M3);
     w[i] = (lo & 0xFFFFu) | (hi << 16);
   }
-  *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
 }
 
-__device__ __forceinline__ void store16_bf16(__nv_bfloat16* p, const float (&x)[16]) {
-  __align__(16) __nv_bfloat162 h[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
-  uint4* q = reinterpret_cast<uint4*>(p);
-  q[0] = reinterpret_cast<const uint4*>(h)[0];
-  q[1] = reinterpret_cast<const uint4*>(h)[1];
+// Chunks [first, first + count) of COUT / CW owned by channel part p (near-equal split).
+template <int COUT>
+__device__ __forceinline__ void part_chunks(int p, int& first, int& count) {
+  constexpr int CH = COUT / CW, base = CH / EPI_PARTS, rem = CH % EPI_PARTS;
+  first = p * base + (p < rem ? p : rem);
+  count = base + (p < rem ? 1 : 0);
 }
 
-// The fused epilogue for one RE (this thread's TMEM lane) and one part of its channels:
-// two passes over the part's accumulator columns -- statistics of every LayerNorm it
-// applies (merged with the other part through shared memory), then the outputs; the head's
-// partial sums are merged the same way and written by part 0.
+// The fused epilogue for one RE (this thread's TMEM lane) and one part of its channels.
+// Pass 1 (when a LayerNorm is applied) folds each branch's values, and the fused product,
+// into shifted first and second moments; the parts of a lane quarter publish theirs in
+// their shared scratch and each part merges all of them in the same order (Chan et al.), so
+// every part normalises with identical statistics.  Pass 1 also writes the biased (and
+// residual-added) values back into TMEM.  Pass 2 applies the pre-activation, the Hadamard
+// fusion and its LayerNorm, writes the residual stream and the next conv's input, and
+// accumulates the head's partial sums, which part 0 reduces through the scratch.
 template <int KIND, int NB, int COUT>
 __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, bool valid, long long m, int part,
-                                            int quarter, int lane, float* xstat, float* xhead) {
-  constexpr int CH = COUT / 16;
-  constexpr int CHP = (CH + EPI_PARTS - 1) / EPI_PARTS;   // chunks of the first part
+                                            int quarter, int lane, float* scr_all) {
   constexpr int QMAX = HEAD_QMAX;
-  const int j_lo = part == 0 ? 0 : CHP;
-  const int j_hi = part == 0 ? CHP : CH;
-  const int n_part = 16 * (j_hi - j_lo);
+  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+  int j_lo, n_ch;
+  part_chunks<COUT>(part, j_lo, n_ch);
+  const int j_hi = j_lo + n_ch;
   const bool pre_ln = a.pre == 2;
   const bool fuse_ln = a.fuse && a.lnf_g != nullptr;
-  bool need_ln1[NB];
   bool any_ln1 = false;
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    need_ln1[b] = a.post[b] == 2;
-    any_ln1 = any_ln1 || need_ln1[b];
-  }
-  bool has_resid = false;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) has_resid = has_resid || a.resid[b] != nullptr;
-  Moments mb[NB], mp;
-  // With a statistics pass and a residual input, the statistics pass writes v (bias and
-  // residual added) back into TMEM so that the output pass reads no global memory again.
+  for (int b = 0; b < NB; ++b) any_ln1 = any_ln1 || a.post[b] == 2;
   const bool stats = pre_ln || fuse_ln || any_ln1;
-  const bool write_back = stats && has_resid;
+  const bool add2 = !stats;   // pass 2 adds bias / residual itself unless pass 1 wrote v back
+
+  float mean_b[NB], rstd_b[NB], mean_p = 0.f, rstd_p = 1.f;
   if (stats) {
-    for (int j = j_lo; j < j_hi; ++j) {
-      float v[NB][16];
-      __syncwarp();
-      load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v);
-      if (write_back) {
+    // shifted sums: shift = the part's first value of each statistic
+    float k_b[NB], s1_b[NB], s2_b[NB], k_p = 0.f, s1_p = 0.f, s2_p = 0.f;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) tc::tmem_st16(tacc + (uint32_t)(b * COUT + 16 * j), v[b]);
+    for (int b = 0; b < NB; ++b) k_b[b] = s1_b[b] = s2_b[b] = 0.f;
+    for (int j = j_lo; j < j_hi; ++j) {
+      float v[NB][CW];
+      __syncwarp();
+      load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v, true);
+      __syncwarp();   // tcgen05.st is warp-collective: reconverge after the per-row residual loads
+#pragma unroll
+      for (int b = 0; b < NB; ++b) tc::tmem_st8_nowait(tacc + (uint32_t)(b * COUT + CW * j), v[b]);
+      // the statistic of branch b is over v_b (pre_ln) or over pre(v_b) (the next block's
+      // LN1); the fused product is over pre(v_b).  pre = 1 is ReLU, applied in place here
+      // (pass 2 re-reads the unactivated values from TMEM).
+      if (a.pre == 1) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int c = 0; c < CW; ++c) v[b][c] = fmaxf(v[b][c], 0.f);
+      }
+      if (j == j_lo) {
+        float p0 = 1.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          k_b[b] = v[b][0];
+          p0 *= v[b][0];
+        }
+        k_p = p0;
       }
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const bool first = (j == j_lo && c == 0);
+      for (int c = 0; c < CW; ++c) {
         float p = 1.f;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          const float x = v[b][c];
-          const float ab = a.pre == 1 ? fmaxf(x, 0.f) : x;
-          if (pre_ln) mb[b].add(x, first);
-          else if (need_ln1[b]) mb[b].add(ab, first);
-          p *= ab;
+          const float d = v[b][c] - k_b[b];
+          s1_b[b] += d;
+          s2_b[b] = fmaf(d, d, s2_b[b]);
+          p *= v[b][c];
         }
-        if (fuse_ln) mp.add(p, first);
+        if (fuse_ln) {
+          const float d = p - k_p;
+          s1_p += d;
+          s2_p = fmaf(d, d, s2_p);
+        }
       }
     }
-  }
-  // merge the parts' moments (the barrier runs every tile, statistics or not, so that the
-  // head exchange below never overtakes a reader of the previous tile)
-  float mean_b[NB], rstd_b[NB], mean_p = 0.f, rstd_p = 1.f;
-  {
-    float* mine = xstat + (((size_t)(quarter * EPI_PARTS + part) * 32 + lane) * (NB + 1)) * 2;
-    float* other = xstat + (((size_t)(quarter * EPI_PARTS + (part ^ 1)) * 32 + lane) * (NB + 1)) * 2;
-    if (stats) {
+    __syncwarp();
+    tc::tmem_wait_st();
+    // publish (mean, M2) of this part, then fold all parts in order
+    const float n_mine = (float)(CW * n_ch);
 #pragma unroll
-      for (int b = 0; b < NB; ++b) mb[b].partial(n_part, mine[2 * b], mine[2 * b + 1]);
-      mp.partial(n_part, mine[2 * NB], mine[2 * NB + 1]);
+    for (int s = 0; s <= NB; ++s) {
+      const float k = s < NB ? k_b[s] : k_p, s1 = s < NB ? s1_b[s] : s1_p, s2 = s < NB ? s2_b[s] : s2_p;
+      const float m1 = n_ch ? s1 / n_mine : 0.f;
+      scr[(2 * s) * 32 + lane] = k + m1;
+      scr[(2 * s + 1) * 32 + lane] = fmaxf(s2 - s1 * m1, 0.f);
     }
     named_barrier(1 + quarter, 32 * EPI_PARTS);
-    if (stats) {
-      const int n_other = COUT - n_part;
 #pragma unroll
-      for (int b = 0; b <= NB; ++b) {
-        float mm, rr;
-        merge_moments(n_part, mine[2 * b], mine[2 * b + 1], n_other, other[2 * b], other[2 * b + 1], mm, rr);
-        if (b < NB) {
-          mean_b[b] = mm;
-          rstd_b[b] = rr;
-        } else {
-          mean_p = mm;
-          rstd_p = rr;
-        }
+    for (int s = 0; s <= NB; ++s) {
+      float n = 0.f, mu = 0.f, M2 = 0.f;
+#pragma unroll
+      for (int pp = 0; pp < EPI_PARTS; ++pp) {
+        int f0, cnt;
+        part_chunks<COUT>(pp, f0, cnt);
+        const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+        chan_fold(n, mu, M2, (float)(CW * cnt), o[(2 * s) * 32 + lane], o[(2 * s + 1) * 32 + lane]);
+      }
+      const float rs = rsqrtf(M2 / (float)COUT + 1e-5f);
+      if (s < NB) {
+        mean_b[s] = mu;
+        rstd_b[s] = rs;
+      } else {
+        mean_p = mu;
+        rstd_p = rs;
       }
     }
+    named_barrier(1 + quarter, 32 * EPI_PARTS);   // scratch free for the stores
   }
 
   float hq[QMAX];
@@ -368,81 +354,89 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
 #pragma unroll
   for (int b = 0; b < NB; ++b) amx[b] = 0.f;
   for (int j = j_lo; j < j_hi; ++j) {
-    float v[NB][16];
+    float v[NB][CW];
     __syncwarp();
-    load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v, !write_back);
-    const int c0 = 16 * j;
+    load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v, add2);
+    const int c0 = CW * j;
     // rows past the grid edge compute on don't-care values and store nothing
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-      if (valid && a.t_out[b]) store16_f32(a.t_out[b] + m * COUT + c0, v[b]);
+      if (valid && a.t_out[b]) stg8(a.t_out[b] + m * COUT + c0, v[b]);
     // a_b = pre(v_b), in place
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       if (a.pre == 1) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[b][c] = fmaxf(v[b][c], 0.f);
+        for (int c = 0; c < CW; ++c) v[b][c] = fmaxf(v[b][c], 0.f);
       } else if (pre_ln) {
-        float g[16], be[16];
-        ldg16(a.ln2_g[b] + c0, g);
-        ldg16(a.ln2_b[b] + c0, be);
+        float g[CW], be[CW];
+        ldg8(a.ln2_g[b] + c0, g);
+        ldg8(a.ln2_b[b] + c0, be);
+        const float mu = mean_b[b], rs = rstd_b[b];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[b][c] = fmaxf((v[b][c] - mean_b[b]) * rstd_b[b] * g[c] + be[c], 0.f);
+        for (int c = 0; c < CW; ++c) v[b][c] = fmaxf((v[b][c] - mu) * rs * g[c] + be[c], 0.f);
       }
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-      if (valid && a.a_out[b]) store16_f32(a.a_out[b] + m * COUT + c0, v[b]);
+      if (valid && a.a_out[b]) stg8(a.a_out[b] + m * COUT + c0, v[b]);
     // x_0 = fused (and normalised) product, or a_0; it replaces v[0] from here on
     if (a.fuse) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < CW; ++c) {
 #pragma unroll
         for (int b = 1; b < NB; ++b) v[0][c] *= v[b][c];
       }
       if (fuse_ln) {
-        float g[16], be[16];
-        ldg16(a.lnf_g + c0, g);
-        ldg16(a.lnf_b + c0, be);
+        float g[CW], be[CW];
+        ldg8(a.lnf_g + c0, g);
+        ldg8(a.lnf_b + c0, be);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[0][c] = (v[0][c] - mean_p) * rstd_p * g[c] + be[c];
+        for (int c = 0; c < CW; ++c) v[0][c] = (v[0][c] - mean_p) * rstd_p * g[c] + be[c];
       }
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      if (valid && a.xs_out[b] && !a.measure) store16_f32(a.xs_out[b] + m * COUT + c0, v[b]);
-      if (valid && a.nx_out[b]) {
-        float o[16];
+      if (valid && a.xs_out[b] && !a.measure) stg8(a.xs_out[b] + m * COUT + c0, v[b]);
+      if (a.nx_out[b]) {
+        float o[CW];
         if (a.post[b] == 2) {
-          float g[16], be[16];
-          ldg16(a.ln1_g[b] + c0, g);
-          ldg16(a.ln1_b[b] + c0, be);
+          float g[CW], be[CW];
+          ldg8(a.ln1_g[b] + c0, g);
+          ldg8(a.ln1_b[b] + c0, be);
+          const float mu = mean_b[b], rs = rstd_b[b];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) o[c] = fmaxf((v[b][c] - mean_b[b]) * rstd_b[b] * g[c] + be[c], 0.f);
+          for (int c = 0; c < CW; ++c) o[c] = fmaxf((v[b][c] - mu) * rs * g[c] + be[c], 0.f);
+        } else if (a.post[b] == 1) {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) o[c] = fmaxf(v[b][c], 0.f);
         } else {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) o[c] = a.post[b] ? fmaxf(v[b][c], 0.f) : v[b][c];
+          for (int c = 0; c < CW; ++c) o[c] = v[b][c];
         }
         if constexpr (KIND == 2) {
-          if (a.amax[b]) {
+          if (a.amax[b] && valid) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) amx[b] = fmaxf(amx[b], fabsf(o[c]));
+            for (int c = 0; c < CW; ++c) amx[b] = fmaxf(amx[b], fabsf(o[c]));
           }
-          if (!a.measure) store16_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, __ldg(a.qinv[b]));
-        } else if constexpr (KIND == 3) {
-          store16_f16(reinterpret_cast<__half*>(a.nx_out[b]) + m * COUT + c0, o);
+          if (valid && !a.measure)
+            store8_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, __ldg(a.qinv[b]));
         } else if constexpr (KIND == 1) {
-          float lo[16];
+          float lo[CW];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
+          for (int c = 0; c < CW; ++c) {
             const float hi = tf32_round(o[c]);
             lo[c] = o[c] - hi;
             o[c] = hi;
           }
-          store16_f32(reinterpret_cast<float*>(a.nx_out[b]) + m * COUT + c0, o);
-          store16_f32(a.nx_lo[b] + m * COUT + c0, lo);
+          if (valid) {
+            stg8(reinterpret_cast<float*>(a.nx_out[b]) + m * COUT + c0, o);
+            stg8(a.nx_lo[b] + m * COUT + c0, lo);
+          }
+        } else if constexpr (KIND == 3) {
+          if (valid) store8_h(reinterpret_cast<__half*>(a.nx_out[b]) + m * COUT + c0, o);
         } else {
-          store16_bf16(reinterpret_cast<__nv_bfloat16*>(a.nx_out[b]) + m * COUT + c0, o);
+          if (valid) store8_h(reinterpret_cast<__nv_bfloat16*>(a.nx_out[b]) + m * COUT + c0, o);
         }
       }
     }
@@ -450,12 +444,12 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
 #pragma unroll
       for (int qq = 0; qq < QMAX; ++qq) {
         if (qq >= a.Q) break;
-        float hw[16];
-        ldg16(a.head_w + qq * COUT + c0, hw);
-        float s = 0.f;
+        float hw[CW];
+        ldg8(a.head_w + qq * COUT + c0, hw);
+        float sacc = 0.f;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) s += hw[c] * v[0][c];
-        hq[qq] += s;
+        for (int c = 0; c < CW; ++c) sacc = fmaf(hw[c], v[0][c], sacc);
+        hq[qq] += sacc;
       }
     }
   }
@@ -470,14 +464,17 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
     }
   }
   if (a.head_w) {
-    float* slot = xhead + ((size_t)quarter * 32 + lane) * QMAX;
-    if (part == 1) {
-#pragma unroll
-      for (int qq = 0; qq < QMAX; ++qq) slot[qq] = hq[qq];
-    }
-    named_barrier(1 + 4 + quarter, 32 * EPI_PARTS);
+    __syncwarp();
+    for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) scr[qq * 32 + lane] = hq[qq];
+    named_barrier(5 + quarter, 32 * EPI_PARTS);
     if (part == 0 && valid && !a.measure) {
-      for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) a.llr[m * a.Q + qq] = hq[qq] + slot[qq] + __ldg(a.head_b + qq);
+      for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) {
+        float sum = 0.f;
+#pragma unroll
+        for (int pp = 0; pp < EPI_PARTS; ++pp)
+          sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
+        a.llr[m * a.Q + qq] = sum + __ldg(a.head_b + qq);
+      }
     }
   }
 }
@@ -504,6 +501,7 @@ __device__ __forceinline__ void prefetch_resid(const TcConvArgs& a, int tile) {
 }
 
 template <int KIND, int NB, int CIN, int COUT, int KC, int HALO>
+// 14 warps: at most 4 per SM sub-partition, so up to 128 registers each.
 __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ TcMaps maps, TcConvArgs a) {
   using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
   extern __shared__ uint8_t smem_raw[];
@@ -513,8 +511,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   uint64_t* tfull = empty + K::STAGES;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-  float* xstat = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256);
-  float* xhead = xstat + (size_t)4 * EPI_PARTS * 32 * (NB + 1) * 2;
+  float* scr_all = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -659,7 +656,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       const bool valid = f < a.F;
       const long long m = ((long long)slot * a.T + t) * a.F + f;
       const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + ((uint32_t)(32 * q) << 16);
-      tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m, part, q, lane, xstat, xhead);
+      tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m, part, q, lane, scr_all);
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[acc]);

@@ -339,11 +339,13 @@ const void* tc_conv_in(const conet_s* h, int idx, int b) {
   return h->nxb[(idx - 1) % 2 == 0 ? 0 : 1][b];
 }
 
-// E4M3 activation scales of the input of conv launch idx, branch b
-size_t fp8_rec(const conet_s* h, int idx, int b) { return ((size_t)idx * h->nb + b) * (size_t)(h->C + 4); }
+// E4M3 activation scales of the input of conv launch idx, branch b: records of C + 8 floats
+// (scale, 1 / scale, padding, then dq[C] on a 32-byte boundary for the epilogue's 256-bit loads)
+constexpr int FP8_REC_PAD = 8;
+size_t fp8_rec(const conet_s* h, int idx, int b) { return ((size_t)idx * h->nb + b) * (size_t)(h->C + FP8_REC_PAD); }
 float* fp8_scale(const conet_s* h, int idx, int b) { return h->fp8_act + fp8_rec(h, idx, b); }
 float* fp8_qinv(const conet_s* h, int idx, int b) { return h->fp8_act + fp8_rec(h, idx, b) + 1; }
-float* fp8_dq(const conet_s* h, int idx, int b) { return h->fp8_act + fp8_rec(h, idx, b) + 4; }
+float* fp8_dq(const conet_s* h, int idx, int b) { return h->fp8_act + fp8_rec(h, idx, b) + FP8_REC_PAD; }
 unsigned* fp8_amax(const conet_s* h, int idx, int b) { return h->fp8_amax + (size_t)idx * h->nb + b; }
 
 }  // namespace
@@ -383,9 +385,9 @@ int tc_setup(conet_s* h) {
   const int n = tc_n_convs(h);
   if (kind == 2) {
     CONET_TRY(dev_alloc_t(h, &h->fp8_wscale, ws));
-    CONET_TRY(dev_alloc_t(h, &h->fp8_act, (size_t)n * h->nb * (h->C + 4)));
+    CONET_TRY(dev_alloc_t(h, &h->fp8_act, (size_t)n * h->nb * (h->C + FP8_REC_PAD)));
     CONET_TRY(dev_alloc_t(h, &h->fp8_amax, (size_t)n * h->nb));
-    CONET_CUDA(cudaMemset(h->fp8_act, 0, (size_t)n * h->nb * (h->C + 4) * sizeof(float)));
+    CONET_CUDA(cudaMemset(h->fp8_act, 0, (size_t)n * h->nb * (h->C + FP8_REC_PAD) * sizeof(float)));
   }
   CONET_TRY(dev_alloc_t(h, &h->d_err, 1));
   CONET_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));

@@ -78,7 +78,7 @@ struct conet_s {
   // E4M3 path
   float* fp8_wscale = nullptr;               // per conv: [Cout] per-output-channel weight scales
   std::map<size_t, size_t> fp8_ws_off;       // master offset -> offset in fp8_wscale
-  float* fp8_act = nullptr;                  // per conv launch and branch: scale, 1/scale, pad, dq[C]
+  float* fp8_act = nullptr;                  // per conv launch and branch: scale, 1/scale, pad to 8, dq[C]
   unsigned* fp8_amax = nullptr;              // per conv launch and branch: largest |input| (float bits)
   bool fp8_calibrated = false;               // activation scales valid for the current weights
   float fp8_margin = 2.f;                    // scale = margin * amax / 448
