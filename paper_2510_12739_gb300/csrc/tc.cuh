@@ -9,13 +9,21 @@
 namespace conet {
 namespace tc {
 
-// Polls of mbarrier.try_wait before a wait gives up (each poll may itself suspend for
-// a hardware-defined interval); a stuck pipeline then reports CONET_ERR_TIMEOUT instead of
-// hanging the GPU.
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+// A wait gives up after WAIT_NS of wall-clock time (the %globaltimer nanosecond clock), so
+// a stuck pipeline reports CONET_ERR_TIMEOUT instead of hanging the GPU.  Between polls the
+// waiting thread is suspended for up to WAIT_HINT_NS (or until the phase completes), so
+// idle producer / issuer warps do not take issue slots from the epilogue warps.
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr uint32_t WAIT_HINT_NS = 100000u;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -47,11 +55,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait that may suspend the thread for up to hint_ns while the phase is incomplete.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity; on timeout records `where` in *err
 // (first writer wins) and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int where) {
-  for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait_suspend(bar, parity, WAIT_HINT_NS)) return true;
+    if (globaltimer_ns() - t0 > WAIT_NS) break;
+  }
   atomicCAS(err, 0, where);
   return false;
 }
