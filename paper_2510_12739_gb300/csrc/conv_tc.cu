@@ -70,8 +70,16 @@ __host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row
 constexpr int HALO_ROWS = TILE_M + 8;   // smem rows reserved for a halo box (a whole swizzle atom)
 __host__ __device__ constexpr int kc_min(int kind) { return 32 / elt_of(kind); }   // one MMA K step
 
-__host__ __device__ constexpr int tc_plan(int kind, int nb, int cin, int cout, bool want_halo) {
-  // returns KC for the requested stage shape, 0 if none fits
+// Branch groups per tile: 1 when two accumulator sets of all branches fit in TMEM's 512
+// columns; else 2 when half the branches double-buffer and a COUT-column stash for the
+// running Hadamard product still fits (4 branches x 96 channels: 2 x 192 + 96 = 480).
+__host__ __device__ constexpr int tc_groups(int nb, int cout) {
+  return 2 * pow2_ceil(nb * cout) <= 512 ? 1 : (nb % 2 == 0 && nb * cout + cout <= 512 ? 2 : 1);
+}
+
+__host__ __device__ constexpr int tc_plan(int kind, int nb_all, int cin, int cout, bool want_halo) {
+  // returns KC for the requested stage shape, 0 if none fits; a stage holds one branch group
+  const int nb = nb_all / tc_groups(nb_all, cout);
   for (int row = 128; row >= 32; row >>= 1) {
     const int kc = row / elt_of(kind);
     if (kc < kc_min(kind) || cin % kc) continue;
@@ -102,12 +110,16 @@ struct Cfg {
   static constexpr int B_PART = TAPS * COUT * ROW;
   static constexpr int A_BYTES = NSPLIT * A_PART;
   static constexpr int B_BYTES = NSPLIT * B_PART;
-  static constexpr int STAGE_TX = NB * NSPLIT * (A_BOX * ROW + B_PART);
-  static constexpr int STAGE = (int)stage_bytes(KIND, NB, COUT, ROW, HALO ? HALO_ROWS : TILE_M, TAPS);
+  static constexpr int NG = tc_groups(NB, COUT);       // branch groups per tile
+  static constexpr int G = NB / NG;                     // branches per MMA unit (one stage holds G)
+  static constexpr int STAGE_TX = G * NSPLIT * (A_BOX * ROW + B_PART);
+  static constexpr int STAGE = (int)stage_bytes(KIND, G, COUT, ROW, HALO ? HALO_ROWS : TILE_M, TAPS);
   static constexpr int K_ITERS = (9 / TAPS) * (CIN / KC);
-  static constexpr int COLS = pow2_ceil(NB * COUT);
-  static constexpr int N_ACC = 2 * COLS <= 512 ? 2 : 1;
-  static constexpr int TMEM_COLS = N_ACC * COLS;
+  static constexpr int COLS = NG == 1 ? pow2_ceil(NB * COUT) : G * COUT;   // stride of accumulator sets
+  static constexpr int N_ACC = NG == 1 ? (2 * COLS <= 512 ? 2 : 1) : 2;
+  static constexpr int STASH = NG == 1 ? 0 : 2 * G * COUT;                 // running-product columns
+  static constexpr int TMEM_COLS = NG == 1 ? N_ACC * COLS : 512;
+  static_assert(NG == 1 || STASH + COUT <= 512, "TMEM columns for the product stash");
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR_BYTES) / STAGE);
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR_BYTES;
@@ -165,9 +177,10 @@ __device__ __forceinline__ void stg8(float* p, const float (&x)[8]) {
 
 // v_b = acc_b (x dq_b on the E4M3 path) + bias_b (+ resid_b) for the 8 channels of chunk j
 // of every branch (add = false: the raw TMEM columns, when an earlier pass wrote v back).
+// (Branches b0 .. b0 + NB - 1, accumulators at TMEM columns 0, COUT, ... from tacc.)
 template <int KIND, int NB, int COUT>
-__device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, int j, bool valid, long long m,
-                                           float (&v)[NB][CW], bool add) {
+__device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, int b0, int j, bool valid,
+                                           long long m, float (&v)[NB][CW], bool add) {
   uint32_t r[NB][CW];
 #pragma unroll
   for (int b = 0; b < NB; ++b) tc::tmem_ld8_nowait(tacc + (uint32_t)(b * COUT + CW * j), r[b]);
@@ -181,19 +194,28 @@ __device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, i
   for (int b = 0; b < NB; ++b) {
     float x[CW];
     if constexpr (KIND == 2) {
-      ldg8(a.dq[b] + CW * j, x);
+      ldg8(a.dq[b0 + b] + CW * j, x);
 #pragma unroll
       for (int c = 0; c < CW; ++c) v[b][c] *= x[c];
     }
-    ldg8(a.bias[b] + CW * j, x);
+    ldg8(a.bias[b0 + b] + CW * j, x);
 #pragma unroll
     for (int c = 0; c < CW; ++c) v[b][c] += x[c];
-    if (a.resid[b] && valid) {
-      ldg8(a.resid[b] + m * COUT + CW * j, x);
+    if (a.resid[b0 + b] && valid) {
+      ldg8(a.resid[b0 + b] + m * COUT + CW * j, x);
 #pragma unroll
       for (int c = 0; c < CW; ++c) v[b][c] += x[c];
     }
   }
+}
+
+// One 8-column chunk of a single TMEM column range (the product stash).
+__device__ __forceinline__ void tmem_get8(uint32_t taddr, float (&x)[CW]) {
+  uint32_t r[CW];
+  tc::tmem_ld8_nowait(taddr, r);
+  tc::tmem_wait_ld();
+#pragma unroll
+  for (int c = 0; c < CW; ++c) x[c] = __uint_as_float(r[c]);
 }
 
 // Round to the nearest TF32 value (10 explicit mantissa bits; low 13 bits zero).
@@ -274,7 +296,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
     for (int j = j_lo; j < j_hi; ++j) {
       float v[NB][CW];
       __syncwarp();
-      load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v, true);
+      load_chunk<KIND, NB, COUT>(a, tacc, 0, j, valid, m, v, true);
       __syncwarp();   // tcgen05.st is warp-collective: reconverge after the per-row residual loads
 #pragma unroll
       for (int b = 0; b < NB; ++b) tc::tmem_st8_nowait(tacc + (uint32_t)(b * COUT + CW * j), v[b]);
@@ -356,7 +378,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
   for (int j = j_lo; j < j_hi; ++j) {
     float v[NB][CW];
     __syncwarp();
-    load_chunk<KIND, NB, COUT>(a, tacc, j, valid, m, v, add2);
+    load_chunk<KIND, NB, COUT>(a, tacc, 0, j, valid, m, v, add2);
     const int c0 = CW * j;
     // rows past the grid edge compute on don't-care values and store nothing
 #pragma unroll
@@ -479,6 +501,288 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
   }
 }
 
+// Epilogue of branch group g (branches g*G .. g*G + G - 1) of a tile whose branches are
+// computed G at a time: the MMAs of one group overlap the epilogue of the previous one, and
+// TMEM columns [tstash, tstash + COUT) carry the running Hadamard product from group to
+// group.  Per-branch work (bias, residual, pre-activation, the branches' own LayerNorms and
+// outputs) happens in the branch's group; branch 0's output -- the fused, normalised
+// product x_0 -- is formed in the last group (in group 0 when this layer does not fuse),
+// which also accumulates the head.  Statistics are merged across the lane quarter's parts
+// as in tc_epilogue.  Fused layers have pre-activation none or ReLU, so the product can be
+// formed in the statistics pass.
+template <int KIND, int NB, int COUT, int G>
+__device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t tacc, uint32_t tstash, int g,
+                                                  bool valid, long long m, int part, int quarter, int lane,
+                                                  float* scr_all) {
+  constexpr int QMAX = HEAD_QMAX;
+  constexpr int NG = NB / G;
+  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+  int j_lo, n_ch;
+  part_chunks<COUT>(part, j_lo, n_ch);
+  const int j_hi = j_lo + n_ch;
+  const int b0 = g * G;
+  const bool first = g == 0, last = g == NG - 1;
+  const bool pre_ln = a.pre == 2;
+  const bool fuse = a.fuse != 0;
+  const bool fuse_ln = fuse && a.lnf_g != nullptr;
+  const bool main_here = fuse ? last : first;   // the group that forms branch 0's output
+  bool any_b = false;
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) any_b = any_b || pre_ln || a.post[b0 + bb] == 2;
+  const bool prod_stats = last && fuse_ln;
+  const bool stats = any_b || prod_stats;
+
+  float mean_b[G], rstd_b[G], mean_p = 0.f, rstd_p = 1.f;
+  if (stats) {
+    float k_b[G], s1_b[G], s2_b[G], k_p = 0.f, s1_p = 0.f, s2_p = 0.f;
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb) k_b[bb] = s1_b[bb] = s2_b[bb] = 0.f;
+    for (int j = j_lo; j < j_hi; ++j) {
+      float v[G][CW];
+      __syncwarp();
+      load_chunk<KIND, G, COUT>(a, tacc, b0, j, valid, m, v, true);
+      __syncwarp();
+#pragma unroll
+      for (int bb = 0; bb < G; ++bb) tc::tmem_st8_nowait(tacc + (uint32_t)(bb * COUT + CW * j), v[bb]);
+      if (a.pre == 1) {
+#pragma unroll
+        for (int bb = 0; bb < G; ++bb)
+#pragma unroll
+          for (int c = 0; c < CW; ++c) v[bb][c] = fmaxf(v[bb][c], 0.f);
+      }
+      if (j == j_lo) {
+#pragma unroll
+        for (int bb = 0; bb < G; ++bb) k_b[bb] = v[bb][0];
+      }
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+#pragma unroll
+        for (int bb = 0; bb < G; ++bb) {
+          const float d = v[bb][c] - k_b[bb];
+          s1_b[bb] += d;
+          s2_b[bb] = fmaf(d, d, s2_b[bb]);
+        }
+      }
+      if (fuse) {
+        float q[CW];
+        if (first) {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) q[c] = 1.f;
+        } else {
+          tmem_get8(tstash + (uint32_t)(CW * j), q);
+        }
+#pragma unroll
+        for (int c = 0; c < CW; ++c)
+#pragma unroll
+          for (int bb = 0; bb < G; ++bb) q[c] *= v[bb][c];
+        if (prod_stats) {
+          if (j == j_lo) k_p = q[0];
+#pragma unroll
+          for (int c = 0; c < CW; ++c) {
+            const float d = q[c] - k_p;
+            s1_p += d;
+            s2_p = fmaf(d, d, s2_p);
+          }
+        }
+        tc::tmem_st8_nowait(tstash + (uint32_t)(CW * j), q);
+      }
+    }
+    __syncwarp();
+    tc::tmem_wait_st();
+    const float n_mine = (float)(CW * n_ch);
+#pragma unroll
+    for (int s = 0; s <= G; ++s) {
+      const float k = s < G ? k_b[s] : k_p, s1 = s < G ? s1_b[s] : s1_p, s2 = s < G ? s2_b[s] : s2_p;
+      const float m1 = n_ch ? s1 / n_mine : 0.f;
+      scr[(2 * s) * 32 + lane] = k + m1;
+      scr[(2 * s + 1) * 32 + lane] = fmaxf(s2 - s1 * m1, 0.f);
+    }
+    named_barrier(1 + quarter, 32 * EPI_PARTS);
+#pragma unroll
+    for (int s = 0; s <= G; ++s) {
+      float n = 0.f, mu = 0.f, M2 = 0.f;
+#pragma unroll
+      for (int pp = 0; pp < EPI_PARTS; ++pp) {
+        int f0, cnt;
+        part_chunks<COUT>(pp, f0, cnt);
+        const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+        chan_fold(n, mu, M2, (float)(CW * cnt), o[(2 * s) * 32 + lane], o[(2 * s + 1) * 32 + lane]);
+      }
+      const float rs = rsqrtf(M2 / (float)COUT + 1e-5f);
+      if (s < G) {
+        mean_b[s] = mu;
+        rstd_b[s] = rs;
+      } else {
+        mean_p = mu;
+        rstd_p = rs;
+      }
+    }
+    named_barrier(1 + quarter, 32 * EPI_PARTS);
+  }
+
+  float hq[QMAX];
+#pragma unroll
+  for (int qq = 0; qq < QMAX; ++qq) hq[qq] = 0.f;
+  float amx_b[G], amx0 = 0.f;
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) amx_b[bb] = 0.f;
+  for (int j = j_lo; j < j_hi; ++j) {
+    float v[G][CW];
+    __syncwarp();
+    load_chunk<KIND, G, COUT>(a, tacc, b0, j, valid, m, v, !stats);
+    const int c0 = CW * j;
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb)
+      if (valid && a.t_out[b0 + bb]) stg8(a.t_out[b0 + bb] + m * COUT + c0, v[bb]);
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb) {
+      if (a.pre == 1) {
+#pragma unroll
+        for (int c = 0; c < CW; ++c) v[bb][c] = fmaxf(v[bb][c], 0.f);
+      } else if (pre_ln) {
+        float gm[CW], be[CW];
+        ldg8(a.ln2_g[b0 + bb] + c0, gm);
+        ldg8(a.ln2_b[b0 + bb] + c0, be);
+        const float mu = mean_b[bb], rs = rstd_b[bb];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) v[bb][c] = fmaxf((v[bb][c] - mu) * rs * gm[c] + be[c], 0.f);
+      }
+    }
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb)
+      if (valid && a.a_out[b0 + bb]) stg8(a.a_out[b0 + bb] + m * COUT + c0, v[bb]);
+    // x_0: the fused product (from the stash when the statistics pass formed it), normalised
+    float x0[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) x0[c] = 0.f;
+    if (fuse) {
+      __syncwarp();
+      if (stats) {
+        if (last) tmem_get8(tstash + (uint32_t)c0, x0);
+      } else {
+        float q[CW];
+        if (first) {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) q[c] = 1.f;
+        } else {
+          tmem_get8(tstash + (uint32_t)c0, q);
+        }
+#pragma unroll
+        for (int c = 0; c < CW; ++c)
+#pragma unroll
+          for (int bb = 0; bb < G; ++bb) q[c] *= v[bb][c];
+        if (last) {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) x0[c] = q[c];
+        } else {
+          __syncwarp();
+          tc::tmem_st8_nowait(tstash + (uint32_t)c0, q);
+        }
+      }
+      if (last && fuse_ln) {
+        float gm[CW], be[CW];
+        ldg8(a.lnf_g + c0, gm);
+        ldg8(a.lnf_b + c0, be);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) x0[c] = (x0[c] - mean_p) * rstd_p * gm[c] + be[c];
+      }
+    } else if (first) {
+#pragma unroll
+      for (int c = 0; c < CW; ++c) x0[c] = v[0][c];
+    }
+    // outputs: the group's branches other than branch 0, then branch 0 where it is formed
+#pragma unroll
+    for (int bb = 0; bb <= G; ++bb) {
+      const bool is_main = bb == G;
+      const int b = is_main ? 0 : b0 + bb;
+      if (is_main ? !main_here : b == 0) continue;
+      const float(&y)[CW] = is_main ? x0 : v[bb < G ? bb : 0];
+      if (valid && a.xs_out[b] && !a.measure) stg8(a.xs_out[b] + m * COUT + c0, y);
+      if (!a.nx_out[b]) continue;
+      float o[CW];
+      if (a.post[b] == 2) {
+        float gm[CW], be[CW];
+        ldg8(a.ln1_g[b] + c0, gm);
+        ldg8(a.ln1_b[b] + c0, be);
+        const float mu = mean_b[bb < G ? bb : 0], rs = rstd_b[bb < G ? bb : 0];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) o[c] = fmaxf((y[c] - mu) * rs * gm[c] + be[c], 0.f);
+      } else if (a.post[b] == 1) {
+#pragma unroll
+        for (int c = 0; c < CW; ++c) o[c] = fmaxf(y[c], 0.f);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CW; ++c) o[c] = y[c];
+      }
+      if constexpr (KIND == 2) {
+        if (a.amax[b] && valid) {
+          float& mx = is_main ? amx0 : amx_b[bb < G ? bb : 0];
+#pragma unroll
+          for (int c = 0; c < CW; ++c) mx = fmaxf(mx, fabsf(o[c]));
+        }
+        if (valid && !a.measure)
+          store8_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, __ldg(a.qinv[b]));
+      } else if constexpr (KIND == 1) {
+        float lo[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const float hi = tf32_round(o[c]);
+          lo[c] = o[c] - hi;
+          o[c] = hi;
+        }
+        if (valid) {
+          stg8(reinterpret_cast<float*>(a.nx_out[b]) + m * COUT + c0, o);
+          stg8(a.nx_lo[b] + m * COUT + c0, lo);
+        }
+      } else if constexpr (KIND == 3) {
+        if (valid) store8_h(reinterpret_cast<__half*>(a.nx_out[b]) + m * COUT + c0, o);
+      } else {
+        if (valid) store8_h(reinterpret_cast<__nv_bfloat16*>(a.nx_out[b]) + m * COUT + c0, o);
+      }
+    }
+    if (main_here && a.head_w) {
+#pragma unroll
+      for (int qq = 0; qq < QMAX; ++qq) {
+        if (qq >= a.Q) break;
+        float hw[CW];
+        ldg8(a.head_w + qq * COUT + c0, hw);
+        float sacc = 0.f;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) sacc = fmaf(hw[c], x0[c], sacc);
+        hq[qq] += sacc;
+      }
+    }
+  }
+  __syncwarp();
+  tc::tmem_wait_st();
+  if constexpr (KIND == 2) {
+#pragma unroll
+    for (int bb = 0; bb <= G; ++bb) {
+      const bool is_main = bb == G;
+      const int b = is_main ? 0 : b0 + bb;
+      if ((is_main ? !main_here : b == 0) || !a.amax[b]) continue;
+      float mx = is_main ? amx0 : amx_b[bb < G ? bb : 0];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx > 0.f) atomicMax(a.amax[b], __float_as_uint(mx));
+    }
+  }
+  if (main_here && a.head_w) {
+    __syncwarp();
+    for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) scr[qq * 32 + lane] = hq[qq];
+    named_barrier(5 + quarter, 32 * EPI_PARTS);
+    if (part == 0 && valid && !a.measure) {
+      for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) {
+        float sum = 0.f;
+#pragma unroll
+        for (int pp = 0; pp < EPI_PARTS; ++pp)
+          sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
+        a.llr[m * a.Q + qq] = sum + __ldg(a.head_b + qq);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void decode_tile(int tile, int T, int nfb, int& slot, int& t, int& fb) {
   fb = tile % nfb;
   const int st = tile / nfb;
@@ -548,7 +852,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
 #pragma unroll
     for (int i = 0; i < 8; ++i) used[i] = false;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x) {
+    for (int unit = blockIdx.x * K::NG; ok && unit < a.n_tiles * K::NG;
+         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1) {
+      const int tile = unit / K::NG, g0 = (unit % K::NG) * K::G;   // tile and its branch group
       int slot, t, fb;
       decode_tile(tile, a.T, a.nfb, slot, t, fb);
       for (int k = 0; k < K::K_ITERS; ++k) {
@@ -565,9 +871,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         const int tap0 = HALO ? 3 * grp : grp;
         uint8_t* st = smem + (size_t)s * K::STAGE;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          uint8_t* ab = st + b * K::A_BYTES;
-          uint8_t* bb = st + NB * K::A_BYTES + b * K::B_BYTES;
+        for (int i = 0; i < K::G; ++i) {
+          const int b = g0 + i;
+          uint8_t* ab = st + i * K::A_BYTES;
+          uint8_t* bb = st + K::G * K::A_BYTES + i * K::B_BYTES;
           tc::tma_load_4d(ab, &maps.a[b], &full[s], ch, f0, t + dt, slot);
           tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap0);
           if constexpr (K::NSPLIT == 2) {
@@ -592,7 +899,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
     uint32_t ph = 0;
     int it = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x, ++it) {
+    for (int unit = blockIdx.x * K::NG; ok && unit < a.n_tiles * K::NG;
+         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1, ++it) {
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
       if (!tc::mbar_wait(&tempty[acc], aph ^ 1u, err, 2)) break;
@@ -606,7 +914,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         tc::fence_after_sync();
         const uint32_t st = tc::smem_u32(smem + (size_t)s * K::STAGE);
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
+        for (int b = 0; b < K::G; ++b) {
 #pragma unroll
           for (int d = 0; d < K::TAPS; ++d) {
 #pragma unroll
@@ -615,7 +923,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
               // function of the shared-memory address, so a whole-row shift of the
               // descriptor's start selects the shifted rows
               const uint32_t aa = st + b * K::A_BYTES + d * K::ROW + 32 * j;
-              const uint32_t ba = st + NB * K::A_BYTES + b * K::B_BYTES + d * COUT * K::ROW + 32 * j;
+              const uint32_t ba = st + K::G * K::A_BYTES + b * K::B_BYTES + d * COUT * K::ROW + 32 * j;
               const uint64_t ad = tc::smem_desc(aa, K::ROW);
               const uint64_t bd = tc::smem_desc(ba, K::ROW);
               tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, bd, K::IDESC, (k | d | j) != 0);
@@ -643,10 +951,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
     const bool prefetcher = warp == 2 && lane == 0;
     if (prefetcher) prefetch_resid<NB, COUT>(a, blockIdx.x);
     int it = 0;
-    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+    for (int unit = blockIdx.x * K::NG; unit < a.n_tiles * K::NG;
+         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1, ++it) {
+      const int tile = unit / K::NG, g = unit % K::NG;
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
-      if (prefetcher) prefetch_resid<NB, COUT>(a, tile + gridDim.x);
+      if (prefetcher && g == 0) prefetch_resid<NB, COUT>(a, tile + gridDim.x);
       const bool got = tc::mbar_wait(&tfull[acc], aph, err, 4);
       if (!barrier_all(1 + q, 32 * EPI_PARTS, got)) break;
       tc::fence_after_sync();
@@ -655,8 +965,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       const int f = fb * TILE_M + row;
       const bool valid = f < a.F;
       const long long m = ((long long)slot * a.T + t) * a.F + f;
-      const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + ((uint32_t)(32 * q) << 16);
-      tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m, part, q, lane, scr_all);
+      const uint32_t lanes = (uint32_t)(32 * q) << 16;
+      const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + lanes;
+      if constexpr (K::NG == 1)
+        tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m, part, q, lane, scr_all);
+      else
+        tc_epilogue_group<KIND, NB, COUT, K::G>(a, tacc, tbase + (uint32_t)K::STASH + lanes, g, valid, m, part, q,
+                                                lane, scr_all);
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[acc]);
@@ -691,6 +1006,10 @@ int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
 }  // namespace
 
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
+  // the branch-group epilogue forms the fused product in its statistics pass and gives the
+  // fused branch 0 no LayerNorm of its own
+  if (a.fuse && (a.pre == 2 || (tc_groups(nb, cout) > 1 && a.post[0] == 2)))
+    return fail(CONET_ERR_UNSUPPORTED, "fused layer with a LayerNorm pre-activation or a normalised fused branch");
 #define TC_CASE(KI, NBV, CI, CO)                                                                          \
   if (kind == KI && nb == NBV && cin == CI && cout == CO)                                                  \
     return launch_tc_t<KI, NBV, CI, CO, tc_kc(KI, NBV, CI, CO), tc_halo(KI, NBV, CI, CO)>(maps, a, s);
