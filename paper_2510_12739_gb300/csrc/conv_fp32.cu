@@ -7,7 +7,8 @@
 // Each thread accumulates an 8 x 8 register tile: REs {4r..4r+3, 64+4r..64+4r+3} and
 // channels {4c..4c+3, Cout/2+4c..Cout/2+4c+3}.  Splitting both sets in halves makes every
 // 8-thread shared-memory phase read one contiguous 128-byte row (no bank conflicts) while
-// one k step costs four 128-bit loads for 64 FFMAs.
+// one k step costs four 128-bit loads for 64 FMAs, issued as 32 packed two-lane FP32 FMAs
+// (fma.rn.f32x2: each lane rounds exactly like fmaf, so results equal the scalar form).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -17,6 +18,22 @@ namespace {
 
 constexpr int TM = 128;   // REs per CTA
 constexpr int HM = TM / 2;
+
+// (lo, hi) as one 64-bit register pair, and back.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// d.lo += a.lo * b.lo, d.hi += a.hi * b.hi, each a fused multiply-add rounded to nearest.
+__device__ __forceinline__ void fma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
 
 template <int CIN, int COUT, int KC>
 __global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_kernel(ConvArgs a) {
@@ -97,11 +114,11 @@ __global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_k
     }
   };
 
-  float acc[8][8];
+  unsigned long long acc2[8][4];   // acc2[i][p] = (acc[i][2p], acc[i][2p + 1])
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int p = 0; p < 4; ++p) acc2[i][p] = 0ull;
 
   load_chunk(0);
   store_chunk(0);
@@ -118,17 +135,24 @@ __global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_k
       const float4 b0 = *reinterpret_cast<const float4*>(Bb + k * COUT + cg * 4);
       const float4 b1 = *reinterpret_cast<const float4*>(Bb + k * COUT + HC + cg * 4);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const unsigned long long bp[4] = {pack2(b0.x, b0.y), pack2(b0.z, b0.w), pack2(b1.x, b1.y), pack2(b1.z, b1.w)};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i) {
+        const unsigned long long ad = pack2(av[i], av[i]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int p = 0; p < 4; ++p) fma2(acc2[i][p], ad, bp[p]);
+      }
     }
     if (c + 1 < NCH) store_chunk(buf ^ 1);
     __syncthreads();
   }
 
   // ---------------------------------------------------------------- epilogue
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) unpack2(acc2[i][p], acc[i][2 * p], acc[i][2 * p + 1]);
   const float* __restrict__ bias = a.bias[br];
   const float* __restrict__ resid = a.resid[br];
   float* __restrict__ out0 = a.out0[br];
