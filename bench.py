@@ -184,6 +184,28 @@ def reference_arm(args, rank, world):
     return 0
 
 
+RANK_SLOT_STRIDE = 1_000_000   # slot ids of rank r start at r * RANK_SLOT_STRIDE (disjoint shards)
+
+
+def rank_slot0(rank: int) -> int:
+    return rank * RANK_SLOT_STRIDE
+
+
+def max_over_ranks(v: float, dist=None, device="cpu") -> float:
+    """The largest v over all ranks (the job's step time is its slowest rank's)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 class Ctx:
     def __init__(self, rank, world, local, dist):
         import torch
@@ -197,11 +219,7 @@ class Ctx:
             self.dist.barrier()
 
     def max_over_ranks(self, v):
-        if self.dist is None:
-            return v
-        t = self.torch.tensor([v], device="cuda")
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, self.dist, "cuda")
 
     def timed(self, fn, steps):
         """Per-step CUDA-event times on the launch stream, L2 flushed between steps."""
@@ -254,7 +272,7 @@ def measure_inference(ctx, w, B, steps, warmup, clocks=False, e2e=False):
     rx = api.Receiver(net, precision=w.precision, max_batch=B)
     rx.init_he(0)
     mask, _ = api.pilots(net)
-    s = api.sim_generate(net, w.sim, 1, ctx.rank * 1_000_000, B)     # each rank its own slots
+    s = api.sim_generate(net, w.sim, 1, rank_slot0(ctx.rank), B)     # each rank its own slots
     Y, bits, nv = s["Y"], s["bits"], s["noise_var"]
     llr = torch.empty((B, T, F, Q), device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -290,7 +308,7 @@ def measure_inference(ctx, w, B, steps, warmup, clocks=False, e2e=False):
     roof = roofline_of(w, net, B, rx, steps, n_sm)
     rx.profile_enable(False)
     rx.sync()
-    out = {"value": B * ctx.world / (ms / 1e3), "ms_per_step": ms, "roofline": roof, "gpu_launches": n_launch,
+    out = {"value": job_rate(B, ctx.world, ms), "ms_per_step": ms, "roofline": roof, "gpu_launches": n_launch,
            "clocks": clk, "step_ms": {"min": min(times), "max": max(times)}}
     if e2e:
         Y_h = Y.cpu().pin_memory()
@@ -312,7 +330,7 @@ def measure_inference(ctx, w, B, steps, warmup, clocks=False, e2e=False):
         torch.cuda.synchronize()
         ctx.barrier()
         ms_e2e = ctx.max_over_ranks(statistics.mean(ctx.timed(e2e_step, steps)))
-        out["e2e"] = {"value": B * ctx.world / (ms_e2e / 1e3), "unit": "slots/s",
+        out["e2e"] = {"value": job_rate(B, ctx.world, ms_e2e), "unit": "slots/s",
                       "h2d_bytes_per_step": int(Y.nbytes + nv.nbytes),
                       "d2h_bytes_per_step": int(llr.nbytes + cnt.nbytes)}
     rx.close()
@@ -329,17 +347,17 @@ def measure_training(ctx, w, steps, warmup):
     it = [0]
 
     def step():
-        rx.train_step(w.sim, 7, ctx.rank * 1_000_000 + it[0], B, 1e-3, want_loss=False)
+        rx.train_step(w.sim, 7, rank_slot0(ctx.rank) + it[0], B, 1e-3, want_loss=False)
         it[0] += 1
 
     for _ in range(warmup):
         step()
     rx.sync()
     times = ctx.timed(step, steps)
-    loss = rx.train_step(w.sim, 7, ctx.rank * 1_000_000 + it[0], B, 1e-3, want_loss=True)
+    loss = rx.train_step(w.sim, 7, rank_slot0(ctx.rank) + it[0], B, 1e-3, want_loss=True)
     ms = ctx.max_over_ranks(statistics.mean(times))
     rx.close()
-    return {"value": B * ctx.world / (ms / 1e3), "unit": "train slots/s", "ms_per_step": ms,
+    return {"value": job_rate(B, ctx.world, ms), "unit": "train slots/s", "ms_per_step": ms,
             "precision": w.precision, "loss_after": loss}
 
 
