@@ -30,17 +30,14 @@ namespace conet {
 namespace {
 
 constexpr int TILE_M = 128;
-constexpr int EPI_PARTS = 3;                      // epilogue warps per TMEM lane quarter (channel parts)
-constexpr int EPI_WARPS = 4 * EPI_PARTS;
-constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int CW = 8;                             // accumulator columns per epilogue chunk
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 constexpr int HEAD_QMAX = 8;
 // Per epilogue warp: shared scratch used in turn for the LayerNorm moment exchange
 // ((NB + 1) x 2 x 32 floats) and the head's partial sums (HEAD_QMAX x 32 floats).
 constexpr int SCR_WARP_FLOATS = 320;
-constexpr size_t SCR_BYTES = (size_t)EPI_WARPS * SCR_WARP_FLOATS * sizeof(float);
 static_assert((4 + 1) * 2 * 32 <= SCR_WARP_FLOATS && HEAD_QMAX * 32 <= SCR_WARP_FLOATS, "epilogue scratch");
+__host__ __device__ constexpr size_t scr_bytes(int ep) { return (size_t)4 * ep * SCR_WARP_FLOATS * sizeof(float); }
 
 __host__ __device__ constexpr int pow2_ceil(int x) {
   int p = 32;
@@ -57,8 +54,8 @@ __host__ __device__ constexpr size_t stage_bytes(int kind, int nb, int cout, int
   return ((size_t)nb * nsplit_of(kind) * ((size_t)a_rows * row + (size_t)taps * cout * row) + 1023) / 1024 * 1024;
 }
 
-__host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row, int a_rows, int taps) {
-  return (int)((SMEM_LIMIT - 1024 - 256 - SCR_BYTES) /
+__host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row, int a_rows, int taps, int ep) {
+  return (int)((SMEM_LIMIT - 1024 - 256 - scr_bytes(ep)) /
                stage_bytes(kind, nb, cout, row, a_rows, taps));
 }
 
@@ -73,17 +70,29 @@ __host__ __device__ constexpr int kc_min(int kind) { return 32 / elt_of(kind); }
 // Branch groups per tile: 1 when two accumulator sets of all branches fit in TMEM's 512
 // columns; else 2 when half the branches double-buffer and a COUT-column stash for the
 // running Hadamard product still fits (4 branches x 96 channels: 2 x 192 + 96 = 480).
-__host__ __device__ constexpr int tc_groups(int nb, int cout) {
-  return 2 * pow2_ceil(nb * cout) <= 512 ? 1 : (nb % 2 == 0 && nb * cout + cout <= 512 ? 2 : 1);
+// Split TF32 runs 3-branch networks one branch at a time: a one-branch stage takes
+// operand rows twice as long, which its TMA-bound main loop needs (measured: +10 %; the
+// 16-bit and E4M3 paths are faster as one group).
+__host__ __device__ constexpr int tc_groups(int kind, int nb, int cout) {
+  return kind == 1 && nb == 3 ? 3
+         : 2 * pow2_ceil(nb * cout) <= 512 ? 1
+                                            : (nb % 2 == 0 && nb * cout + cout <= 512 ? 2 : 1);
 }
+
+// Epilogue warps per TMEM lane quarter (channel parts): 3 (14 warps, up to 128 registers
+// each); 4 for the branch-group epilogue, whose smaller per-thread state fits the 96
+// registers of 18 warps.
+__host__ __device__ constexpr int epi_parts(int kind, int nb, int cout) { return tc_groups(kind, nb, cout) > 1 ? 4 : 3; }
 
 __host__ __device__ constexpr int tc_plan(int kind, int nb_all, int cin, int cout, bool want_halo) {
   // returns KC for the requested stage shape, 0 if none fits; a stage holds one branch group
-  const int nb = nb_all / tc_groups(nb_all, cout);
+  const int nb = nb_all / tc_groups(kind, nb_all, cout);
+  const int ep = epi_parts(kind, nb_all, cout);
   for (int row = 128; row >= 32; row >>= 1) {
     const int kc = row / elt_of(kind);
     if (kc < kc_min(kind) || cin % kc) continue;
-    if (want_halo ? stages_fit(kind, nb, cout, row, HALO_ROWS, 3) >= 3 : stages_fit(kind, nb, cout, row, TILE_M, 1) >= 2)
+    if (want_halo ? stages_fit(kind, nb, cout, row, HALO_ROWS, 3, ep) >= 3
+                  : stages_fit(kind, nb, cout, row, TILE_M, 1, ep) >= 2)
       return kc;
   }
   return 0;
@@ -110,7 +119,7 @@ struct Cfg {
   static constexpr int B_PART = TAPS * COUT * ROW;
   static constexpr int A_BYTES = NSPLIT * A_PART;
   static constexpr int B_BYTES = NSPLIT * B_PART;
-  static constexpr int NG = tc_groups(NB, COUT);       // branch groups per tile
+  static constexpr int NG = tc_groups(KIND, NB, COUT); // branch groups per tile
   static constexpr int G = NB / NG;                     // branches per MMA unit (one stage holds G)
   static constexpr int STAGE_TX = G * NSPLIT * (A_BOX * ROW + B_PART);
   static constexpr int STAGE = (int)stage_bytes(KIND, G, COUT, ROW, HALO ? HALO_ROWS : TILE_M, TAPS);
@@ -120,9 +129,13 @@ struct Cfg {
   static constexpr int STASH = NG == 1 ? 0 : 2 * G * COUT;                 // running-product columns
   static constexpr int TMEM_COLS = NG == 1 ? N_ACC * COLS : 512;
   static_assert(NG == 1 || STASH + COUT <= 512, "TMEM columns for the product stash");
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR_BYTES) / STAGE);
+  static constexpr int EP = epi_parts(KIND, NB, COUT);  // channel parts per lane quarter
+  static constexpr int EPI_WARPS = 4 * EP;
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr size_t SCR = scr_bytes(EP);
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR) / STAGE);
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR_BYTES;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR;
   static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT);   // BF16 / TF32 / F16, E4M3
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
   static_assert(COUT % 16 == 0 && COUT <= 256 && COUT % CW == 0, "MMA N");
@@ -256,9 +269,9 @@ __device__ __forceinline__ void store8_e4m3(uint8_t* p, const float (&x)[8], flo
 }
 
 // Chunks [first, first + count) of COUT / CW owned by channel part p (near-equal split).
-template <int COUT>
+template <int COUT, int EP>
 __device__ __forceinline__ void part_chunks(int p, int& first, int& count) {
-  constexpr int CH = COUT / CW, base = CH / EPI_PARTS, rem = CH % EPI_PARTS;
+  constexpr int CH = COUT / CW, base = CH / EP, rem = CH % EP;
   first = p * base + (p < rem ? p : rem);
   count = base + (p < rem ? 1 : 0);
 }
@@ -271,13 +284,13 @@ __device__ __forceinline__ void part_chunks(int p, int& first, int& count) {
 // residual-added) values back into TMEM.  Pass 2 applies the pre-activation, the Hadamard
 // fusion and its LayerNorm, writes the residual stream and the next conv's input, and
 // accumulates the head's partial sums, which part 0 reduces through the scratch.
-template <int KIND, int NB, int COUT>
+template <int KIND, int NB, int COUT, int EP>
 __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, bool valid, long long m, int part,
                                             int quarter, int lane, float* scr_all) {
   constexpr int QMAX = HEAD_QMAX;
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
   int j_lo, n_ch;
-  part_chunks<COUT>(part, j_lo, n_ch);
+  part_chunks<COUT, EP>(part, j_lo, n_ch);
   const int j_hi = j_lo + n_ch;
   const bool pre_ln = a.pre == 2;
   const bool fuse_ln = a.fuse && a.lnf_g != nullptr;
@@ -346,14 +359,14 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
       scr[(2 * s) * 32 + lane] = k + m1;
       scr[(2 * s + 1) * 32 + lane] = fmaxf(s2 - s1 * m1, 0.f);
     }
-    named_barrier(1 + quarter, 32 * EPI_PARTS);
+    named_barrier(1 + quarter, 32 * EP);
 #pragma unroll
     for (int s = 0; s <= NB; ++s) {
       float n = 0.f, mu = 0.f, M2 = 0.f;
 #pragma unroll
-      for (int pp = 0; pp < EPI_PARTS; ++pp) {
+      for (int pp = 0; pp < EP; ++pp) {
         int f0, cnt;
-        part_chunks<COUT>(pp, f0, cnt);
+        part_chunks<COUT, EP>(pp, f0, cnt);
         const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
         chan_fold(n, mu, M2, (float)(CW * cnt), o[(2 * s) * 32 + lane], o[(2 * s + 1) * 32 + lane]);
       }
@@ -366,7 +379,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
         rstd_p = rs;
       }
     }
-    named_barrier(1 + quarter, 32 * EPI_PARTS);   // scratch free for the stores
+    named_barrier(1 + quarter, 32 * EP);   // scratch free for the stores
   }
 
   float hq[QMAX];
@@ -488,12 +501,12 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
   if (a.head_w) {
     __syncwarp();
     for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) scr[qq * 32 + lane] = hq[qq];
-    named_barrier(5 + quarter, 32 * EPI_PARTS);
+    named_barrier(5 + quarter, 32 * EP);
     if (part == 0 && valid && !a.measure) {
       for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) {
         float sum = 0.f;
 #pragma unroll
-        for (int pp = 0; pp < EPI_PARTS; ++pp)
+        for (int pp = 0; pp < EP; ++pp)
           sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
         a.llr[m * a.Q + qq] = sum + __ldg(a.head_b + qq);
       }
@@ -510,7 +523,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
 // which also accumulates the head.  Statistics are merged across the lane quarter's parts
 // as in tc_epilogue.  Fused layers have pre-activation none or ReLU, so the product can be
 // formed in the statistics pass.
-template <int KIND, int NB, int COUT, int G>
+template <int KIND, int NB, int COUT, int G, int EP>
 __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t tacc, uint32_t tstash, int g,
                                                   bool valid, long long m, int part, int quarter, int lane,
                                                   float* scr_all) {
@@ -518,7 +531,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
   constexpr int NG = NB / G;
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
   int j_lo, n_ch;
-  part_chunks<COUT>(part, j_lo, n_ch);
+  part_chunks<COUT, EP>(part, j_lo, n_ch);
   const int j_hi = j_lo + n_ch;
   const int b0 = g * G;
   const bool first = g == 0, last = g == NG - 1;
@@ -597,14 +610,14 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
       scr[(2 * s) * 32 + lane] = k + m1;
       scr[(2 * s + 1) * 32 + lane] = fmaxf(s2 - s1 * m1, 0.f);
     }
-    named_barrier(1 + quarter, 32 * EPI_PARTS);
+    named_barrier(1 + quarter, 32 * EP);
 #pragma unroll
     for (int s = 0; s <= G; ++s) {
       float n = 0.f, mu = 0.f, M2 = 0.f;
 #pragma unroll
-      for (int pp = 0; pp < EPI_PARTS; ++pp) {
+      for (int pp = 0; pp < EP; ++pp) {
         int f0, cnt;
-        part_chunks<COUT>(pp, f0, cnt);
+        part_chunks<COUT, EP>(pp, f0, cnt);
         const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
         chan_fold(n, mu, M2, (float)(CW * cnt), o[(2 * s) * 32 + lane], o[(2 * s + 1) * 32 + lane]);
       }
@@ -617,7 +630,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
         rstd_p = rs;
       }
     }
-    named_barrier(1 + quarter, 32 * EPI_PARTS);
+    named_barrier(1 + quarter, 32 * EP);
   }
 
   float hq[QMAX];
@@ -770,12 +783,12 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
   if (main_here && a.head_w) {
     __syncwarp();
     for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) scr[qq * 32 + lane] = hq[qq];
-    named_barrier(5 + quarter, 32 * EPI_PARTS);
+    named_barrier(5 + quarter, 32 * EP);
     if (part == 0 && valid && !a.measure) {
       for (int qq = 0; qq < a.Q && qq < QMAX; ++qq) {
         float sum = 0.f;
 #pragma unroll
-        for (int pp = 0; pp < EPI_PARTS; ++pp)
+        for (int pp = 0; pp < EP; ++pp)
           sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
         a.llr[m * a.Q + qq] = sum + __ldg(a.head_b + qq);
       }
@@ -805,9 +818,12 @@ __device__ __forceinline__ void prefetch_resid(const TcConvArgs& a, int tile) {
 }
 
 template <int KIND, int NB, int CIN, int COUT, int KC, int HALO>
-// 14 warps: at most 4 per SM sub-partition, so up to 128 registers each.
-__global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ TcMaps maps, TcConvArgs a) {
+// 2 + 4 x EP warps: 14 (at most 4 per SM sub-partition, up to 128 registers each) or 18
+// (up to 96 registers each).
+__global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS), 1)
+    conv_tc_kernel(const __grid_constant__ TcMaps maps, TcConvArgs a) {
   using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
+  constexpr int EP = K::EP;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)K::STAGES * K::STAGE);
@@ -826,7 +842,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       }
       for (int i = 0; i < 2; ++i) {
         tc::mbar_init(&tfull[i], 1);
-        tc::mbar_init(&tempty[i], EPI_WARPS);
+        tc::mbar_init(&tempty[i], K::EPI_WARPS);
       }
       tc::fence_mbar_init();
       for (int b = 0; b < NB; ++b) {
@@ -958,7 +974,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
       if (prefetcher && g == 0) prefetch_resid<NB, COUT>(a, tile + gridDim.x);
       const bool got = tc::mbar_wait(&tfull[acc], aph, err, 4);
-      if (!barrier_all(1 + q, 32 * EPI_PARTS, got)) break;
+      if (!barrier_all(1 + q, 32 * EP, got)) break;
       tc::fence_after_sync();
       int slot, t, fb;
       decode_tile(tile, a.T, a.nfb, slot, t, fb);
@@ -968,9 +984,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       const uint32_t lanes = (uint32_t)(32 * q) << 16;
       const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + lanes;
       if constexpr (K::NG == 1)
-        tc_epilogue<KIND, NB, COUT>(a, tacc, valid, m, part, q, lane, scr_all);
+        tc_epilogue<KIND, NB, COUT, EP>(a, tacc, valid, m, part, q, lane, scr_all);
       else
-        tc_epilogue_group<KIND, NB, COUT, K::G>(a, tacc, tbase + (uint32_t)K::STASH + lanes, g, valid, m, part, q,
+        tc_epilogue_group<KIND, NB, COUT, K::G, EP>(a, tacc, tbase + (uint32_t)K::STASH + lanes, g, valid, m, part, q,
                                                 lane, scr_all);
       tc::fence_before_sync();
       __syncwarp();
@@ -999,7 +1015,7 @@ int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
   CONET_CUDA(cudaGetDevice(&dev));
   CONET_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = a.n_tiles < n_sm ? a.n_tiles : n_sm;
-  conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO><<<grid, TC_THREADS, K::SMEM, s>>>(maps, a);
+  conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO><<<grid, K::THREADS, K::SMEM, s>>>(maps, a);
   return check_launch("conv_tc_kernel");
 }
 
@@ -1008,7 +1024,7 @@ int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
   // the branch-group epilogue forms the fused product in its statistics pass and gives the
   // fused branch 0 no LayerNorm of its own
-  if (a.fuse && (a.pre == 2 || (tc_groups(nb, cout) > 1 && a.post[0] == 2)))
+  if (a.fuse && (a.pre == 2 || (tc_groups(kind, nb, cout) > 1 && a.post[0] == 2)))
     return fail(CONET_ERR_UNSUPPORTED, "fused layer with a LayerNorm pre-activation or a normalised fused branch");
 #define TC_CASE(KI, NBV, CI, CO)                                                                          \
   if (kind == KI && nb == NBV && cin == CI && cout == CO)                                                  \
