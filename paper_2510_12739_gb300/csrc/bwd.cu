@@ -276,13 +276,24 @@ __global__ void __launch_bounds__(EW_THREADS) channel_sums_kernel(const float* _
   block_store_partials<1>(pv, C, part);
 }
 
-// out[j] (+)= sum_i part[i * n + j]
-__global__ void reduce_partials_kernel(const float* __restrict__ part, int n_part, int n, float* __restrict__ out,
-                                       int accumulate) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int i = 0; i < n_part; ++i) s += part[(size_t)i * n + j];
-    out[j] = accumulate ? out[j] + s : s;
+// out[j] (+)= sum_i part[i * n + j].  One CTA per group of 32 consecutive j: its 8 warps
+// stride the partial rows (lane = j, so every load is one coalesced row segment) and are
+// combined in a fixed order, so the sum is deterministic.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const float* __restrict__ part, int n_part, int n,
+                                                              float* __restrict__ out, int accumulate) {
+  __shared__ float red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (j < n)
+    for (int i = w; i < n_part; i += 8) s += part[(size_t)i * n + j];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && j < n) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    out[j] = accumulate ? out[j] + t : t;
   }
 }
 
@@ -431,8 +442,188 @@ int launch_channel_sums(const float* g, long long M, int C, float* part, cudaStr
 }
 
 int launch_reduce_partials(const float* part, int n_part, int n, float* out, int accumulate, cudaStream_t s) {
-  reduce_partials_kernel<<<grid_for(n, 256, 256), 256, 0, s>>>(part, n_part, n, out, accumulate);
+  reduce_partials_kernel<<<(n + 31) / 32, 256, 0, s>>>(part, n_part, n, out, accumulate);
   return check_launch("reduce_partials_kernel");
+}
+
+// Weight gradient on the FP32 FMA pipes as a split-K GEMM: one CTA per (RE range, branch)
+// computes the whole [tap][ci] x [co] block (9 CIN x COUT) of that range, each thread an
+// 8 x 8 sub-block (8 input channels of one tap x 8 output channels) with packed two-lane
+// FMAs.  REs go through shared memory in chunks of RC: the grad rows of the chunk and, per
+// symbol shift dt, the input rows m + dt F - 1 .. m + dt F + RC (the subcarrier halo),
+// with a per-RE mask of the taps whose shifted position lies in the grid (zero padding).
+// Partials go to part[split][branch][tap][ci][co], summed in a fixed order afterwards.
+namespace {
+
+constexpr int WT_RC = 64;
+
+__device__ __forceinline__ unsigned long long wt_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void wt_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ void wt_fma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__((9 * CIN / 8) * (COUT / 8)) wgrad_tiled_kernel(WgradArgs a, int S) {
+  constexpr int NT = (9 * CIN / 8) * (COUT / 8);
+  constexpr int XR = WT_RC + 2;          // input rows per symbol shift
+  constexpr int XS = CIN + 4;            // padded row (shifts rows across banks)
+  extern __shared__ float4 wt_smem4[];
+  float* xs = reinterpret_cast<float*>(wt_smem4);   // [3][XR][XS]
+  float* gs = xs + 3 * XR * XS;                     // [WT_RC][COUT]
+  int* mk = reinterpret_cast<int*>(gs + WT_RC * COUT);   // [WT_RC]
+  const int br = blockIdx.y, split = blockIdx.x, tid = threadIdx.x;
+  const int rbk = tid / (COUT / 8), cbk = tid % (COUT / 8);
+  const int tap = rbk / (CIN / 8), ci0 = (rbk % (CIN / 8)) * 8, co0 = cbk * 8;
+  const int dt = tap / 3 - 1, df = tap % 3 - 1;
+  const long long M = a.M;
+  const int T = a.T, F = a.F, TF = T * F;
+  const float* __restrict__ x = a.x[br];
+  const float* __restrict__ g = a.g[br];
+  const long long per = ((M + S - 1) / S + WT_RC - 1) / WT_RC * WT_RC;
+  const long long r0 = (long long)split * per, r1 = r0 + per < M ? r0 + per : M;
+  unsigned long long acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[i][p] = 0ull;
+  for (long long c0 = r0; c0 < r1; c0 += WT_RC) {
+    const int n = r1 - c0 < WT_RC ? (int)(r1 - c0) : WT_RC;
+    __syncthreads();
+    for (int idx = tid; idx < 3 * XR * (CIN / 4); idx += NT) {
+      const int sft = idx / (XR * (CIN / 4)), rem = idx % (XR * (CIN / 4)), i = rem / (CIN / 4), q = rem % (CIN / 4);
+      const long long row = c0 + (long long)(sft - 1) * F - 1 + i;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i <= n + 1 && row >= 0 && row < M) v = __ldg(reinterpret_cast<const float4*>(x + row * CIN) + q);
+      *reinterpret_cast<float4*>(xs + (sft * XR + i) * XS + 4 * q) = v;
+    }
+    for (int idx = tid; idx < WT_RC * (COUT / 4); idx += NT) {
+      const int i = idx / (COUT / 4), q = idx % (COUT / 4);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < n) v = __ldg(reinterpret_cast<const float4*>(g + (c0 + i) * COUT) + q);
+      *reinterpret_cast<float4*>(gs + i * COUT + 4 * q) = v;
+    }
+    for (int i = tid; i < WT_RC; i += NT) {
+      int bits = 0;
+      if (i < n) {
+        const int tf = (int)((c0 + i) % TF), t = tf / F, f = tf % F;
+#pragma unroll
+        for (int tp = 0; tp < 9; ++tp) {
+          const int tt = t + tp / 3 - 1, ff = f + tp % 3 - 1;
+          if (tt >= 0 && tt < T && ff >= 0 && ff < F) bits |= 1 << tp;
+        }
+      }
+      mk[i] = bits;
+    }
+    __syncthreads();
+    const float* xrow = xs + (dt + 1) * XR * XS + (1 + df) * XS + ci0;
+    for (int i = 0; i < n; ++i) {
+      const bool on = (mk[i] >> tap) & 1;
+      float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
+      if (on) {
+        xa = *reinterpret_cast<const float4*>(xrow + i * XS);
+        xb = *reinterpret_cast<const float4*>(xrow + i * XS + 4);
+      }
+      const float4 ga = *reinterpret_cast<const float4*>(gs + i * COUT + co0);
+      const float4 gb = *reinterpret_cast<const float4*>(gs + i * COUT + co0 + 4);
+      const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+      const unsigned long long gp[4] = {wt_pack(ga.x, ga.y), wt_pack(ga.z, ga.w), wt_pack(gb.x, gb.y),
+                                        wt_pack(gb.z, gb.w)};
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const unsigned long long xd = wt_pack(xv[r], xv[r]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) wt_fma2(acc[r][p], xd, gp[p]);
+      }
+    }
+  }
+  float* out = a.part + ((((size_t)split * a.n_br + br) * 9 + tap) * CIN + ci0) * COUT + co0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float v[8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) wt_unpack(acc[r][p], v[2 * p], v[2 * p + 1]);
+    reinterpret_cast<float4*>(out + r * COUT)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(out + r * COUT)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+template <int CIN, int COUT>
+int launch_wgrad_tiled_t(const WgradArgs& a, int S, cudaStream_t s) {
+  constexpr int NT = (9 * CIN / 8) * (COUT / 8);
+  constexpr size_t smem = (size_t)(3 * (WT_RC + 2) * (CIN + 4) + WT_RC * COUT) * sizeof(float) + WT_RC * sizeof(int);
+  static bool attr = false;
+  if (!attr) {
+    CONET_CUDA(cudaFuncSetAttribute(wgrad_tiled_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    attr = true;
+  }
+  wgrad_tiled_kernel<CIN, COUT><<<dim3(S, a.n_br), NT, smem, s>>>(a, S);
+  return check_launch("wgrad_tiled_kernel");
+}
+
+}  // namespace
+
+int wgrad_tiled_splits(long long M, int n_br) {
+  long long s = (long long)WG_TILED_MAX_CTAS / n_br;
+  const long long by_size = (M + 4 * WT_RC - 1) / (4 * WT_RC);   // >= 256 REs per split
+  if (s > by_size) s = by_size;
+  return s < 1 ? 1 : (int)s;
+}
+
+// dW[co][tap][ci] (ci < cin_src) = sum over splits k of part[k][br][tap][ci][co]: CTAs over
+// groups of 32 consecutive (tap, ci, co), 8 warps striding the splits, a fixed combine order.
+__global__ void __launch_bounds__(256) wgrad_reduce_rows_kernel(const float* __restrict__ part, int S, int n_br,
+                                                                int br, int cin, int cout, int cin_src,
+                                                                float* __restrict__ dW) {
+  __shared__ float red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = 9 * cin * cout;
+  const int j = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (j < n)
+    for (int k = w; k < S; k += 8) s += part[((size_t)k * n_br + br) * n + j];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && j < n) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    const int co = j % cout, rem = j / cout, ci = rem % cin, tap = rem / cin;
+    if (ci < cin_src) dW[((size_t)co * 9 + tap) * cin_src + ci] = t;
+  }
+}
+
+int launch_wgrad_tiled(const WgradArgs& a, cudaStream_t s) {
+  const int S = wgrad_tiled_splits(a.M, a.n_br);
+  int rc = CONET_ERR_UNSUPPORTED;
+#define WT_CASE(CI, CO) \
+  else if (a.cin == CI && a.cout == CO) rc = launch_wgrad_tiled_t<CI, CO>(a, S, s);
+  if (false) {
+  }
+  WT_CASE(8, 16)
+  WT_CASE(16, 16)
+  WT_CASE(8, 32)
+  WT_CASE(32, 32)
+  WT_CASE(8, 64)
+  WT_CASE(64, 64)
+#undef WT_CASE
+  else return launch_wgrad(a, s);   // other shapes: the general kernel
+  CONET_TRY(rc);
+  for (int b = 0; b < a.n_br; ++b) {
+    wgrad_reduce_rows_kernel<<<(9 * a.cin * a.cout + 31) / 32, 256, 0, s>>>(a.part, S, a.n_br, b, a.cin, a.cout,
+                                                                             a.cin_src[b], a.dW[b]);
+    CONET_LAUNCHED("wgrad_reduce_rows_kernel");
+  }
+  return CONET_OK;
 }
 
 int wgrad_splits(long long M, int cin, int cout, int n_br) {

@@ -108,6 +108,7 @@ int launch_fuse(const FuseArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------- backward
 constexpr int EW_PART_CTAS = 512;     // CTAs (hence partial rows) of the elementwise bwd kernels
 constexpr int WG_MAX_SPLITS = 64;
+constexpr int WG_TILED_MAX_CTAS = 152 * 6;   // split-K CTAs (all branches) of the tiled weight gradient
 
 // Hadamard fusion backward (+ post-fusion LN, + ReLU mask of the fused activations):
 // gu_0 = dp prod_{i>0} u_i,  gu_b = gxs_b + dp prod_{i!=b} u_i  (fuse), else gu_b = gx_b.
@@ -163,6 +164,11 @@ struct WgradArgs {
 int wgrad_splits(long long M, int cin, int cout, int n_br);
 size_t wgrad_partial_floats(long long M, int cin, int cout, int n_br);
 int launch_wgrad(const WgradArgs& a, cudaStream_t s);
+// The same gradient through the tiled split-K kernel where instantiated (cin, cout in
+// {8/16, 16/16, 8/32, 32/32, 8/64, 64/64}), else launch_wgrad; partials need
+// wgrad_tiled_splits(M, n_br) * n_br * 9 * cin * cout floats.
+int launch_wgrad_tiled(const WgradArgs& a, cudaStream_t s);
+int wgrad_tiled_splits(long long M, int n_br);
 
 int launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2, float eps,
                 float bc1, float bc2, cudaStream_t s);

@@ -147,8 +147,9 @@ int net_setup(conet_s* h) {
     for (int k = 0; k < 3; ++k)
       for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->G[k][b], re * h->C));
     CONET_TRY(dev_alloc_t(h, &h->ew_part, (size_t)EW_PART_CTAS * (size_t)(h->Q * h->C + h->Q + 2 * h->C)));
-    // split partials of the weight gradient, sized for the largest split count
-    const size_t wg = (size_t)WG_MAX_SPLITS * h->nb * 9 * (size_t)(h->C > h->c_pad ? h->C : h->c_pad) * h->C;
+    // split partials of the weight gradient, sized for the largest split count of either kernel
+    const size_t splits = (size_t)(WG_MAX_SPLITS * h->nb > WG_TILED_MAX_CTAS ? WG_MAX_SPLITS * h->nb : WG_TILED_MAX_CTAS);
+    const size_t wg = splits * 9 * (size_t)(h->C > h->c_pad ? h->C : h->c_pad) * h->C;
     CONET_TRY(dev_alloc_t(h, &h->wg_part, wg));
     CONET_TRY(dev_alloc_t(h, &h->sim_Y, re * h->N * 2));
     CONET_TRY(dev_alloc_t(h, &h->sim_bits, re * h->Q));
@@ -633,7 +634,7 @@ struct Bwd {
     w.F = h->F;
     w.M = M;
     prof_begin(h, PK_BACKWARD, s);
-    const int rc = launch_wgrad(w, s);
+    const int rc = launch_wgrad_tiled(w, s);
     prof_end(h, s);
     CONET_TRY(rc);
     for (int b = 0; b < h->nb; ++b) CONET_TRY(bias(g[b], b_off[b]));
