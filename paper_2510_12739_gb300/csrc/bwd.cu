@@ -17,10 +17,11 @@ namespace conet {
 
 namespace {
 
-constexpr int CPL = 4;          // channels per lane (C <= 128)
+// CPL: channels per lane, C <= 32 CPL (kernels are instantiated for CPL = 1 .. 4).
 constexpr int EW_THREADS = 256;
 constexpr int EW_WARPS = EW_THREADS / 32;
 
+template <int CPL>
 __device__ __forceinline__ void load_row(const float* __restrict__ p, long long m, int C, int lane, float (&x)[CPL]) {
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
@@ -29,6 +30,7 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, long long 
   }
 }
 
+template <int CPL>
 __device__ __forceinline__ void store_row(float* __restrict__ p, long long m, int C, int lane, const float (&x)[CPL]) {
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
@@ -40,6 +42,7 @@ __device__ __forceinline__ void store_row(float* __restrict__ p, long long m, in
 // LayerNorm backward for one RE held by a warp.  x: LN input, gy: grad wrt the LN output
 // (before the affine gain is applied, gy is the grad of y = g*xhat + b).
 // Returns dx; accumulates dgamma (gy*xhat) and dbeta (gy) in the lane's registers.
+template <int CPL>
 __device__ __forceinline__ void ln_backward(const float (&x)[CPL], const float (&gy)[CPL], const float* __restrict__ g,
                                             int C, int lane, float (&dx)[CPL], float (&dg)[CPL], float (&db)[CPL]) {
   float s = 0.f;
@@ -71,7 +74,7 @@ __device__ __forceinline__ void ln_backward(const float (&x)[CPL], const float (
 }
 
 // Block reduction of per-lane channel partials [n_vec][CPL] into part[blockIdx][n_vec * C].
-template <int NV>
+template <int NV, int CPL>
 __device__ void block_store_partials(float (&v)[NV][CPL], int C, float* __restrict__ part) {
   __shared__ float red[EW_WARPS][NV][128];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -91,6 +94,7 @@ __device__ void block_store_partials(float (&v)[NV][CPL], int C, float* __restri
   }
 }
 
+template <int CPL>
 __global__ void __launch_bounds__(EW_THREADS) fuse_bwd_kernel(FuseBwdArgs a) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -153,9 +157,10 @@ __global__ void __launch_bounds__(EW_THREADS) fuse_bwd_kernel(FuseBwdArgs a) {
       store_row(a.gu[b], m, C, lane, gu[b]);
     }
   }
-  if (a.part) block_store_partials<2>(pv, C, a.part);
+  if (a.part) block_store_partials<2, CPL>(pv, C, a.part);
 }
 
+template <int CPL>
 __global__ void __launch_bounds__(EW_THREADS) ln_relu_bwd_kernel(LnReluBwdArgs a) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -201,9 +206,10 @@ __global__ void __launch_bounds__(EW_THREADS) ln_relu_bwd_kernel(LnReluBwdArgs a
     }
     store_row(a.out, m, C, lane, out);
   }
-  if (a.part) block_store_partials<2>(pv, C, a.part);
+  if (a.part) block_store_partials<2, CPL>(pv, C, a.part);
 }
 
+template <int CPL>
 __global__ void __launch_bounds__(EW_THREADS) head_bwd_kernel(HeadBwdArgs a) {
   constexpr int QMAX = 8;
   const int lane = threadIdx.x & 31;
@@ -259,6 +265,7 @@ __global__ void __launch_bounds__(EW_THREADS) head_bwd_kernel(HeadBwdArgs a) {
   }
 }
 
+template <int CPL>
 __global__ void __launch_bounds__(EW_THREADS) channel_sums_kernel(const float* __restrict__ g, long long M, int C,
                                                                   float* __restrict__ part) {
   const int lane = threadIdx.x & 31;
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(EW_THREADS) channel_sums_kernel(const float* _
 #pragma unroll
     for (int j = 0; j < CPL; ++j) pv[0][j] += x[j];
   }
-  block_store_partials<1>(pv, C, part);
+  block_store_partials<1, CPL>(pv, C, part);
 }
 
 // out[j] (+)= sum_i part[i * n + j].  One CTA per group of 32 consecutive j: its 8 warps
@@ -421,23 +428,47 @@ __global__ void weights_dgrad_kernel(const float* __restrict__ w, int C, float* 
 int ew_grid(long long M) { return grid_for(M * 32, EW_THREADS, EW_PART_CTAS); }
 
 int launch_fuse_bwd(const FuseBwdArgs& a, cudaStream_t s) {
-  fuse_bwd_kernel<<<ew_grid(a.M), EW_THREADS, 0, s>>>(a);
+  const int cpl = (a.C + 31) / 32;
+  if (cpl < 1 || cpl > 4) return fail(CONET_ERR_UNSUPPORTED, "width %d > 128", a.C);
+  const int g = ew_grid(a.M);
+  if (cpl == 1) fuse_bwd_kernel<1><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 2) fuse_bwd_kernel<2><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 3) fuse_bwd_kernel<3><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 4) fuse_bwd_kernel<4><<<g, EW_THREADS, 0, s>>>(a);
   return check_launch("fuse_bwd_kernel");
 }
 
 int launch_ln_relu_bwd(const LnReluBwdArgs& a, cudaStream_t s) {
-  ln_relu_bwd_kernel<<<ew_grid(a.M), EW_THREADS, 0, s>>>(a);
+  const int cpl = (a.C + 31) / 32;
+  if (cpl < 1 || cpl > 4) return fail(CONET_ERR_UNSUPPORTED, "width %d > 128", a.C);
+  const int g = ew_grid(a.M);
+  if (cpl == 1) ln_relu_bwd_kernel<1><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 2) ln_relu_bwd_kernel<2><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 3) ln_relu_bwd_kernel<3><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 4) ln_relu_bwd_kernel<4><<<g, EW_THREADS, 0, s>>>(a);
   return check_launch("ln_relu_bwd_kernel");
 }
 
 int launch_head_bwd(const HeadBwdArgs& a, cudaStream_t s) {
   if (a.Q > 8) return fail(CONET_ERR_UNSUPPORTED, "Q > 8");
-  head_bwd_kernel<<<ew_grid(a.M), EW_THREADS, 0, s>>>(a);
+  const int cpl = (a.C + 31) / 32;
+  if (cpl < 1 || cpl > 4) return fail(CONET_ERR_UNSUPPORTED, "width %d > 128", a.C);
+  const int g = ew_grid(a.M);
+  if (cpl == 1) head_bwd_kernel<1><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 2) head_bwd_kernel<2><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 3) head_bwd_kernel<3><<<g, EW_THREADS, 0, s>>>(a);
+  if (cpl == 4) head_bwd_kernel<4><<<g, EW_THREADS, 0, s>>>(a);
   return check_launch("head_bwd_kernel");
 }
 
-int launch_channel_sums(const float* g, long long M, int C, float* part, cudaStream_t s) {
-  channel_sums_kernel<<<ew_grid(M), EW_THREADS, 0, s>>>(g, M, C, part);
+int launch_channel_sums(const float* gr, long long M, int C, float* part, cudaStream_t s) {
+  const int cpl = (C + 31) / 32;
+  if (cpl < 1 || cpl > 4) return fail(CONET_ERR_UNSUPPORTED, "width %d > 128", C);
+  const int g = ew_grid(M);
+  if (cpl == 1) channel_sums_kernel<1><<<g, EW_THREADS, 0, s>>>(gr, M, C, part);
+  if (cpl == 2) channel_sums_kernel<2><<<g, EW_THREADS, 0, s>>>(gr, M, C, part);
+  if (cpl == 3) channel_sums_kernel<3><<<g, EW_THREADS, 0, s>>>(gr, M, C, part);
+  if (cpl == 4) channel_sums_kernel<4><<<g, EW_THREADS, 0, s>>>(gr, M, C, part);
   return check_launch("channel_sums_kernel");
 }
 
