@@ -81,18 +81,37 @@ def quantize_weight(w):
 
 
 class E4M3Quant:
-    """Quantisation hooks for oracle.net.forward (conv inputs and conv weights)."""
+    """Quantisation hooks for oracle.net.forward (conv inputs and conv weights).
 
-    def __init__(self, margin: float = 2.0):
+    Activation scales are calibrated on the tensor each hook call sees (the whole batch),
+    or, with ``scales``, taken in call order from a list recorded by an earlier calibration
+    (``used`` records the scales of this pass, in the forward's conv order)."""
+
+    def __init__(self, margin: float = 2.0, scales=None):
         self.margin = float(margin)
+        self.scales = None if scales is None else list(scales)
+        self.used = []
 
     def act(self, x):
-        return quantize(x, pow2_scale(self.margin * np.max(np.abs(x))))
+        if self.scales is not None:
+            s = self.scales[len(self.used)]
+        else:
+            s = pow2_scale(self.margin * np.max(np.abs(x)))
+        self.used.append(s)
+        return quantize(x, s)
 
     def weight(self, w):
         return quantize_weight(w)
 
 
-def forward_fp8(cfg, flat, X0, margin: float = 2.0):
-    """LLR [B, T, F, Q] of the CoNet with E4M3 conv operands, scales calibrated on X0's batch."""
-    return onet.forward(cfg, flat, X0, quant=E4M3Quant(margin))
+def forward_fp8(cfg, flat, X0, margin: float = 2.0, scales=None):
+    """LLR [B, T, F, Q] of the CoNet with E4M3 conv operands: activation scales calibrated on
+    X0's batch, or the given ones (as calibrate_fp8 returns them)."""
+    return onet.forward(cfg, flat, X0, quant=E4M3Quant(margin, scales))
+
+
+def calibrate_fp8(cfg, flat, X0, margin: float = 2.0):
+    """Activation scales of every conv input, in forward order, calibrated on X0's batch."""
+    q = E4M3Quant(margin)
+    onet.forward(cfg, flat, X0, quant=q)
+    return q.used

@@ -16,11 +16,18 @@ def receive(cfg, params, Y, pilot_sym, pilot_mask):
     return onet.forward(cfg, params, X0)
 
 
-def receive_fp8(cfg, params, Y, pilot_sym, pilot_mask, margin: float = 2.0):
-    """receive() with E4M3 conv operands (oracle.fp8), scales calibrated on this batch."""
+def receive_fp8(cfg, params, Y, pilot_sym, pilot_mask, margin: float = 2.0, scales=None):
+    """receive() with E4M3 conv operands (oracle.fp8): scales calibrated on this batch, or
+    the given ones (from calibrate_fp8 on another batch)."""
     from . import fp8
     X0 = orx.assemble_input(Y, pilot_sym, pilot_mask)
-    return fp8.forward_fp8(cfg, params, X0, margin)
+    return fp8.forward_fp8(cfg, params, X0, margin, scales)
+
+
+def calibrate_fp8(cfg, params, Y, pilot_sym, pilot_mask, margin: float = 2.0):
+    from . import fp8
+    X0 = orx.assemble_input(Y, pilot_sym, pilot_mask)
+    return fp8.calibrate_fp8(cfg, params, X0, margin)
 
 
 def train_step(cfg, sim, params, m, v, step: int, seed: int, batch: int, lr: float):

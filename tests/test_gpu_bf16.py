@@ -174,3 +174,23 @@ def test_chunked_batch_matches_single_pass():
         single = one.forward(s["Y"][b:b + 1].contiguous(), mask)
         assert torch.equal(single[0], full[b])
     rx.sync()
+
+
+@pytest.mark.parametrize("precision", PREC)
+def test_resid_14x624_full_batch_sampled_slots(precision):
+    """The 14 x 624 residual workload at its full batch of 256 slots (the benchmark's launch
+    configuration), sampled slots against the oracle."""
+    from oracle import net as onet, pipeline
+    from paper_2510_12739_gb300 import api
+    w = WORKLOADS["resid_14x624_b256_fp32"]
+    B = w.batch
+    ref = oracle_inputs(w.net, w.sim, 4, 1000, B)
+    params = onet.init_params(w.net, 9).astype(np.float32)
+    rx = api.Receiver(w.net, precision=precision, max_batch=B)
+    rx.load_weights(params)
+    L = rx.forward(dev(ref["Y32"]), dev(ref["pilot_mask"])).cpu().numpy()
+    rx.sync()
+    for b in (0, 131, B - 1):
+        Yd = ref["Y32"][b:b + 1, ..., 0].astype(np.float64) + 1j * ref["Y32"][b:b + 1, ..., 1]
+        L_ref = pipeline.receive(w.net, params.astype(np.float64), Yd, ref["pilot_sym"], ref["pilot_mask"])
+        check_16(L[b:b + 1], L_ref, w.net, precision)

@@ -59,17 +59,17 @@ def ln_fused(net):
     return bool(net.norm or net.residual) and net.n_branches >= 2
 
 
-def check_emu(L, L_emu, net):
+def check_emu(L, L_emu, net, p99=P99_EMU_LN, med=MED_EMU):
     assert np.all(np.isfinite(L))
     scale = np.max(np.abs(L_emu))
     err = np.abs(L - L_emu) / scale
     tol = TOL_EMU
     if ln_fused(net):
-        tol = P99_EMU_LN
+        tol = p99
         assert np.quantile(err, 0.99) < tol, np.quantile(err, 0.99)
     else:
         assert err.max() < tol, err.max()
-    assert np.median(err) < MED_EMU
+    assert np.median(err) < med, np.median(err)
     sure = np.abs(L_emu) > tol * scale
     assert np.mean((L > 0)[sure] == (L_emu > 0)[sure]) >= 0.999
 
@@ -211,3 +211,62 @@ def test_fp8_interference_full_batch_sampled_slots():
     L_emu = fp8.forward_fp8(w.net, params.astype(np.float64), X0)
     for b in (0, 255, B - 1):
         check_emu(L[b:b + 1], L_emu[b:b + 1], w.net)
+
+
+def _calibrated_pair(w, B, n_cal, wseed):
+    """A handle calibrated explicitly on the first n_cal slots, then run on all B slots (the
+    workload's batch, as the benchmark runs it); the oracle's scales from the same slots."""
+    from oracle import net as onet, pipeline
+    from paper_2510_12739_gb300 import api
+    ref = oracle_inputs(w.net, w.sim, 7, 0, B)
+    params = onet.init_params(w.net, wseed).astype(np.float32)
+    rx = api.Receiver(w.net, precision="fp8", max_batch=B)
+    rx.load_weights(params)
+    Y, mask = dev(ref["Y32"]), dev(ref["pilot_mask"])
+    rx.calibrate(Y[:n_cal].contiguous(), mask, margin=2.0)
+    L = rx.forward(Y, mask).cpu().numpy()
+    rx.sync()
+    Yd = ref["Y32"][..., 0].astype(np.float64) + 1j * ref["Y32"][..., 1]
+    p64 = params.astype(np.float64)
+    scales = pipeline.calibrate_fp8(w.net, p64, Yd[:n_cal], ref["pilot_sym"], ref["pilot_mask"])
+    return L, ref, Yd, p64, scales
+
+
+def test_fp8_resid_14x624_full_batch_calibrated_on_four_slots():
+    """The 14 x 624 residual network in E4M3 at the benchmark's batch of 256, scales
+    calibrated on 4 slots: sampled slots against the emulation with the oracle's scales
+    from the same 4 slots."""
+    from oracle import pipeline
+    w = WORKLOADS["resid_14x624_b256_fp32"]
+    L, ref, Yd, p64, scales = _calibrated_pair(w, w.batch, 4, 8)
+    for b in (0, 131, w.batch - 1):
+        L_emu = pipeline.receive_fp8(w.net, p64, Yd[b:b + 1], ref["pilot_sym"], ref["pilot_mask"], scales=scales)
+        check_emu(L[b:b + 1], L_emu, w.net)
+
+
+def test_fp8_resid_14x3276_sampled_res_calibrated_on_one_slot():
+    """The 14 x 3276, 4-branch x 96 network in E4M3 (branch groups of two), B = 6, scales
+    calibrated on one slot: sampled subcarriers against the emulation on the exact
+    receptive-field crop with the oracle's scales from that slot.
+
+    This network is 17 convs deep with a LayerNorm after each of its 9 fusions.  An output's
+    receptive field holds millions of quantised values, so the rare codes that FP32 and FP64
+    round to opposite sides of a boundary are many, and their normalised effect spreads
+    over the whole distribution.  Measured on 896 LLRs: median 2.5e-4, 99th percentile
+    3.9e-2, max 7.4e-2, hard decisions all equal.  The E4M3 format's own error against FP64
+    on these networks is ~100x the median.  The bar is 1e-3 at the median and 0.1 at the
+    99th percentile."""
+    from gpu_util import receptive_radius
+    from oracle import fp8, rx as orx
+    w = WORKLOADS["resid_14x3276_b1024_bf16"]
+    L, ref, Yd, p64, scales = _calibrated_pair(w, 6, 1, 9)
+    R = receptive_radius(w.net)
+    got, want = [], []
+    for b, f in [(0, 0), (3, 1637), (5, 3275), (1, 128), (2, 2000)]:
+        lo, hi = max(0, f - R), min(w.net.n_sc, f + R + 1)
+        X0 = orx.assemble_input(Yd[b:b + 1, :, :, lo:hi], ref["pilot_sym"][:, lo:hi], ref["pilot_mask"][:, lo:hi])
+        crop = replace(w.net, n_sc=hi - lo)
+        Lc = fp8.forward_fp8(crop, p64, X0, scales=scales)
+        got.append(L[b, :, f, :])
+        want.append(Lc[0, :, f - lo, :])
+    check_emu(np.array(got), np.array(want), w.net, p99=0.1, med=1e-3)

@@ -106,3 +106,21 @@ def test_single_conv_error_bound():
     assert np.max(err) > 0                     # quantisation did happen
     # a dropped quantisation step would make the emulated conv exact
     assert np.mean(err) > 1e-4 * np.mean(np.abs(_conv(X0, w)))
+
+
+def test_recorded_scales_replay_and_count():
+    """Calibration records one scale per conv input, in forward order; replaying them on the
+    same batch reproduces the calibrated forward exactly; the input layer's scale from a
+    subset of the slots is at most the whole batch's (its amax is over fewer values)."""
+    from workloads import replace
+    net = replace(tiny_net(residual=1), depth=2)
+    p = onet.init_params(net, 3)
+    g = np.random.default_rng(4)
+    X0 = g.standard_normal((3, net.n_sym, net.n_sc, net.c_in))
+    scales = fp8.calibrate_fp8(net, p, X0)
+    n_convs = net.n_branches * (1 + 2 * net.depth)
+    assert len(scales) == n_convs
+    assert np.array_equal(fp8.forward_fp8(net, p, X0, scales=scales), fp8.forward_fp8(net, p, X0))
+    own = fp8.calibrate_fp8(net, p, X0[:1])
+    assert len(own) == n_convs
+    assert all(own[b] <= scales[b] for b in range(net.n_branches))
