@@ -37,6 +37,24 @@ constexpr int HEAD_QMAX = 8;
 // ((NB + 1) x 2 x 32 floats) and the head's partial sums (HEAD_QMAX x 32 floats).
 constexpr int SCR_WARP_FLOATS = 320;
 static_assert((4 + 1) * 2 * 32 <= SCR_WARP_FLOATS && HEAD_QMAX * 32 <= SCR_WARP_FLOATS, "epilogue scratch");
+
+// The epilogue's per-channel parameters, copied once per CTA into shared memory: every tile
+// reads all of them, and from global memory they would share the few KB of L1 left beside
+// the operand stages with the streaming residual traffic (and mostly miss).  Layout in
+// floats: the fused LayerNorm's gamma and beta, the head's [HEAD_QMAX][Cout] weights and
+// HEAD_QMAX biases, the E4M3 output scales 1 / s of up to 8 branches, then per branch its
+// bias, LN2 gamma and beta, LN1 gamma and beta and E4M3 dequantisation factors.
+enum { PF_BIAS, PF_LN2G, PF_LN2B, PF_LN1G, PF_LN1B, PF_DQ, PF_N };
+static_assert(MAX_BR <= 8, "E4M3 output scales");
+template <int COUT>
+struct ParLayout {
+  static constexpr int LNFG = 0, LNFB = COUT, HEADW = 2 * COUT, HEADB = HEADW + HEAD_QMAX * COUT,
+                       QINV = HEADB + HEAD_QMAX, BR = QINV + 8;
+  static constexpr int at(int b, int f) { return BR + (PF_N * b + f) * COUT; }
+};
+__host__ __device__ constexpr size_t par_bytes(int nb, int cout) {
+  return ((size_t)((2 + HEAD_QMAX) * cout + HEAD_QMAX + 8 + PF_N * nb * cout) * sizeof(float) + 127) / 128 * 128;
+}
 __host__ __device__ constexpr size_t scr_bytes(int ep) { return (size_t)4 * ep * SCR_WARP_FLOATS * sizeof(float); }
 
 __host__ __device__ constexpr int pow2_ceil(int x) {
@@ -54,9 +72,9 @@ __host__ __device__ constexpr size_t stage_bytes(int kind, int nb, int cout, int
   return ((size_t)nb * nsplit_of(kind) * ((size_t)a_rows * row + (size_t)taps * cout * row) + 1023) / 1024 * 1024;
 }
 
-__host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row, int a_rows, int taps, int ep) {
-  return (int)((SMEM_LIMIT - 1024 - 256 - scr_bytes(ep)) /
-               stage_bytes(kind, nb, cout, row, a_rows, taps));
+__host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row, int a_rows, int taps, int ep,
+                                             size_t par) {
+  return (int)((SMEM_LIMIT - 1024 - 256 - scr_bytes(ep) - par) / stage_bytes(kind, nb, cout, row, a_rows, taps));
 }
 
 // K chunk (channels per operand row) and stage shape of an instantiation.  Preferred: the
@@ -88,11 +106,12 @@ __host__ __device__ constexpr int tc_plan(int kind, int nb_all, int cin, int cou
   // returns KC for the requested stage shape, 0 if none fits; a stage holds one branch group
   const int nb = nb_all / tc_groups(kind, nb_all, cout);
   const int ep = epi_parts(kind, nb_all, cout);
+  const size_t par = par_bytes(nb_all, cout);
   for (int row = 128; row >= 32; row >>= 1) {
     const int kc = row / elt_of(kind);
     if (kc < kc_min(kind) || cin % kc) continue;
-    if (want_halo ? stages_fit(kind, nb, cout, row, HALO_ROWS, 3, ep) >= 3
-                  : stages_fit(kind, nb, cout, row, TILE_M, 1, ep) >= 2)
+    if (want_halo ? stages_fit(kind, nb, cout, row, HALO_ROWS, 3, ep, par) >= 3
+                  : stages_fit(kind, nb, cout, row, TILE_M, 1, ep, par) >= 2)
       return kc;
   }
   return 0;
@@ -133,9 +152,10 @@ struct Cfg {
   static constexpr int EPI_WARPS = 4 * EP;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr size_t SCR = scr_bytes(EP);
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR) / STAGE);
+  static constexpr size_t PAR = par_bytes(NB, COUT);
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR - PAR) / STAGE);
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR + PAR;
   static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT);   // BF16 / TF32 / F16, E4M3
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
   static_assert(COUT % 16 == 0 && COUT <= 256 && COUT % CW == 0, "MMA N");
@@ -188,12 +208,63 @@ __device__ __forceinline__ void stg8(float* p, const float (&x)[8]) {
                : "memory");
 }
 
+// 8 (or 1) parameter floats from the shared-memory copy; every lane reads the same address
+// (a broadcast).  Volatile keeps the loads after the barrier that publishes the copy.
+__device__ __forceinline__ void lds8(const float* p, float (&x)[8]) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(s));
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4 + 16];" : "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7]) : "r"(s));
+}
+
+__device__ __forceinline__ float lds1(const float* p) {
+  float x;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x) : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return x;
+}
+
+// Copy of the epilogue parameters (layout ParLayout) by threads i0, i0 + stride, ...; null
+// or unused entries read as 0.
+template <int KIND, int NB, int COUT>
+__device__ void stage_params(const TcConvArgs& a, float* par, int i0, int stride) {
+  using PL = ParLayout<COUT>;
+  constexpr int N = PL::at(NB, 0);
+  const int qn = a.Q < HEAD_QMAX ? a.Q : HEAD_QMAX;
+  for (int i = i0; i < N; i += stride) {
+    const float* src = nullptr;
+    int k = 0;
+    if (i < PL::HEADW) {
+      src = i < PL::LNFB ? a.lnf_g : a.lnf_b;
+      k = i % COUT;
+    } else if (i < PL::HEADB) {
+      k = i - PL::HEADW;
+      if (k < qn * COUT) src = a.head_w;
+    } else if (i < PL::QINV) {
+      k = i - PL::HEADB;
+      if (k < qn) src = a.head_b;
+    } else if (i < PL::BR) {
+      const int b = i - PL::QINV;
+      if (KIND == 2 && b < NB) src = a.qinv[b];
+    } else {
+      const int r = i - PL::BR, b = r / (PF_N * COUT), f = (r / COUT) % PF_N;
+      k = r % COUT;
+      src = f == PF_BIAS   ? a.bias[b]
+            : f == PF_LN2G ? a.ln2_g[b]
+            : f == PF_LN2B ? a.ln2_b[b]
+            : f == PF_LN1G ? a.ln1_g[b]
+            : f == PF_LN1B ? a.ln1_b[b]
+                           : (KIND == 2 ? a.dq[b] : nullptr);
+    }
+    par[i] = src ? src[k] : 0.f;
+  }
+}
+
 // v_b = acc_b (x dq_b on the E4M3 path) + bias_b (+ resid_b) for the 8 channels of chunk j
 // of every branch (add = false: the raw TMEM columns, when an earlier pass wrote v back).
 // (Branches b0 .. b0 + NB - 1, accumulators at TMEM columns 0, COUT, ... from tacc.)
 template <int KIND, int NB, int COUT>
-__device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, int b0, int j, bool valid,
-                                           long long m, float (&v)[NB][CW], bool add) {
+__device__ __forceinline__ void load_chunk(const TcConvArgs& a, const float* par, uint32_t tacc, int b0, int j,
+                                           bool valid, long long m, float (&v)[NB][CW], bool add) {
+  using PL = ParLayout<COUT>;
   uint32_t r[NB][CW];
 #pragma unroll
   for (int b = 0; b < NB; ++b) tc::tmem_ld8_nowait(tacc + (uint32_t)(b * COUT + CW * j), r[b]);
@@ -207,11 +278,11 @@ __device__ __forceinline__ void load_chunk(const TcConvArgs& a, uint32_t tacc, i
   for (int b = 0; b < NB; ++b) {
     float x[CW];
     if constexpr (KIND == 2) {
-      ldg8(a.dq[b0 + b] + CW * j, x);
+      lds8(par + PL::at(b0 + b, PF_DQ) + CW * j, x);
 #pragma unroll
       for (int c = 0; c < CW; ++c) v[b][c] *= x[c];
     }
-    ldg8(a.bias[b0 + b] + CW * j, x);
+    lds8(par + PL::at(b0 + b, PF_BIAS) + CW * j, x);
 #pragma unroll
     for (int c = 0; c < CW; ++c) v[b][c] += x[c];
     if (a.resid[b0 + b] && valid) {
@@ -285,9 +356,10 @@ __device__ __forceinline__ void part_chunks(int p, int& first, int& count) {
 // fusion and its LayerNorm, writes the residual stream and the next conv's input, and
 // accumulates the head's partial sums, which part 0 reduces through the scratch.
 template <int KIND, int NB, int COUT, int EP>
-__device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, bool valid, long long m, int part,
-                                            int quarter, int lane, float* scr_all) {
+__device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* par, uint32_t tacc, bool valid,
+                                            long long m, int part, int quarter, int lane, float* scr_all) {
   constexpr int QMAX = HEAD_QMAX;
+  using PL = ParLayout<COUT>;
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
   int j_lo, n_ch;
   part_chunks<COUT, EP>(part, j_lo, n_ch);
@@ -309,7 +381,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
     for (int j = j_lo; j < j_hi; ++j) {
       float v[NB][CW];
       __syncwarp();
-      load_chunk<KIND, NB, COUT>(a, tacc, 0, j, valid, m, v, true);
+      load_chunk<KIND, NB, COUT>(a, par, tacc, 0, j, valid, m, v, true);
       __syncwarp();   // tcgen05.st is warp-collective: reconverge after the per-row residual loads
 #pragma unroll
       for (int b = 0; b < NB; ++b) tc::tmem_st8_nowait(tacc + (uint32_t)(b * COUT + CW * j), v[b]);
@@ -391,7 +463,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
   for (int j = j_lo; j < j_hi; ++j) {
     float v[NB][CW];
     __syncwarp();
-    load_chunk<KIND, NB, COUT>(a, tacc, 0, j, valid, m, v, add2);
+    load_chunk<KIND, NB, COUT>(a, par, tacc, 0, j, valid, m, v, add2);
     const int c0 = CW * j;
     // rows past the grid edge compute on don't-care values and store nothing
 #pragma unroll
@@ -405,8 +477,8 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
         for (int c = 0; c < CW; ++c) v[b][c] = fmaxf(v[b][c], 0.f);
       } else if (pre_ln) {
         float g[CW], be[CW];
-        ldg8(a.ln2_g[b] + c0, g);
-        ldg8(a.ln2_b[b] + c0, be);
+        lds8(par + PL::at(b, PF_LN2G) + c0, g);
+        lds8(par + PL::at(b, PF_LN2B) + c0, be);
         const float mu = mean_b[b], rs = rstd_b[b];
 #pragma unroll
         for (int c = 0; c < CW; ++c) v[b][c] = fmaxf((v[b][c] - mu) * rs * g[c] + be[c], 0.f);
@@ -424,8 +496,8 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
       }
       if (fuse_ln) {
         float g[CW], be[CW];
-        ldg8(a.lnf_g + c0, g);
-        ldg8(a.lnf_b + c0, be);
+        lds8(par + PL::LNFG + c0, g);
+        lds8(par + PL::LNFB + c0, be);
 #pragma unroll
         for (int c = 0; c < CW; ++c) v[0][c] = (v[0][c] - mean_p) * rstd_p * g[c] + be[c];
       }
@@ -437,8 +509,8 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
         float o[CW];
         if (a.post[b] == 2) {
           float g[CW], be[CW];
-          ldg8(a.ln1_g[b] + c0, g);
-          ldg8(a.ln1_b[b] + c0, be);
+          lds8(par + PL::at(b, PF_LN1G) + c0, g);
+          lds8(par + PL::at(b, PF_LN1B) + c0, be);
           const float mu = mean_b[b], rs = rstd_b[b];
 #pragma unroll
           for (int c = 0; c < CW; ++c) o[c] = fmaxf((v[b][c] - mu) * rs * g[c] + be[c], 0.f);
@@ -455,7 +527,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
             for (int c = 0; c < CW; ++c) amx[b] = fmaxf(amx[b], fabsf(o[c]));
           }
           if (valid && !a.measure)
-            store8_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, __ldg(a.qinv[b]));
+            store8_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, lds1(par + PL::QINV + b));
         } else if constexpr (KIND == 1) {
           float lo[CW];
 #pragma unroll
@@ -480,7 +552,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
       for (int qq = 0; qq < QMAX; ++qq) {
         if (qq >= a.Q) break;
         float hw[CW];
-        ldg8(a.head_w + qq * COUT + c0, hw);
+        lds8(par + PL::HEADW + qq * COUT + c0, hw);
         float sacc = 0.f;
 #pragma unroll
         for (int c = 0; c < CW; ++c) sacc = fmaf(hw[c], v[0][c], sacc);
@@ -508,7 +580,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
 #pragma unroll
         for (int pp = 0; pp < EP; ++pp)
           sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
-        a.llr[m * a.Q + qq] = sum + __ldg(a.head_b + qq);
+        a.llr[m * a.Q + qq] = sum + lds1(par + PL::HEADB + qq);
       }
     }
   }
@@ -524,10 +596,11 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, uint32_t tacc, 
 // as in tc_epilogue.  Fused layers have pre-activation none or ReLU, so the product can be
 // formed in the statistics pass.
 template <int KIND, int NB, int COUT, int G, int EP>
-__device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t tacc, uint32_t tstash, int g,
-                                                  bool valid, long long m, int part, int quarter, int lane,
-                                                  float* scr_all) {
+__device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const float* par, uint32_t tacc,
+                                                  uint32_t tstash, int g, bool valid, long long m, int part,
+                                                  int quarter, int lane, float* scr_all) {
   constexpr int QMAX = HEAD_QMAX;
+  using PL = ParLayout<COUT>;
   constexpr int NG = NB / G;
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
   int j_lo, n_ch;
@@ -553,7 +626,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
     for (int j = j_lo; j < j_hi; ++j) {
       float v[G][CW];
       __syncwarp();
-      load_chunk<KIND, G, COUT>(a, tacc, b0, j, valid, m, v, true);
+      load_chunk<KIND, G, COUT>(a, par, tacc, b0, j, valid, m, v, true);
       __syncwarp();
 #pragma unroll
       for (int bb = 0; bb < G; ++bb) tc::tmem_st8_nowait(tacc + (uint32_t)(bb * COUT + CW * j), v[bb]);
@@ -642,7 +715,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
   for (int j = j_lo; j < j_hi; ++j) {
     float v[G][CW];
     __syncwarp();
-    load_chunk<KIND, G, COUT>(a, tacc, b0, j, valid, m, v, !stats);
+    load_chunk<KIND, G, COUT>(a, par, tacc, b0, j, valid, m, v, !stats);
     const int c0 = CW * j;
 #pragma unroll
     for (int bb = 0; bb < G; ++bb)
@@ -654,8 +727,8 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
         for (int c = 0; c < CW; ++c) v[bb][c] = fmaxf(v[bb][c], 0.f);
       } else if (pre_ln) {
         float gm[CW], be[CW];
-        ldg8(a.ln2_g[b0 + bb] + c0, gm);
-        ldg8(a.ln2_b[b0 + bb] + c0, be);
+        lds8(par + PL::at(b0 + bb, PF_LN2G) + c0, gm);
+        lds8(par + PL::at(b0 + bb, PF_LN2B) + c0, be);
         const float mu = mean_b[bb], rs = rstd_b[bb];
 #pragma unroll
         for (int c = 0; c < CW; ++c) v[bb][c] = fmaxf((v[bb][c] - mu) * rs * gm[c] + be[c], 0.f);
@@ -694,8 +767,8 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
       }
       if (last && fuse_ln) {
         float gm[CW], be[CW];
-        ldg8(a.lnf_g + c0, gm);
-        ldg8(a.lnf_b + c0, be);
+        lds8(par + PL::LNFG + c0, gm);
+        lds8(par + PL::LNFB + c0, be);
 #pragma unroll
         for (int c = 0; c < CW; ++c) x0[c] = (x0[c] - mean_p) * rstd_p * gm[c] + be[c];
       }
@@ -715,8 +788,8 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
       float o[CW];
       if (a.post[b] == 2) {
         float gm[CW], be[CW];
-        ldg8(a.ln1_g[b] + c0, gm);
-        ldg8(a.ln1_b[b] + c0, be);
+        lds8(par + PL::at(b, PF_LN1G) + c0, gm);
+        lds8(par + PL::at(b, PF_LN1B) + c0, be);
         const float mu = mean_b[bb < G ? bb : 0], rs = rstd_b[bb < G ? bb : 0];
 #pragma unroll
         for (int c = 0; c < CW; ++c) o[c] = fmaxf((y[c] - mu) * rs * gm[c] + be[c], 0.f);
@@ -734,7 +807,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
           for (int c = 0; c < CW; ++c) mx = fmaxf(mx, fabsf(o[c]));
         }
         if (valid && !a.measure)
-          store8_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, __ldg(a.qinv[b]));
+          store8_e4m3(reinterpret_cast<uint8_t*>(a.nx_out[b]) + m * COUT + c0, o, lds1(par + PL::QINV + b));
       } else if constexpr (KIND == 1) {
         float lo[CW];
 #pragma unroll
@@ -758,7 +831,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
       for (int qq = 0; qq < QMAX; ++qq) {
         if (qq >= a.Q) break;
         float hw[CW];
-        ldg8(a.head_w + qq * COUT + c0, hw);
+        lds8(par + PL::HEADW + qq * COUT + c0, hw);
         float sacc = 0.f;
 #pragma unroll
         for (int c = 0; c < CW; ++c) sacc = fmaf(hw[c], x0[c], sacc);
@@ -790,7 +863,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, uint32_t 
 #pragma unroll
         for (int pp = 0; pp < EP; ++pp)
           sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
-        a.llr[m * a.Q + qq] = sum + __ldg(a.head_b + qq);
+        a.llr[m * a.Q + qq] = sum + lds1(par + PL::HEADB + qq);
       }
     }
   }
@@ -832,6 +905,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   float* scr_all = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256);
+  float* par = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256 + K::SCR);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -852,6 +926,8 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
     }
     __syncwarp();
     tc::tmem_alloc(tmem_slot, K::TMEM_COLS);
+  } else if (warp >= 2) {
+    stage_params<KIND, NB, COUT>(a, par, threadIdx.x - 64, K::THREADS - 64);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -984,10 +1060,10 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
       const uint32_t lanes = (uint32_t)(32 * q) << 16;
       const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + lanes;
       if constexpr (K::NG == 1)
-        tc_epilogue<KIND, NB, COUT, EP>(a, tacc, valid, m, part, q, lane, scr_all);
+        tc_epilogue<KIND, NB, COUT, EP>(a, par, tacc, valid, m, part, q, lane, scr_all);
       else
-        tc_epilogue_group<KIND, NB, COUT, K::G, EP>(a, tacc, tbase + (uint32_t)K::STASH + lanes, g, valid, m, part, q,
-                                                lane, scr_all);
+        tc_epilogue_group<KIND, NB, COUT, K::G, EP>(a, par, tacc, tbase + (uint32_t)K::STASH + lanes, g, valid, m,
+                                                    part, q, lane, scr_all);
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[acc]);
