@@ -97,10 +97,13 @@ __host__ __device__ constexpr int tc_groups(int kind, int nb, int cout) {
                                             : (nb % 2 == 0 && nb * cout + cout <= 512 ? 2 : 1);
 }
 
-// Epilogue warps per TMEM lane quarter (channel parts): 3 (14 warps, up to 128 registers
-// each); 4 for the branch-group epilogue, whose smaller per-thread state fits the 96
-// registers of 18 warps.
-__host__ __device__ constexpr int epi_parts(int kind, int nb, int cout) { return tc_groups(kind, nb, cout) > 1 ? 4 : 3; }
+// Epilogue warps per TMEM lane quarter (channel parts): 4 (18 warps, up to 96 registers
+// each), except 3 (14 warps, up to 128 registers) for single-group E4M3 epilogues of three
+// or more branches, whose dequantisation state does not fit 96 registers (measured on the
+// 14x624 network: 4 parts are 5 % faster with 16-bit operands, 6 % slower with E4M3).
+__host__ __device__ constexpr int epi_parts(int kind, int nb, int cout) {
+  return tc_groups(kind, nb, cout) == 1 && kind == 2 && nb >= 3 ? 3 : 4;
+}
 
 __host__ __device__ constexpr int tc_plan(int kind, int nb_all, int cin, int cout, bool want_halo) {
   // returns KC for the requested stage shape, 0 if none fits; a stage holds one branch group
