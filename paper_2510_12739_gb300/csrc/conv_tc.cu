@@ -880,17 +880,19 @@ __device__ __forceinline__ void decode_tile(int tile, int T, int nfb, int& slot,
   slot = st / T;
 }
 
-// Start moving a tile's residual rows (contiguous: consecutive subcarriers of one symbol)
-// from HBM into L2, so that the epilogue's loads of them wait on L2 rather than on DRAM.
+// Start moving the residual rows of branches b0 .. b0 + NB - 1 of a tile (contiguous:
+// consecutive subcarriers of one symbol) from HBM into L2, so that the epilogue's loads of
+// them wait on L2 rather than on DRAM.  Issued one MMA unit ahead: earlier, part of it is
+// evicted again by the streaming traffic before use.
 template <int NB, int COUT>
-__device__ __forceinline__ void prefetch_resid(const TcConvArgs& a, int tile) {
+__device__ __forceinline__ void prefetch_resid(const TcConvArgs& a, int tile, int b0) {
   if (tile >= a.n_tiles) return;
   int slot, t, fb;
   decode_tile(tile, a.T, a.nfb, slot, t, fb);
   const int rows = a.F - fb * TILE_M < TILE_M ? a.F - fb * TILE_M : TILE_M;
   const long long m0 = ((long long)slot * a.T + t) * a.F + (long long)fb * TILE_M;
 #pragma unroll
-  for (int b = 0; b < NB; ++b)
+  for (int b = b0; b < b0 + NB; ++b)
     if (a.resid[b]) tc::prefetch_l2(a.resid[b] + m0 * COUT, (uint32_t)(rows * COUT * sizeof(float)));
 }
 
@@ -1045,14 +1047,19 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
     const int part = (warp - 2) / 4;        // which share of the channels this warp handles
     const int row = 32 * q + lane;
     const bool prefetcher = warp == 2 && lane == 0;
-    if (prefetcher) prefetch_resid<NB, COUT>(a, blockIdx.x);
+    if (prefetcher) prefetch_resid<K::G, COUT>(a, blockIdx.x, 0);
     int it = 0;
     for (int unit = blockIdx.x * K::NG; unit < a.n_tiles * K::NG;
          unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1, ++it) {
       const int tile = unit / K::NG, g = unit % K::NG;
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
-      if (prefetcher && g == 0) prefetch_resid<NB, COUT>(a, tile + gridDim.x);
+      if (prefetcher) {
+        if (g + 1 < K::NG)
+          prefetch_resid<K::G, COUT>(a, tile, (g + 1) * K::G);
+        else
+          prefetch_resid<K::G, COUT>(a, tile + gridDim.x, 0);
+      }
       const bool got = tc::mbar_wait(&tfull[acc], aph, err, 4);
       if (!barrier_all(1 + q, 32 * EP, got)) break;
       tc::fence_after_sync();
