@@ -63,13 +63,13 @@ int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int
   return CONET_OK;
 }
 
-int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int taps) {
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CONET_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const int e = (kind == 0 || kind == 3) ? 2 : kind == 1 ? 4 : 1;
   const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)cout, 9};
   const cuuint64_t strides[2] = {(cuuint64_t)cin * e, (cuuint64_t)cout * cin * e};
-  const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)cout, (cuuint32_t)taps};
+  const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)rows, (cuuint32_t)taps};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(map, dtype_of(kind), 3, const_cast<void*>(base), dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(kc * e), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -81,6 +81,10 @@ int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int c
 // Channels per K chunk and taps per stage of the instantiation for (kind, nb, cin, cout).
 int tc_chunk(int kind, int nb, int cin, int cout) { return tc_kc(kind, nb, cin, cout); }
 int tc_taps(int kind, int nb, int cin, int cout) { return tc_halo(kind, nb, cin, cout) ? 3 : 1; }
+int tc_wbox_rows(int kind, int nb, int cin, int cout) { return cout / tc_cluster(kind, nb, cin, cout); }
+int tc_wbox_taps(int kind, int nb, int cin, int cout) {
+  return tc_cluster(kind, nb, cin, cout) > 1 ? 1 : tc_taps(kind, nb, cin, cout);
+}
 
 // [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] TF32 hi and FP32 lo = w - hi
 __global__ void weights_split_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,

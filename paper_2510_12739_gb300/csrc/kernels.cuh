@@ -223,11 +223,13 @@ struct TcConvArgs {
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
 // TMA maps of one conv operand: activations [slots][T][F][C] read in boxes of kc channels x
 // (TILE_M, or TILE_M + 2 when taps == 3) subcarriers; weights [9][cout][cin] in boxes of
-// kc x cout x taps.
+// kc x rows x taps (rows = tc_wbox_rows, taps = tc_wbox_taps of the conv's shape).
 int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc, int taps);
-int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int taps);
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps);
 int tc_chunk(int kind, int nb, int cin, int cout);
 int tc_taps(int kind, int nb, int cin, int cout);
+int tc_wbox_rows(int kind, int nb, int cin, int cout);   // output channels per weight box
+int tc_wbox_taps(int kind, int nb, int cin, int cout);   // taps per weight box
 int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s);
 int launch_weights_split(const float* w, int cout, int cin_src, int cin_dst, float* hi, float* lo, cudaStream_t s);
 int launch_assemble_split(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,

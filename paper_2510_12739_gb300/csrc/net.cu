@@ -397,16 +397,17 @@ int tc_setup(conet_s* h) {
     const int cin = idx == 0 ? cin0 : h->C;
     const int kc = tc_chunk(kind, h->nb, cin, h->C);
     const int taps = tc_taps(kind, h->nb, cin, h->C);
+    const int wrows = tc_wbox_rows(kind, h->nb, cin, h->C), wtaps = tc_wbox_taps(kind, h->nb, cin, h->C);
     if (kc <= 0) return fail(CONET_ERR_UNSUPPORTED, "no tensor-core stage fits (kind %d, Cin %d, C %d)", kind, cin, h->C);
     for (int b = 0; b < h->nb; ++b) {
       const size_t woff = h->wb_off.at((size_t)tc_conv_w(h, idx, b));
       CONET_TRY(make_act_map(&h->tcmaps[idx].a[b], kind, tc_conv_in(h, idx, b), cin, h->F, h->T, h->chunk, kc, taps));
       CONET_TRY(make_weight_map(&h->tcmaps[idx].w[b], kind, static_cast<const uint8_t*>(h->wb) + woff * e, cin,
-                                h->C, kc, taps));
+                                h->C, kc, wrows, wtaps));
       if (split) {
         CONET_TRY(make_act_map(&h->tcmaps[idx].a_lo[b], kind, tc_conv_in_lo(h, idx, b), cin, h->F, h->T, h->chunk,
                                kc, taps));
-        CONET_TRY(make_weight_map(&h->tcmaps[idx].w_lo[b], kind, h->wb_lo + woff, cin, h->C, kc, taps));
+        CONET_TRY(make_weight_map(&h->tcmaps[idx].w_lo[b], kind, h->wb_lo + woff, cin, h->C, kc, wrows, wtaps));
       }
     }
   }
