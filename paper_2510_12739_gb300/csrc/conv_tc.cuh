@@ -106,7 +106,7 @@ __host__ __device__ constexpr int tc_groups(int kind, int nb, int cout) {
 // it to both, so L2 serves every weight byte once per pair.  The halves start on whole
 // swizzle atoms (Cout / 2 a multiple of 8 rows).
 __host__ __device__ constexpr int tc_cluster(int kind, int nb, int cin, int cout) {
-  return (cout / 2) % 8 == 0 ? 2 : 1;
+  return (cout / 2) % 8 == 0 ? 2 : 1;   // (clusters of four measured 4-7 % slower)
 }
 
 // Epilogue warps per TMEM lane quarter (channel parts): 4 (18 warps, up to 96 registers
@@ -166,6 +166,7 @@ struct Cfg {
   static constexpr int EP = epi_parts(KIND, NB, COUT);  // channel parts per lane quarter
   static constexpr int CL = tc_cluster(KIND, NB, CIN, COUT);   // CTAs per cluster (weight multicast)
   static constexpr int B_ROWS = COUT / CL;                      // weight rows one CTA loads per tap
+  static constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);   // every CTA of the cluster
   static constexpr int EPI_WARPS = 4 * EP;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr size_t SCR = scr_bytes(EP);
@@ -1026,9 +1027,9 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
             for (int d = 0; d < K::TAPS; ++d) {
               const int r0 = (int)rank * K::B_ROWS;
               const size_t off = (size_t)(d * COUT + r0) * K::ROW;
-              tc::tma_load_3d_mc(bb + off, &maps.w[b], &full[s], ch, r0, tap0 + d, (uint16_t)3u);
+              tc::tma_load_3d_mc(bb + off, &maps.w[b], &full[s], ch, r0, tap0 + d, K::CL_MASK);
               if constexpr (K::NSPLIT == 2)
-                tc::tma_load_3d_mc(bb + K::B_PART + off, &maps.w_lo[b], &full[s], ch, r0, tap0 + d, (uint16_t)3u);
+                tc::tma_load_3d_mc(bb + K::B_PART + off, &maps.w_lo[b], &full[s], ch, r0, tap0 + d, K::CL_MASK);
             }
           } else {
             tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap0);
@@ -1093,7 +1094,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
           }
         }
         if constexpr (K::CL > 1)
-          tc::mma_commit_mc(&empty[s], (uint16_t)3u);   // the stage holds the peer's weight half too
+          tc::mma_commit_mc(&empty[s], K::CL_MASK);   // the stage holds the other CTAs' weight parts too
         else
           tc::mma_commit(&empty[s]);
         if (++s == K::STAGES) {
