@@ -105,6 +105,28 @@ def test_plain_two_branches_with_layernorm(precision):
 
 
 @pytest.mark.parametrize("precision", PREC)
+@pytest.mark.parametrize("n_sym,pilots,B", [(3, (1,), 1), (7, (1, 5), 23)])
+def test_odd_tile_counts(precision, n_sym, pilots, B):
+    """Odd numbers of 128-RE tiles (one per symbol of a slot here).  The conv kernels run in
+    CTA pairs that share the weight loads, so a pair's second CTA then runs units past the
+    last tile (zero operands, no stores): in the first round (3 tiles) or in the second
+    persistent round (161 tiles on 152 SMs)."""
+    w = WORKLOADS["plain_14x72_b16_fp32"]
+    net = replace(w.net, n_sym=n_sym, pilot_syms=pilots, n_sc=40, depth=3, n_branches=3, width=32)
+    L, L_ref = run_16(net, w.sim, B, precision)
+    check_16(L, L_ref, net, precision)
+
+
+def test_residual_odd_tile_count():
+    """The residual network's fixed-shape epilogues on 161 tiles (7 symbols x 23 slots, one
+    tile each): the second CTA of the last active pair runs a unit past the last tile."""
+    w = WORKLOADS["resid_14x624_b256_fp32"]
+    net = replace(w.net, n_sym=7, pilot_syms=(1, 5), n_sc=37, depth=2)
+    L, L_ref = run_16(net, w.sim, 23, "bf16")
+    check_16(L, L_ref, net, "bf16")
+
+
+@pytest.mark.parametrize("precision", PREC)
 def test_residual_64_ragged(precision):
     w = WORKLOADS["resid_14x624_b256_fp32"]
     net = replace(w.net, n_sc=37)
