@@ -168,6 +168,19 @@ int conet_forward(conet_t h, const float* Y, const uint8_t* pilot_mask, const fl
                   int B, float* llr, void* stream);
 
 /*
+ * CUDA-graph replay of conet_forward (on by default for inference handles).  The first
+ * call with given (Y, pilot_mask, B, llr) pointers and batch runs eagerly; a second
+ * identical call captures its launches into a CUDA graph on an internal stream and
+ * launches it on the caller's stream; later identical calls only launch the graph, so a
+ * launch-bound small batch costs one graph launch instead of one launch per kernel.
+ * Results are identical to the eager forward: the graph runs the same kernels on the same
+ * buffers (weights loaded later are read from those buffers).  Training handles, launch
+ * profiling and an E4M3 pass that still calibrates always run eagerly; a capture that
+ * fails turns replay off for the handle.  enable = 0 turns it off (and drops the graph).
+ */
+int conet_graphs(conet_t h, int enable);
+
+/*
  * Activation scales of a CONET_FP8E4M3 handle.  Every conv input (the assembled grid and each
  * branch's activation entering each conv) is stored as E4M3 of value / s with one scale s per
  * tensor; the weights of each output channel carry their own scale (the smallest power of
@@ -308,7 +321,8 @@ int conet_profile_read(conet_t h, int kind, double* total_ms, long long* launche
  */
 int conet_sync(conet_t h, void* stream);
 
-/* Kernel launches issued by this library in this process so far (all handles). */
+/* Kernel launches issued by this library in this process so far (all handles); a replayed
+ * forward graph (conet_graphs) counts the kernels it runs. */
 unsigned long long conet_launch_count(void);
 
 /* Thread-local text of the last error (never NULL). */

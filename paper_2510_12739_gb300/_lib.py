@@ -48,6 +48,7 @@ SIGNATURES = {
     "conet_params_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
     "conet_grads_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
     "conet_forward": (I, [P, P, P, P, I, P, P]),
+    "conet_graphs": (I, [P, I]),
     "conet_calibrate": (I, [P, P, P, I, F32, P]),
     "conet_backward": (I, [P, P, I, P]),
     "conet_adam_step": (I, [P, F32, I, P]),

@@ -121,6 +121,10 @@ class Receiver:
                                   _stream(stream)))
         return llr
 
+    def graphs(self, enable: bool = True):
+        """CUDA-graph replay of repeated identical forward calls (on by default)."""
+        check(lib().conet_graphs(self.h, int(bool(enable))))
+
     def calibrate(self, Y, pilot_mask, margin: float = 2.0, stream=None):
         """E4M3 activation scales from these slots (no-op for other precisions)."""
         check(lib().conet_calibrate(self.h, _ptr(Y), _ptr(pilot_mask), Y.shape[0], margin, _stream(stream)))

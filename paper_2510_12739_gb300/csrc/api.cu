@@ -47,6 +47,9 @@ int check_launch(const char* what) {
   return check_cuda(cudaGetLastError(), what);
 }
 
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+void launch_count_add(long long n) { __atomic_add_fetch(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+
 // ------------------------------------------------------------------ parameter layout
 bool fused_at(const conet_config& c, int i) {
   if (c.resnet_baseline || c.n_branches < 2) return false;
@@ -196,6 +199,8 @@ int conet_param_count(const conet_config* cfg, size_t* n_out) {
 
 void conet_destroy(conet_t h) {
   if (!h) return;
+  net_graph_reset(h);
+  if (h->g_stream) cudaStreamDestroy(h->g_stream);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
@@ -280,7 +285,14 @@ int conet_forward(conet_t h, const float* Y, const uint8_t* pilot_mask, const fl
   (void)noise_var;
   if (!h || !Y || !pilot_mask || !llr) return fail(CONET_ERR_ARG, "NULL argument");
   if (B < 1 || B > h->cfg.max_batch) return fail(CONET_ERR_SHAPE, "B = %d outside 1..max_batch (%d)", B, h->cfg.max_batch);
-  return net_forward(h, Y, pilot_mask, B, llr, (cudaStream_t)stream);
+  return net_forward_replay(h, Y, pilot_mask, B, llr, (cudaStream_t)stream);
+}
+
+int conet_graphs(conet_t h, int enable) {
+  if (!h) return fail(CONET_ERR_ARG, "handle is NULL");
+  net_graph_reset(h);
+  h->graphs = enable != 0;
+  return CONET_OK;
 }
 
 int conet_calibrate(conet_t h, const float* Y, const uint8_t* pilot_mask, int B, float margin, void* stream) {

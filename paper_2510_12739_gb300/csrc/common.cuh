@@ -17,6 +17,10 @@ void set_error(const char* fmt, ...);
 int fail(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);
 int check_launch(const char* what);
+// The process-wide count of kernel launches (conet_launch_count), and an adjustment of it:
+// a replayed CUDA graph adds its kernels, a capture takes back the launches it recorded.
+unsigned long long launch_count();
+void launch_count_add(long long n);
 
 #define CONET_TRY(expr)            \
   do {                             \

@@ -203,6 +203,64 @@ static FuseArgs fuse_args(conet_s* h, int B) {
   return f;
 }
 
+void net_graph_reset(conet_s* h) {
+  if (h->g_exec) cudaGraphExecDestroy(h->g_exec);
+  h->g_exec = nullptr;
+  h->g_Y = h->g_mask = h->g_llr = nullptr;
+  h->g_B = 0;
+}
+
+// The forward as a replayed CUDA graph where that is sound: an inference handle, no launch
+// profiling, and (E4M3) activation scales already calibrated, since a calibrating pass
+// changes host state.  Any capture failure falls back to the eager forward for good.
+int net_forward_replay(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
+  const bool eligible = h->graphs && !h->cfg.train && !h->prof_on &&
+                        !(h->prec == CONET_FP8E4M3 && !h->fp8_calibrated);
+  if (!eligible) {
+    net_graph_reset(h);
+    return net_forward(h, Y, mask, B, llr, s);
+  }
+  const bool same = h->g_Y == Y && h->g_mask == mask && h->g_llr == llr && h->g_B == B;
+  if (same && h->g_exec) {
+    CONET_CUDA(cudaGraphLaunch(h->g_exec, s));
+    launch_count_add(h->g_kernels);
+    h->fwd_B = B;
+    return CONET_OK;
+  }
+  if (!same) {
+    net_graph_reset(h);
+    h->g_Y = Y;
+    h->g_mask = mask;
+    h->g_llr = llr;
+    h->g_B = B;
+    return net_forward(h, Y, mask, B, llr, s);
+  }
+  if (!h->g_stream) CONET_CUDA(cudaStreamCreateWithFlags(&h->g_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  const unsigned long long n0 = launch_count();
+  CONET_CUDA(cudaStreamBeginCapture(h->g_stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = net_forward(h, Y, mask, B, llr, h->g_stream);
+  const cudaError_t e = cudaStreamEndCapture(h->g_stream, &g);
+  const long long n_cap = (long long)(launch_count() - n0);
+  launch_count_add(-n_cap);   // recorded, not run
+  cudaGetLastError();
+  cudaGraphExec_t ex = nullptr;
+  const bool ok = rc == CONET_OK && e == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    net_graph_reset(h);
+    h->graphs = false;
+    return net_forward(h, Y, mask, B, llr, s);
+  }
+  h->g_exec = ex;
+  h->g_kernels = n_cap;
+  CONET_CUDA(cudaGraphLaunch(h->g_exec, s));
+  launch_count_add(h->g_kernels);
+  h->fwd_B = B;
+  return CONET_OK;
+}
+
 int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
   if (h->prec == CONET_BF16 || h->prec == CONET_FP16 || h->prec == CONET_TF32X3 || h->prec == CONET_FP8E4M3)
     return net_forward_tc(h, Y, mask, B, llr, s);

@@ -92,6 +92,17 @@ struct conet_s {
   int fwd_B = 0;
   int chunk = 1;                             // slots per pass (activation buffers hold this many)
   std::vector<void*> allocs;
+  // Inference forward replayed as a CUDA graph: the first call with a given (Y, mask, B, llr)
+  // runs eagerly, the second identical call captures its launches into a graph (on an
+  // internal stream), later identical calls launch that graph on the caller's stream.
+  bool graphs = true;                        // conet_graphs
+  cudaGraphExec_t g_exec = nullptr;
+  cudaStream_t g_stream = nullptr;           // capture stream
+  const void* g_Y = nullptr;
+  const void* g_mask = nullptr;
+  const void* g_llr = nullptr;
+  int g_B = 0;
+  long long g_kernels = 0;                   // kernel launches the graph holds
   bool prof_on = false;                      // CUDA-event timing of launches by kind
   std::vector<cudaEvent_t> prof_ev;          // 2 events per recorded launch
   std::vector<int> prof_kind;
@@ -114,6 +125,8 @@ inline int dev_alloc_t(conet_s* h, Tp** p, size_t count) {
 int net_setup(conet_s* h);
 int net_weights_changed(conet_s* h, cudaStream_t s);
 int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
+int net_forward_replay(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
+void net_graph_reset(conet_s* h);
 int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s);
 int net_adam(conet_s* h, float lr, int step, cudaStream_t s);
 int net_train_step(conet_s* h, const SimArgs& a, uint64_t step, int B, float lr, double* loss_out, cudaStream_t s);

@@ -1,0 +1,85 @@
+"""CUDA-graph replay of the inference forward (conet_graphs): repeated identical calls replay
+a captured graph and must give exactly the eager forward's LLRs, follow weight reloads (the
+graph reads the weight buffers), and still count their kernel launches."""
+import numpy as np
+import pytest
+
+from gpu_util import dev, need_gpu, oracle_inputs, torch
+from workloads import WORKLOADS, replace
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _setup(key, precision, B, **net_kw):
+    from oracle import net as onet
+    from paper_2510_12739_gb300 import api
+    w = WORKLOADS[key]
+    net = replace(w.net, **net_kw) if net_kw else w.net
+    ref = oracle_inputs(net, w.sim, 5, 0, B)
+    rng = np.random.default_rng(7)
+    p1 = onet.init_params(net, 3)
+    p1 = (p1 + 0.02 * rng.standard_normal(p1.size)).astype(np.float32)
+    p2 = (p1 + 0.05 * rng.standard_normal(p1.size)).astype(np.float32)
+    Y, mask = dev(ref["Y32"]), dev(ref["pilot_mask"])
+    llr = torch.empty((B, net.n_sym, net.n_sc, net.qam_bits), device="cuda", dtype=torch.float32)
+    return api, net, p1, p2, Y, mask, llr
+
+
+def _eager(api, net, precision, params, Y, mask, B):
+    rx = api.Receiver(net, precision=precision, max_batch=B)
+    rx.graphs(False)
+    rx.load_weights(params)
+    out = rx.forward(Y, mask).clone()
+    rx.sync()
+    return out.cpu().numpy()
+
+
+CASES = [("plain_14x72_b16_fp32", "fp32", 16, {}),
+         ("plain_14x72_b16_fp32", "bf16", 16, {}),
+         ("resid_14x624_b256_fp32", "bf16", 2, dict(n_sc=37, depth=2)),
+         ("resid_14x624_b256_fp32", "tf32x3", 2, dict(n_sc=37, depth=2)),
+         ("interf_14x72_b512_fp8", "fp8", 32, {})]
+
+
+@pytest.mark.parametrize("key,precision,B,net_kw", CASES)
+def test_replay_matches_eager_and_follows_weights(key, precision, B, net_kw):
+    from paper_2510_12739_gb300._lib import lib
+    api, net, p1, p2, Y, mask, llr = _setup(key, precision, B, **net_kw)
+    want1 = _eager(api, net, precision, p1, Y, mask, B)
+    want2 = _eager(api, net, precision, p2, Y, mask, B)
+    rx = api.Receiver(net, precision=precision, max_batch=B)
+    rx.load_weights(p1)
+    counts = []
+    for call in range(4):   # eager (E4M3: calibrating), eager, captured + replayed, replayed
+        llr.fill_(float("nan"))
+        n0 = lib().conet_launch_count()
+        rx.forward(Y, mask, llr=llr)
+        rx.sync()
+        counts.append(lib().conet_launch_count() - n0)
+        np.testing.assert_array_equal(llr.cpu().numpy(), want1, err_msg=f"call {call}")
+    # every call issues (or replays) the same kernels, the calibrating E4M3 call more
+    assert counts[-1] > 0 and counts[-1] == counts[-2], counts
+    rx.load_weights(p2)
+    for call in range(3):   # E4M3 recalibrates after new weights, then replays again
+        llr.fill_(float("nan"))
+        rx.forward(Y, mask, llr=llr)
+        rx.sync()
+        np.testing.assert_array_equal(llr.cpu().numpy(), want2, err_msg=f"reload call {call}")
+
+
+def test_new_output_buffer_runs_eagerly_then_replays():
+    api, net, p1, _, Y, mask, llr = _setup("plain_14x72_b16_fp32", "bf16", 8)
+    want = _eager(api, net, "bf16", p1, Y, mask, 8)
+    rx = api.Receiver(net, precision="bf16", max_batch=8)
+    rx.load_weights(p1)
+    other = torch.empty_like(llr)
+    for out in (llr, llr, llr, other, other, other, llr):
+        out.fill_(float("nan"))
+        rx.forward(Y, mask, llr=out)
+        rx.sync()
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
