@@ -1203,14 +1203,13 @@ int tc_mode(int kind, int nb, const TcConvArgs& a) {
 }  // namespace
 
 // Launch of one instantiated shape (used by the per-type dispatchers below): every shape
-// with its run-time epilogue (Lay<0>), and the single-group body convs of residual networks
-// (Cin = Cout, two or more branches) also with the two fixed residual-block shapes
-// (measured on the 14x624 network: E4M3 +13 %, BF16 +1 %, split TF32 +2 %; the
-// branch-group kernels of 4 x 96 channels ran 2 % slower with them and keep Lay<0>).
+// with its run-time epilogue (Lay<0>), and the body convs of residual networks (Cin = Cout,
+// two or more branches) also with the two fixed residual-block shapes (measured: 14x624
+// E4M3 +13 %, BF16 +1 %, split TF32 +2 %; 14x3276 E4M3 +22 %, BF16 +1 %).
 #define TC_CASE(KI, NBV, CI, CO)                                                                                  \
   if (kind == KI && nb == NBV && cin == CI && cout == CO) {                                                        \
     constexpr int KC_ = tc_kc(KI, NBV, CI, CO), HALO_ = tc_halo(KI, NBV, CI, CO);                                  \
-    constexpr bool BODY_ = CI == CO && NBV >= 2 && tc_groups(KI, NBV, CO) == 1;                                    \
+    constexpr bool BODY_ = CI == CO && NBV >= 2;                                                                   \
     if (BODY_ && mode == 1) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, BODY_ ? 1 : 0>(maps, a, s);            \
     if (BODY_ && mode == 2) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, BODY_ ? 2 : 0>(maps, a, s);            \
     return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, 0>(maps, a, s);                                                \
