@@ -278,23 +278,26 @@ __device__ void stage_params(const TcConvArgs& a, float* par, int i0, int stride
 }
 
 // Layer shape seen by an epilogue.  MODE 0 reads every flag and output pointer at run time;
-// MODE 1 (first conv of a residual block: LN2 + ReLU, next input only) and MODE 2 (second
-// conv of a fused residual block: residual add, fusion + LN, the stream, LN1 + ReLU of the
-// supports and ReLU of the main branch, next input) fix them at compile time, so their
-// epilogues test no absent output and take no run-time branch on the layer type.
+// MODE 1 (first conv of a residual block: LN2 + ReLU, next input only), MODE 2 (second conv
+// of a fused residual block: residual add, fusion + LN, the stream, LN1 + ReLU of the
+// supports and ReLU of the main branch, next input) and MODE 3 (input layer of a fused
+// residual network: MODE 2 with a ReLU pre-activation and no residual) fix them at compile
+// time, so their epilogues test no absent output and take no run-time branch on the layer
+// type.
 template <int MODE>
 struct Lay {
-  __device__ static bool pre_relu(const TcConvArgs& a) { return MODE == 0 && a.pre == 1; }
+  static constexpr bool FUSED = MODE == 2 || MODE == 3;
+  __device__ static bool pre_relu(const TcConvArgs& a) { return MODE == 0 ? a.pre == 1 : MODE == 3; }
   __device__ static bool pre_ln(const TcConvArgs& a) { return MODE == 0 ? a.pre == 2 : MODE == 1; }
-  __device__ static bool fuse(const TcConvArgs& a) { return MODE == 0 ? a.fuse != 0 : MODE == 2; }
+  __device__ static bool fuse(const TcConvArgs& a) { return MODE == 0 ? a.fuse != 0 : FUSED; }
   __device__ static bool fuse_ln(const TcConvArgs& a) {
-    return MODE == 0 ? (a.fuse != 0 && a.lnf_g != nullptr) : MODE == 2;
+    return MODE == 0 ? (a.fuse != 0 && a.lnf_g != nullptr) : FUSED;
   }
-  __device__ static int post(const TcConvArgs& a, int b) { return MODE == 0 ? a.post[b] : MODE == 2 ? (b == 0 ? 1 : 2) : 0; }
+  __device__ static int post(const TcConvArgs& a, int b) { return MODE == 0 ? a.post[b] : FUSED ? (b == 0 ? 1 : 2) : 0; }
   __device__ static bool resid(const TcConvArgs& a, int b) { return MODE == 0 ? a.resid[b] != nullptr : MODE == 2; }
   __device__ static bool t_out(const TcConvArgs& a, int b) { return MODE == 0 && a.t_out[b] != nullptr; }
   __device__ static bool a_out(const TcConvArgs& a, int b) { return MODE == 0 && a.a_out[b] != nullptr; }
-  __device__ static bool xs_out(const TcConvArgs& a, int b) { return MODE == 0 ? a.xs_out[b] != nullptr : MODE == 2; }
+  __device__ static bool xs_out(const TcConvArgs& a, int b) { return MODE == 0 ? a.xs_out[b] != nullptr : FUSED; }
   __device__ static bool nx_out(const TcConvArgs& a, int b) { return MODE == 0 ? a.nx_out[b] != nullptr : true; }
   __device__ static bool head(const TcConvArgs& a) { return MODE == 0 && a.head_w != nullptr; }
   __device__ static bool measure(const TcConvArgs& a) { return MODE == 0 && a.measure != 0; }
@@ -1189,29 +1192,33 @@ int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
 // The compile-time layer shape (Lay) that a launch's arguments match, 0 if none.
 int tc_mode(int kind, int nb, const TcConvArgs& a) {
   if (a.measure || a.head_w || nb < 2) return 0;
-  bool m1 = a.pre == 2 && !a.fuse, m2 = a.pre == 0 && a.fuse && a.lnf_g;
+  bool m1 = a.pre == 2 && !a.fuse, m2 = a.pre == 0 && a.fuse && a.lnf_g, m3 = a.pre == 1 && a.fuse && a.lnf_g;
   for (int b = 0; b < nb; ++b) {
     if (a.t_out[b] || a.a_out[b] || !a.nx_out[b] || a.amax[b]) return 0;
     if (kind == 1 && !a.nx_lo[b]) return 0;
     if (kind == 2 && !a.qinv[b]) return 0;
     m1 = m1 && !a.resid[b] && a.post[b] == 0 && !a.xs_out[b];
-    m2 = m2 && a.resid[b] && a.post[b] == (b == 0 ? 1 : 2) && a.xs_out[b] && (b == 0 || (a.ln1_g[b] && a.ln1_b[b]));
+    const bool fused_out = a.post[b] == (b == 0 ? 1 : 2) && a.xs_out[b] && (b == 0 || (a.ln1_g[b] && a.ln1_b[b]));
+    m2 = m2 && a.resid[b] && fused_out;
+    m3 = m3 && !a.resid[b] && fused_out;
   }
-  return m1 ? 1 : m2 ? 2 : 0;
+  return m1 ? 1 : m2 ? 2 : m3 ? 3 : 0;
 }
 
 }  // namespace
 
 // Launch of one instantiated shape (used by the per-type dispatchers below): every shape
-// with its run-time epilogue (Lay<0>), and the body convs of residual networks (Cin = Cout,
-// two or more branches) also with the two fixed residual-block shapes (measured: 14x624
-// E4M3 +13 %, BF16 +1 %, split TF32 +2 %; 14x3276 E4M3 +22 %, BF16 +1 %).
+// with its run-time epilogue (Lay<0>); the body convs of residual networks (Cin = Cout, two
+// or more branches) also with the two fixed residual-block shapes (measured: 14x624 E4M3
+// +13 %, BF16 +1 %, split TF32 +2 %; 14x3276 E4M3 +22 %, BF16 +1 %), and the input layers
+// of the 3- and 4-branch residual networks with the fixed input-layer shape.
 #define TC_CASE(KI, NBV, CI, CO)                                                                                  \
   if (kind == KI && nb == NBV && cin == CI && cout == CO) {                                                        \
     constexpr int KC_ = tc_kc(KI, NBV, CI, CO), HALO_ = tc_halo(KI, NBV, CI, CO);                                  \
-    constexpr bool BODY_ = CI == CO && NBV >= 2;                                                                   \
+    constexpr bool BODY_ = CI == CO && NBV >= 2, INPUT_ = CI != CO && NBV >= 3;                                    \
     if (BODY_ && mode == 1) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, BODY_ ? 1 : 0>(maps, a, s);            \
     if (BODY_ && mode == 2) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, BODY_ ? 2 : 0>(maps, a, s);            \
+    if (INPUT_ && mode == 3) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, INPUT_ ? 3 : 0>(maps, a, s);          \
     return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, 0>(maps, a, s);                                                \
   }
 
