@@ -114,6 +114,38 @@ __global__ void weights_bf16_kernel(const float* __restrict__ w, int cout, int c
   }
 }
 
+__global__ void weights_dgrad_bf16_kernel(const float* __restrict__ w, int C, __nv_bfloat16* __restrict__ out) {
+  const int n = 9 * C * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int in = i % C, rem = i / C, o = rem % C, tp = rem / C;
+    out[i] = __float2bfloat16_rn(w[((size_t)in * 9 + (8 - tp)) * C + o]);
+  }
+}
+
+struct GradsBf16Args {
+  const float* in[MAX_BR];
+  __nv_bfloat16* out[MAX_BR];
+};
+
+// 8 values per thread step (n a multiple of 8: rows of C = 16k channels)
+__global__ void grads_bf16_kernel(GradsBf16Args a, int nb, long long n8) {
+  const long long total = n8 * nb;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / n8);
+    const long long k = i - (long long)b * n8;
+    const float4 x0 = __ldg(reinterpret_cast<const float4*>(a.in[b]) + 2 * k);
+    const float4 x1 = __ldg(reinterpret_cast<const float4*>(a.in[b]) + 2 * k + 1);
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(x0.x, x0.y), h1 = __floats2bfloat162_rn(x0.z, x0.w);
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(x1.x, x1.y), h3 = __floats2bfloat162_rn(x1.z, x1.w);
+    uint4 o;
+    o.x = *reinterpret_cast<const uint32_t*>(&h0);
+    o.y = *reinterpret_cast<const uint32_t*>(&h1);
+    o.z = *reinterpret_cast<const uint32_t*>(&h2);
+    o.w = *reinterpret_cast<const uint32_t*>(&h3);
+    reinterpret_cast<uint4*>(a.out[b])[k] = o;
+  }
+}
+
 __global__ void weights_f16_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
                                    __half* __restrict__ out) {
   const int n = 9 * cout * cin_dst;
@@ -121,6 +153,23 @@ __global__ void weights_f16_kernel(const float* __restrict__ w, int cout, int ci
     const int ci = i % cin_dst, rem = i / cin_dst, co = rem % cout, tap = rem / cout;
     out[i] = __float2half_rn(ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f);
   }
+}
+
+int launch_weights_dgrad_bf16(const float* w, int C, void* out, cudaStream_t s) {
+  weights_dgrad_bf16_kernel<<<grid_for(9LL * C * C, 256, 512), 256, 0, s>>>(w, C,
+                                                                            static_cast<__nv_bfloat16*>(out));
+  return check_launch("weights_dgrad_bf16_kernel");
+}
+
+int launch_grads_bf16(const float* const* in, void* const* out, int nb, long long n, cudaStream_t s) {
+  if (nb < 1 || nb > MAX_BR || n % 8) return fail(CONET_ERR_UNSUPPORTED, "grads_bf16: nb %d, n %lld", nb, n);
+  GradsBf16Args a = {};
+  for (int b = 0; b < nb; ++b) {
+    a.in[b] = in[b];
+    a.out[b] = static_cast<__nv_bfloat16*>(out[b]);
+  }
+  grads_bf16_kernel<<<grid_for(n / 8 * nb, 256, 152 * 8), 256, 0, s>>>(a, nb, n / 8);
+  return check_launch("grads_bf16_kernel");
 }
 
 int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s) {

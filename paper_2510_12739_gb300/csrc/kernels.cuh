@@ -227,6 +227,11 @@ int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, cons
 int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc, int taps);
 int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps);
 int tc_chunk(int kind, int nb, int cin, int cout);
+// BF16 tensor-core dgrad operands: Wd[tap'][o][i] = W[i][8 - tap'][o] (the kernel rotated by
+// 180 degrees, input and output channels exchanged; input channel fastest) from the FP32
+// master [C][9][C]; and the BF16 copies of n values of each of nb gradient tensors.
+int launch_weights_dgrad_bf16(const float* w, int C, void* out, cudaStream_t s);
+int launch_grads_bf16(const float* const* in, void* const* out, int nb, long long n, cudaStream_t s);
 int tc_taps(int kind, int nb, int cin, int cout);
 int tc_wbox_rows(int kind, int nb, int cin, int cout);   // output channels per weight box
 int tc_wbox_taps(int kind, int nb, int cin, int cout);   // taps per weight box

@@ -144,6 +144,13 @@ int net_setup(conet_s* h) {
       wd += (size_t)9 * c.cin * c.cout;
     }
     CONET_TRY(dev_alloc_t(h, &h->wd, wd ? wd : 1));
+    h->tc_dgrad = h->prec == CONET_BF16;
+    if (h->tc_dgrad) {
+      CONET_TRY(dev_alloc(h, &h->wd16, (wd ? wd : 1) * sizeof(uint16_t)));
+      for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc(h, &h->g16[b], re * h->C * sizeof(uint16_t)));
+      CONET_TRY(dev_alloc_t(h, &h->zero_c, (size_t)h->C));
+      CONET_CUDA(cudaMemset(h->zero_c, 0, (size_t)h->C * sizeof(float)));
+    }
     for (int k = 0; k < 3; ++k)
       for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->G[k][b], re * h->C));
     CONET_TRY(dev_alloc_t(h, &h->ew_part, (size_t)EW_PART_CTAS * (size_t)(h->Q * h->C + h->Q + 2 * h->C)));
@@ -166,8 +173,13 @@ int net_weights_changed(conet_s* h, cudaStream_t s) {
   for (const auto& c : h->L.convs) {
     const int cin_dst = c.cin == h->cin ? h->c_pad : c.cin;
     CONET_TRY(launch_weights_to_tap_major(h->params + c.off, c.cout, c.cin, cin_dst, h->wt + h->wt_off.at(c.off), s));
-    if (h->cfg.train && c.cin != h->cin)
-      CONET_TRY(launch_weights_dgrad_layout(h->params + c.off, c.cout, h->wd + h->wd_off.at(c.off), s));
+    if (h->cfg.train && c.cin != h->cin) {
+      if (h->tc_dgrad)
+        CONET_TRY(launch_weights_dgrad_bf16(h->params + c.off, c.cout,
+                                            static_cast<uint16_t*>(h->wd16) + h->wd_off.at(c.off), s));
+      else
+        CONET_TRY(launch_weights_dgrad_layout(h->params + c.off, c.cout, h->wd + h->wd_off.at(c.off), s));
+    }
   }
   return tc_weights_changed(h, s);
 }
@@ -699,8 +711,49 @@ struct Bwd {
     for (int b = 0; b < h->nb; ++b) CONET_TRY(bias(g[b], b_off[b]));
     return CONET_OK;
   }
-  // data gradient of a body conv of every branch: out = conv3x3(g, rotated W)
+  // tensor maps of the BF16 dgrad conv of one layer (built on first use; host-side encoding)
+  int dg_maps_for(const long* w_off, const TcMaps** out) {
+    auto it = h->dg_index.find((size_t)w_off[0]);
+    if (it == h->dg_index.end()) {
+      TcMaps m = {};
+      const int C = h->C, nb = h->nb;
+      const int kc = tc_chunk(0, nb, C, C), taps = tc_taps(0, nb, C, C);
+      const int wrows = tc_wbox_rows(0, nb, C, C), wtaps = tc_wbox_taps(0, nb, C, C);
+      if (kc <= 0) return fail(CONET_ERR_UNSUPPORTED, "no tensor-core stage fits the dgrad conv (C %d)", C);
+      for (int b = 0; b < nb; ++b) {
+        CONET_TRY(make_act_map(&m.a[b], 0, h->g16[b], C, h->F, h->T, h->chunk, kc, taps));
+        CONET_TRY(make_weight_map(&m.w[b], 0, static_cast<const uint16_t*>(h->wd16) + h->wd_off.at((size_t)w_off[b]),
+                                  C, C, kc, wrows, wtaps));
+      }
+      h->dg_maps.push_back(m);
+      it = h->dg_index.emplace((size_t)w_off[0], h->dg_maps.size() - 1).first;
+    }
+    *out = &h->dg_maps[it->second];
+    return CONET_OK;
+  }
+  // data gradient of a body conv of every branch: out = conv3x3(g, rotated W); with BF16
+  // training on the tensor cores (BF16 operands, FP32 accumulation and output)
   int dgrad(float* const* g, const long* w_off, float* const* out) {
+    if (h->tc_dgrad) {
+      const TcMaps* maps = nullptr;
+      CONET_TRY(dg_maps_for(w_off, &maps));
+      CONET_TRY(launch_grads_bf16(g, h->g16, h->nb, M * h->C, s));
+      TcConvArgs a = {};
+      a.T = h->T;
+      a.F = h->F;
+      a.nfb = (h->F + 127) / 128;
+      a.n_tiles = (int)(M / ((long long)h->T * h->F)) * h->T * a.nfb;
+      a.Q = h->Q;
+      a.err = h->d_err;
+      for (int b = 0; b < h->nb; ++b) {
+        a.bias[b] = h->zero_c;
+        a.t_out[b] = out[b];
+      }
+      prof_begin(h, PK_BACKWARD, s);
+      const int rc = launch_conv_tc(0, h->nb, h->C, h->C, *maps, a, s);
+      prof_end(h, s);
+      return rc;
+    }
     ConvArgs c = {};
     c.M = (int)M;
     c.T = h->T;

@@ -74,6 +74,14 @@ struct conet_s {
   void* wb = nullptr;                        // BF16 weights [9][Cout][Cin_pad] per conv
   std::map<size_t, size_t> wb_off;
   std::vector<conet::TcMaps> tcmaps;         // tensor maps per conv launch
+  // BF16 training: the data gradient of each body conv runs on the tensor cores as the conv
+  // of a BF16 copy of the incoming gradient with the rotated, transposed BF16 weights
+  bool tc_dgrad = false;
+  void* wd16 = nullptr;                      // [9][Cin][Cout] per body conv, offsets wd_off
+  void* g16[conet::MAX_BR] = {};             // BF16 copies of the incoming data gradients
+  float* zero_c = nullptr;                   // C zeros: the dgrad conv has no bias
+  std::vector<conet::TcMaps> dg_maps;        // per body conv (in wd_off order)
+  std::map<size_t, size_t> dg_index;         // branch 0's conv weight offset -> dg_maps index
   int* d_err = nullptr;                      // device error word of the tensor-core kernels
   // E4M3 path
   float* fp8_wscale = nullptr;               // per conv: [Cout] per-output-channel weight scales
