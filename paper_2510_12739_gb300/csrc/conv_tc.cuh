@@ -110,11 +110,13 @@ __host__ __device__ constexpr int tc_cluster(int kind, int nb, int cin, int cout
 }
 
 // Epilogue warps per TMEM lane quarter (channel parts): 4 (18 warps, up to 96 registers
-// each), except 3 (14 warps, up to 128 registers) for single-group E4M3 epilogues of three
-// or more branches, whose dequantisation state does not fit 96 registers (measured on the
-// 14x624 network: 4 parts are 5 % faster with 16-bit operands, 6 % slower with E4M3).
+// each), or 3 (14 warps, up to 128 registers) for the single-group E4M3 epilogues of three
+// or more branches, whose dequantisation state needs the larger budget, and for the
+// branch-group epilogues (measured: 4 parts 5 % faster than 3 with 16-bit operands on the
+// 14x624 network, 6 % slower with E4M3; on the 14x3276 branch-group network 3 parts are
+// 3.5 % faster now that its epilogues have fixed layer shapes).
 __host__ __device__ constexpr int epi_parts(int kind, int nb, int cout) {
-  return tc_groups(kind, nb, cout) == 1 && kind == 2 && nb >= 3 ? 3 : 4;
+  return (tc_groups(kind, nb, cout) == 1 && kind == 2 && nb >= 3) || tc_groups(kind, nb, cout) > 1 ? 3 : 4;
 }
 
 __host__ __device__ constexpr int tc_plan(int kind, int nb_all, int cin, int cout, bool want_halo) {
