@@ -150,6 +150,12 @@ int conet_save_weights(conet_t h, float* host_params, size_t n);
 int conet_params_device(conet_t h, float** dev_params, size_t* n);
 int conet_grads_device(conet_t h, float** dev_grads, size_t* n);
 
+/* After the caller changed the master parameters in place (through conet_params_device,
+ * e.g. with its own optimiser), re-derive the kernels' weight layouts from them, on
+ * `stream`; conet_load_weights, conet_init_he and conet_adam_step do this themselves.  E4M3
+ * handles recalibrate their activation scales on the next forward. */
+int conet_params_updated(conet_t h, void* stream);
+
 /* ---------------------------------------------------------------- forward / backward */
 
 /*

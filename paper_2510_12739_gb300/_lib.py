@@ -47,6 +47,7 @@ SIGNATURES = {
     "conet_save_weights": (I, [P, P, SZ]),
     "conet_params_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
     "conet_grads_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
+    "conet_params_updated": (I, [P, P]),
     "conet_forward": (I, [P, P, P, P, I, P, P]),
     "conet_graphs": (I, [P, I]),
     "conet_calibrate": (I, [P, P, P, I, F32, P]),

@@ -112,6 +112,10 @@ class Receiver:
         check(lib().conet_grads_device(self.h, C.byref(p), C.byref(n)))
         return torch.as_tensor(_DevView(p.value, n.value, self), device="cuda")
 
+    def params_updated(self, stream=None):
+        """Re-derive the kernels' weight layouts after an in-place change of params_device()."""
+        check(lib().conet_params_updated(self.h, _stream(stream)))
+
     def forward(self, Y, pilot_mask, noise_var=None, llr=None, stream=None) -> torch.Tensor:
         B = Y.shape[0]
         if llr is None:
@@ -153,6 +157,48 @@ class Receiver:
         check(lib().conet_train_step(self.h, C.byref(make_sim(sim)), seed, step, B, lr,
                                      C.byref(loss) if want_loss else None, _stream(stream)))
         return loss.value if want_loss else None
+
+
+class CoNetFn(torch.autograd.Function):
+    """LLRs = CoNet(Y) as an autograd node over the flat master parameters.
+
+    ``params`` must be the handle's own parameter buffer (``Receiver.params_device()``, as
+    ``CoNet.weight`` holds it): the forward reads the weights from the library, not from the
+    tensor.  Forward saves only the handle (the library keeps the activations); backward
+    runs conet_backward on the incoming LLR gradient and returns a copy of the library's
+    parameter gradient.  There is no gradient with respect to Y or the pilot mask."""
+
+    @staticmethod
+    def forward(ctx, params, rx, Y, pilot_mask):
+        ctx.rx = rx
+        return rx.forward(Y, pilot_mask)
+
+    @staticmethod
+    def backward(ctx, dllr):
+        ctx.rx.backward(dllr.contiguous())
+        return ctx.rx.grads_device().clone(), None, None, None
+
+
+class CoNet(torch.nn.Module):
+    """A trainable CoNet receiver: ``weight`` is an nn.Parameter aliasing the library's FP32
+    master parameters, so ``loss.backward()`` fills ``weight.grad`` through CoNetFn.  Update
+    the weights with ``adam_step`` (the library's Adam), or change ``weight`` in place with a
+    torch optimiser and then call ``params_updated()``."""
+
+    def __init__(self, net, precision: str = "fp32", max_batch: int = 1, seed: int = 0):
+        super().__init__()
+        self.rx = Receiver(net, precision=precision, max_batch=max_batch, train=True)
+        self.rx.init_he(seed)
+        self.weight = torch.nn.Parameter(self.rx.params_device(), requires_grad=True)
+
+    def forward(self, Y, pilot_mask):
+        return CoNetFn.apply(self.weight, self.rx, Y, pilot_mask)
+
+    def adam_step(self, lr: float, step: int):
+        self.rx.adam_step(lr, step)
+
+    def params_updated(self):
+        self.rx.params_updated()
 
 
 def pilots(net, device="cuda", stream=None):

@@ -273,6 +273,11 @@ int conet_params_device(conet_t h, float** p, size_t* n) {
   return CONET_OK;
 }
 
+int conet_params_updated(conet_t h, void* stream) {
+  if (!h) return fail(CONET_ERR_ARG, "handle is NULL");
+  return net_weights_changed(h, (cudaStream_t)stream);
+}
+
 int conet_grads_device(conet_t h, float** p, size_t* n) {
   if (!h || !p || !n) return fail(CONET_ERR_ARG, "NULL argument");
   *p = h->grads;
