@@ -247,10 +247,15 @@ int net_forward_replay(conet_s* h, const float* Y, const uint8_t* mask, int B, f
     h->g_B = B;
     return net_forward(h, Y, mask, B, llr, s);
   }
-  if (!h->g_stream) CONET_CUDA(cudaStreamCreateWithFlags(&h->g_stream, cudaStreamNonBlocking));
+  if ((!h->g_stream && cudaStreamCreateWithFlags(&h->g_stream, cudaStreamNonBlocking) != cudaSuccess) ||
+      cudaStreamBeginCapture(h->g_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    net_graph_reset(h);
+    h->graphs = false;
+    return net_forward(h, Y, mask, B, llr, s);
+  }
   cudaGraph_t g = nullptr;
   const unsigned long long n0 = launch_count();
-  CONET_CUDA(cudaStreamBeginCapture(h->g_stream, cudaStreamCaptureModeThreadLocal));
   const int rc = net_forward(h, Y, mask, B, llr, h->g_stream);
   const cudaError_t e = cudaStreamEndCapture(h->g_stream, &g);
   const long long n_cap = (long long)(launch_count() - n0);
