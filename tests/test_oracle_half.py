@@ -1,0 +1,74 @@
+"""Pins of the oracle's 16-bit emulation (oracle.half): the rounding against independent
+implementations and hand-derived cases, and the forward's hook against the exact forward."""
+import numpy as np
+import pytest
+
+from oracle import half, net as onet
+from workloads import WORKLOADS, replace
+
+torch = pytest.importorskip("torch")
+
+
+def test_bf16_representable_values_are_fixed_points():
+    m = np.arange(128)
+    vals = np.concatenate([(1 + m / 128.0) * 2.0 ** e for e in range(-20, 21)])
+    vals = np.concatenate([vals, -vals, [0.0]])
+    assert np.array_equal(half.round16(vals, "bf16"), vals)
+
+
+def test_bf16_ties_to_even_hand_cases():
+    # spacing 2^-7 on [1, 2): 1 + 2^-8 lies halfway between 1 (even) and 1 + 2^-7 (odd)
+    cases = {1 + 2.0 ** -8: 1.0,
+             1 + 3 * 2.0 ** -8: 1 + 2.0 ** -6,              # between 1 + 2^-7 (odd) and 1 + 2^-6 (even)
+             1 + 2.0 ** -8 + 2.0 ** -20: 1 + 2.0 ** -7,     # just above the tie
+             -(2 + 2.0 ** -7): -2.0,                         # spacing 2^-6 on [2, 4)
+             3.0 * 2.0 ** -130: 3.0 * 2.0 ** -130}          # subnormal, exactly representable
+    for x, want in cases.items():
+        assert half.round16(x, "bf16") == want, x
+
+
+def test_bf16_matches_torch_on_float32_inputs():
+    rng = np.random.default_rng(0)
+    x = (rng.standard_normal(200_000) * np.exp(rng.uniform(-30, 30, 200_000))).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(half.round16(x.astype(np.float64), "bf16"), want)
+
+
+def test_fp16_matches_numpy_including_subnormals_and_overflow():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(200_000) * np.exp(rng.uniform(-20, 12, 200_000))
+    x = np.concatenate([x, [65504.0, 65519.9, 65520.0, 7e4, -7e4, 2.0 ** -24, 3 * 2.0 ** -26]])
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float16).astype(np.float64)
+    assert np.array_equal(half.round16(x, "fp16"), want)
+
+
+def test_rounding_error_bound():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal(100_000) * np.exp(rng.uniform(-10, 10, 100_000))
+    for fmt, bits in (("bf16", 8), ("fp16", 11)):
+        y = x[np.abs(x) > 2.0 ** -14] if fmt == "fp16" else x
+        y = y[np.abs(y) < 6e4]
+        r = half.round16(y, fmt)
+        spacing = np.ldexp(1.0, np.frexp(np.abs(y))[1] - 1 - (bits - 1))
+        assert np.all(np.abs(r - y) <= 0.5 * spacing)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_hook_rounds_only_conv_operands(fmt):
+    """With every weight and input already representable, the emulated forward is the exact
+    forward; with arbitrary ones it stays within a few 16-bit roundings of it."""
+    w = WORKLOADS["plain_14x72_b16_fp32"]
+    net = replace(w.net, n_sc=12, depth=3, width=8, n_sym=6, pilot_syms=(1, 4))
+    rng = np.random.default_rng(3)
+    flat = onet.init_params(net, 5)
+    X0 = rng.standard_normal((2, net.n_sym, net.n_sc, 2 * net.n_rx + 3))
+    exact = onet.forward(net, half.round16(flat, fmt), half.round16(X0, fmt))
+    # rounded weights and input are fixed points, so only the rounding of inner activations differs
+    L = half.forward_16(net, half.round16(flat, fmt), half.round16(X0, fmt), fmt)
+    unit = 2.0 ** -8 if fmt == "bf16" else 2.0 ** -11
+    scale = np.max(np.abs(exact))
+    assert np.max(np.abs(L - exact)) <= 20 * unit * scale
+    assert not np.array_equal(L, exact) or net.depth == 1   # inner activations were rounded
+    L_all = half.forward_16(net, flat, X0, fmt)
+    assert np.max(np.abs(L_all - onet.forward(net, flat, X0))) <= 40 * unit * np.max(np.abs(L_all))
