@@ -238,9 +238,11 @@ int conet_conv3x3_wgrad(const float* x, const float* dz, int B, int T, int F, in
  * 4.25 MiB, held by every GPU that loads the library until the process exits); a size whose
  * partials would not fit returns CONET_ERR_SHAPE (never the case for cin, cout <= 128 with
  * the library's split rule).  The first call on each device, with that device current,
- * looks up the array's device address once (cudaGetSymbolAddress): make that first call
- * before any stream capture.  All calls share the array, so calls that overlap on the GPU
- * (other streams, other host threads) race; serialise them.
+ * looks up the array's device address once (cudaGetSymbolAddress) and keeps it: make that
+ * first call before any stream capture.  The kept address is valid until the device is reset;
+ * do not call this entry point on a device after cudaDeviceReset in the same process.  All
+ * calls share the array, so calls that overlap on the GPU (other streams, other host threads)
+ * race; serialise them.
  */
 int conet_conv3x3_wgrad_noalloc(const float* x, const float* dz, int B, int T, int F, int cin, int cout,
                                 float* dW, float* db, void* stream);

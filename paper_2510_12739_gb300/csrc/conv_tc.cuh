@@ -99,16 +99,6 @@ __host__ __device__ constexpr int tc_groups(int kind, int nb, int cout) {
                                             : (nb % 2 == 0 && nb * cout + cout <= 512 ? 2 : 1);
 }
 
-// CTAs per cluster.  Every 128-RE unit needs its branches' whole 3 x 3 x Cin x Cout weights;
-// streamed from L2 for each unit they were two thirds of the operand traffic, which bounds
-// the main loop (L2 -> shared memory) and slows the epilogue's own L2 traffic.  A cluster of
-// two CTAs splits each weight box by output channels: each CTA loads one half and multicasts
-// it to both, so L2 serves every weight byte once per pair.  The halves start on whole
-// swizzle atoms (Cout / 2 a multiple of 8 rows).
-__host__ __device__ constexpr int tc_cluster(int kind, int nb, int cin, int cout) {
-  return (cout / 2) % 8 == 0 ? 2 : 1;   // (clusters of four measured 4-7 % slower)
-}
-
 // Epilogue warps per TMEM lane quarter (channel parts): 4 (18 warps, up to 96 registers
 // each), or 3 (14 warps, up to 128 registers) for the single-group E4M3 epilogues of three
 // or more branches, whose dequantisation state needs the larger budget, and for the
@@ -166,9 +156,6 @@ struct Cfg {
   static constexpr int TMEM_COLS = NG == 1 ? N_ACC * COLS : 512;
   static_assert(NG == 1 || STASH + COUT <= 512, "TMEM columns for the product stash");
   static constexpr int EP = epi_parts(KIND, NB, COUT);  // channel parts per lane quarter
-  static constexpr int CL = tc_cluster(KIND, NB, CIN, COUT);   // CTAs per cluster (weight multicast)
-  static constexpr int B_ROWS = COUT / CL;                      // weight rows one CTA loads per tap
-  static constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);   // every CTA of the cluster
   static constexpr int EPI_WARPS = 4 * EP;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr size_t SCR = scr_bytes(EP);
@@ -957,16 +944,11 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
   float* par = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256 + K::SCR);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Both CTAs of a cluster walk the same number of units (those of its first CTA), since
-  // every stage waits for the other CTA's weight half; a unit past the last tile computes
-  // on zero-filled operands and stores nothing.
-  const uint32_t rank = K::CL > 1 ? tc::cluster_ctarank() : 0u;
-  const int lag = (int)rank * K::NG;   // this CTA's unit index minus its cluster leader's
   if (warp == 0) {
     if (lane == 0) {
       for (int s = 0; s < K::STAGES; ++s) {
         tc::mbar_init(&full[s], 1);
-        tc::mbar_init(&empty[s], K::CL);   // this CTA's MMA commit and, with a cluster, the peer's
+        tc::mbar_init(&empty[s], 1);
       }
       for (int i = 0; i < 2; ++i) {
         tc::mbar_init(&tfull[i], 1);
@@ -984,10 +966,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
     stage_params<KIND, NB, COUT>(a, par, threadIdx.x - 64, K::THREADS - 64);
   }
   tc::fence_before_sync();
-  if constexpr (K::CL > 1)
-    tc::cluster_sync();   // the peer's barriers are initialised before any multicast reaches them
-  else
-    __syncthreads();
+  __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tmem_slot;
   int* err = a.err;
@@ -1001,7 +980,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
 #pragma unroll
     for (int i = 0; i < 8; ++i) used[i] = false;
     bool ok = true;
-    for (int unit = blockIdx.x * K::NG; ok && unit - lag < a.n_tiles * K::NG;
+    for (int unit = blockIdx.x * K::NG; ok && unit < a.n_tiles * K::NG;
          unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1) {
       const int tile = unit / K::NG, g0 = (unit % K::NG) * K::G;   // tile and its branch group
       int slot, t, fb;
@@ -1026,20 +1005,8 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
           uint8_t* bb = st + K::G * K::A_BYTES + i * K::B_BYTES;
           tc::tma_load_4d(ab, &maps.a[b], &full[s], ch, f0, t + dt, slot);
           if constexpr (K::NSPLIT == 2) tc::tma_load_4d(ab + K::A_PART, &maps.a_lo[b], &full[s], ch, f0, t + dt, slot);
-          if constexpr (K::CL > 1) {
-            // this CTA's half of each tap's [Cout][KC] slice, into both CTAs
-#pragma unroll
-            for (int d = 0; d < K::TAPS; ++d) {
-              const int r0 = (int)rank * K::B_ROWS;
-              const size_t off = (size_t)(d * COUT + r0) * K::ROW;
-              tc::tma_load_3d_mc(bb + off, &maps.w[b], &full[s], ch, r0, tap0 + d, K::CL_MASK);
-              if constexpr (K::NSPLIT == 2)
-                tc::tma_load_3d_mc(bb + K::B_PART + off, &maps.w_lo[b], &full[s], ch, r0, tap0 + d, K::CL_MASK);
-            }
-          } else {
-            tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap0);
-            if constexpr (K::NSPLIT == 2) tc::tma_load_3d(bb + K::B_PART, &maps.w_lo[b], &full[s], ch, 0, tap0);
-          }
+          tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap0);
+          if constexpr (K::NSPLIT == 2) tc::tma_load_3d(bb + K::B_PART, &maps.w_lo[b], &full[s], ch, 0, tap0);
         }
         used[s] = true;
         last_par[s] = ph;
@@ -1049,20 +1016,16 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
         }
       }
     }
-    // drain: every issued load has landed, and (with a cluster) both CTAs' MMAs have
-    // released every stage, before the CTA may exit
+    // drain: every issued load has landed before the CTA may exit
     for (int i = 0; i < K::STAGES; ++i)
-      if (used[i]) {
-        tc::mbar_wait(&full[i], last_par[i], err, 9);
-        if constexpr (K::CL > 1) tc::mbar_wait(&empty[i], last_par[i], err, 10);
-      }
+      if (used[i]) tc::mbar_wait(&full[i], last_par[i], err, 9);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     int s = 0;
     uint32_t ph = 0;
     int it = 0;
     bool ok = true;
-    for (int unit = blockIdx.x * K::NG; ok && unit - lag < a.n_tiles * K::NG;
+    for (int unit = blockIdx.x * K::NG; ok && unit < a.n_tiles * K::NG;
          unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1, ++it) {
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
@@ -1098,10 +1061,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
             }
           }
         }
-        if constexpr (K::CL > 1)
-          tc::mma_commit_mc(&empty[s], K::CL_MASK);   // the stage holds the other CTAs' weight parts too
-        else
-          tc::mma_commit(&empty[s]);
+        tc::mma_commit(&empty[s]);
         if (++s == K::STAGES) {
           s = 0;
           ph ^= 1u;
@@ -1117,7 +1077,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
     const bool prefetcher = warp == 2 && lane == 0;
     if (prefetcher) prefetch_resid<K::G, COUT>(a, blockIdx.x, 0);
     int it = 0;
-    for (int unit = blockIdx.x * K::NG; unit - lag < a.n_tiles * K::NG;
+    for (int unit = blockIdx.x * K::NG; unit < a.n_tiles * K::NG;
          unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1, ++it) {
       const int tile = unit / K::NG, g = unit % K::NG;
       const int acc = it % K::N_ACC;
@@ -1155,39 +1115,25 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
     tc::fence_after_sync();
     tc::tmem_dealloc(tbase, K::TMEM_COLS);
   }
-  if constexpr (K::CL > 1) tc::cluster_sync();   // neither CTA leaves while the other may still signal it
 }
 
 template <int KIND, int NB, int CIN, int COUT, int KC, int HALO, int MODE>
 int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
   using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
   auto* kern = conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO, MODE>;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = K::CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(K::THREADS);
-  cfg.dynamicSmemBytes = K::SMEM;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  // persistent grid: as many CTAs as can be resident at once (whole clusters of them)
+  // persistent grid: one CTA per SM (a CTA takes nearly all of an SM's shared memory)
   static int max_ctas = 0;
   if (!max_ctas) {
     CONET_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM));
-    int dev = 0, n_sm = 0, n_cl = 0;
+    int dev = 0, n_sm = 0, per_sm = 0;
     CONET_CUDA(cudaGetDevice(&dev));
     CONET_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    cfg.gridDim = dim3((unsigned)(n_sm / K::CL * K::CL));
-    CONET_CUDA(cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg));
-    if (n_cl < 1) return fail(CONET_ERR_CUDA, "conv_tc_kernel: no cluster of %d CTAs fits an SM pair", K::CL);
-    max_ctas = n_cl * K::CL < n_sm ? n_cl * K::CL : n_sm / K::CL * K::CL;
+    CONET_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::THREADS, K::SMEM));
+    if (per_sm < 1) return fail(CONET_ERR_CUDA, "conv_tc_kernel: a CTA does not fit an SM");
+    max_ctas = n_sm * per_sm;
   }
-  const int want = (a.n_tiles + K::CL - 1) / K::CL * K::CL;
-  cfg.gridDim = dim3((unsigned)(want < max_ctas ? want : max_ctas));
-  CONET_CUDA(cudaLaunchKernelEx(&cfg, kern, maps, a));
+  const int grid = a.n_tiles < max_ctas ? a.n_tiles : max_ctas;
+  conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO, MODE><<<grid, K::THREADS, K::SMEM, s>>>(maps, a);
   return check_launch("conv_tc_kernel");
 }
 

@@ -12,7 +12,9 @@
 // loads the library holds it until the process exits.  Host code cannot use the array's
 // name as a device address, so the first call on each device, with that device current,
 // resolves the address once through cudaGetSymbolAddress and caches it; make that first
-// call before any stream capture.  All calls share the array and it keeps the last call's
+// call before any stream capture.  The cached address outlives a device reset
+// (cudaDeviceReset unloads the module that holds the array), so the entry point must not be
+// called on a device after it was reset in the same process.  All calls share the array and it keeps the last call's
 // contents: every element a call reads is written by that same call first, and two calls
 // that overlap on the GPU (different streams, or different host threads) race on it.
 #include <mutex>

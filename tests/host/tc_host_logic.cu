@@ -26,7 +26,6 @@ void check_plan() {
   CHECK(K::STAGES >= (HALO ? 3 : 2));
   CHECK(K::TMEM_COLS <= 512);
   CHECK(K::THREADS == 64 + 128 * K::EP);
-  CHECK(K::CL == 1 || (CO / K::CL) % 8 == 0);   // weight halves start on whole swizzle atoms
   CHECK((long)K::THREADS * (K::EP == 3 ? 128 : 96) <= 65536);
 }
 
