@@ -42,7 +42,7 @@ typedef enum {
   CONET_ERR_CUDA = -3,         /* a CUDA runtime call or launch failed */
   CONET_ERR_NOMEM = -4,        /* device allocation failed at create time */
   CONET_ERR_WEIGHTS = -5,      /* weight vector of the wrong size */
-  CONET_ERR_NONFINITE = -6,    /* NaN / Inf met in a loss */
+  CONET_ERR_NONFINITE = -6,    /* NaN / Inf met in a loss or written as an LLR */
   CONET_ERR_TIMEOUT = -7,      /* a bounded device-side wait gave up */
   CONET_ERR_UNSUPPORTED = -8   /* valid request this build does not implement */
 } conet_status;
@@ -144,6 +144,32 @@ int conet_init_he(conet_t h, uint64_t seed, void* stream);
  * A wrong n returns CONET_ERR_WEIGHTS and changes nothing.  Load zeroes Adam state. */
 int conet_load_weights(conet_t h, const float* host_params, size_t n);
 int conet_save_weights(conet_t h, float* host_params, size_t n);
+
+/*
+ * Versioned training checkpoint, so that an interrupted run resumes exactly: a 64-byte
+ * header (magic "CONETCK", format version 1, a 64-bit FNV-1a hash of the network shape and
+ * pilot grid, the parameter count n, the caller's Adam step, the handle's precision), then
+ * n FP32 master parameters, n Adam first moments and n Adam second moments in the flat
+ * layout above.  The training workflow of Sec. IV needs the optimiser state as well as the
+ * weights; the paper specifies no file format.
+ *   conet_checkpoint_hash   the header's hash of a config (host only, no handle needed).
+ *   conet_checkpoint_bytes  size of a checkpoint of this handle.
+ *   conet_save_checkpoint   host_buf (host, exactly that size) <- the handle's state, with
+ *                           adam_step recorded (the `step` a following conet_train_step
+ *                           takes); synchronises the device.
+ *   conet_load_checkpoint   the handle's parameters and Adam moments <- host_buf, re-deriving
+ *                           the kernels' weight layouts; *adam_step (may be NULL) <- the
+ *                           recorded step; synchronises.  A buffer that is not a version-1
+ *                           checkpoint of a network with the same hash and parameter count,
+ *                           or of the wrong size, returns CONET_ERR_WEIGHTS and changes
+ *                           nothing.
+ * Resuming with the loaded state and the recorded step continues bitwise as the
+ * uninterrupted run would (every training kernel reduces in a fixed order).
+ */
+int conet_checkpoint_hash(const conet_config* cfg, uint64_t* hash);
+int conet_checkpoint_bytes(conet_t h, size_t* bytes);
+int conet_save_checkpoint(conet_t h, uint64_t adam_step, void* host_buf, size_t bytes);
+int conet_load_checkpoint(conet_t h, const void* host_buf, size_t bytes, uint64_t* adam_step);
 
 /* Views of the library's FP32 master parameters and their gradients (device, n floats,
  * flat layout above), valid until conet_destroy. */
@@ -324,10 +350,21 @@ int conet_profile_read(conet_t h, int kind, double* total_ms, long long* launche
 
 /*
  * Wait for `stream` and report device-side failures of this handle's kernels since the
- * last call: CONET_ERR_TIMEOUT when a bounded pipeline wait gave up (the word is then
- * cleared), CONET_ERR_CUDA for an asynchronous CUDA error.
+ * last call: CONET_ERR_TIMEOUT when a bounded pipeline wait gave up, CONET_ERR_NONFINITE
+ * when a forward pass wrote a NaN or infinite LLR (both status words are then cleared; a
+ * timeout is reported first), CONET_ERR_CUDA for an asynchronous CUDA error.
  */
 int conet_sync(conet_t h, void* stream);
+
+/*
+ * Failure-detection self-test: launches one kernel on `stream` that waits, with the same
+ * bounded mbarrier wait as the tensor-core pipelines but a limit of limit_s seconds
+ * (1e-6 .. 1, else CONET_ERR_ARG), for a phase that nothing completes.  The wait gives up,
+ * records its site (100) in the handle's status word and the kernel returns, so the next
+ * conet_sync returns CONET_ERR_TIMEOUT and the context stays usable.  Diagnostics only:
+ * the paper has no counterpart.
+ */
+int conet_selftest_timeout(conet_t h, double limit_s, void* stream);
 
 /* Kernel launches issued by this library in this process so far (all handles); a replayed
  * forward graph (conet_graphs) counts the kernels it runs. */

@@ -45,6 +45,10 @@ SIGNATURES = {
     "conet_init_he": (I, [P, U64, P]),
     "conet_load_weights": (I, [P, P, SZ]),
     "conet_save_weights": (I, [P, P, SZ]),
+    "conet_checkpoint_hash": (I, [CFG, C.POINTER(U64)]),
+    "conet_checkpoint_bytes": (I, [P, C.POINTER(SZ)]),
+    "conet_save_checkpoint": (I, [P, U64, P, SZ]),
+    "conet_load_checkpoint": (I, [P, P, SZ, C.POINTER(U64)]),
     "conet_params_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
     "conet_grads_device": (I, [P, C.POINTER(P), C.POINTER(SZ)]),
     "conet_params_updated": (I, [P, P]),
@@ -65,6 +69,7 @@ SIGNATURES = {
     "conet_profile_read": (I, [P, I, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "conet_launch_count": (C.c_ulonglong, []),
     "conet_sync": (I, [P, P]),
+    "conet_selftest_timeout": (I, [P, C.c_double, P]),
     "conet_last_error": (C.c_char_p, []),
 }
 

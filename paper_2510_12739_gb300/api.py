@@ -102,6 +102,25 @@ class Receiver:
         check(lib().conet_save_weights(self.h, out.ctypes.data_as(C.c_void_p), out.size))
         return out
 
+    def save_checkpoint(self, adam_step: int) -> bytes:
+        """Versioned checkpoint: parameters, Adam moments and the Adam step to resume at."""
+        n = C.c_size_t()
+        check(lib().conet_checkpoint_bytes(self.h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        check(lib().conet_save_checkpoint(self.h, int(adam_step), C.cast(buf, C.c_void_p), n.value))
+        return buf.raw
+
+    def load_checkpoint(self, blob: bytes) -> int:
+        """Restore a checkpoint; returns the Adam step it recorded."""
+        step = C.c_uint64()
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        check(lib().conet_load_checkpoint(self.h, C.cast(buf, C.c_void_p), len(blob), C.byref(step)))
+        return step.value
+
+    def selftest_timeout(self, limit_s: float = 1e-3, stream=None):
+        """Launch the failure-detection self-test (a bounded wait that gives up)."""
+        check(lib().conet_selftest_timeout(self.h, float(limit_s), _stream(stream)))
+
     def params_device(self) -> torch.Tensor:
         p, n = C.c_void_p(), C.c_size_t()
         check(lib().conet_params_device(self.h, C.byref(p), C.byref(n)))
@@ -259,6 +278,13 @@ def conv3x3_wgrad(x, dz, want_bias=True, stream=None):
     db = torch.empty(cout, dtype=torch.float32, device=x.device) if want_bias else None
     check(lib().conet_conv3x3_wgrad(_ptr(x), _ptr(dz), B, T, F, cin, cout, _ptr(dW), _ptr(db), _stream(stream)))
     return dW, db
+
+
+def checkpoint_hash(net) -> int:
+    """The checkpoint header's hash of a network description."""
+    h = C.c_uint64()
+    check(lib().conet_checkpoint_hash(C.byref(make_config(net)), C.byref(h)))
+    return h.value
 
 
 def launch_count() -> int:

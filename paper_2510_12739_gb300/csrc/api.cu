@@ -3,6 +3,7 @@
 // argument before the first launch; the kernels do all the arithmetic of the path.
 #include <math.h>
 #include <stdarg.h>
+#include <string.h>
 
 #include <map>
 #include <string>
@@ -152,14 +153,11 @@ unsigned long long conet_launch_count(void) { return __atomic_load_n(&g_launches
 int conet_sync(conet_t h, void* stream) {
   if (!h) return fail(CONET_ERR_ARG, "handle is NULL");
   CONET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-  if (h->d_err) {
-    int e = 0;
-    CONET_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) {
-      CONET_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
-      return fail(CONET_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (site %d)", e);
-    }
-  }
+  int e[2] = {0, 0};
+  CONET_CUDA(cudaMemcpy(e, h->d_err, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e[0] || e[1]) CONET_CUDA(cudaMemset(h->d_err, 0, sizeof(e)));
+  if (e[0]) return fail(CONET_ERR_TIMEOUT, "a device pipeline wait timed out (site %d)", e[0]);
+  if (e[1]) return fail(CONET_ERR_NONFINITE, "a forward pass wrote a NaN or infinite LLR");
   return CONET_OK;
 }
 
@@ -433,6 +431,109 @@ int conet_loss_ber(const float* llr, const uint8_t* bits, const uint8_t* pilot_m
   if (B < 1 || T < 1 || F < 1 || Q < 1 || Q > 16) return fail(CONET_ERR_SHAPE, "bad sizes B=%d T=%d F=%d Q=%d", B, T, F, Q);
   return launch_loss_ber(llr, bits, pilot_mask, B, T, F, Q, grad_scale, dllr, loss_sum, err_bits, n_bits,
                          (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ checkpoints
+// Version-1 layout: a 64-byte header, then the FP32 master parameters, Adam's first and
+// second moments (n floats each, the flat parameter layout).
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t header_bytes;
+  uint64_t config_hash;
+  uint64_t n_params;
+  uint64_t adam_step;
+  uint32_t precision;
+  uint32_t flags;
+  uint8_t reserved[16];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header");
+constexpr char CKPT_MAGIC[8] = {'C', 'O', 'N', 'E', 'T', 'C', 'K', 0};
+constexpr uint32_t CKPT_VERSION = 1;
+constexpr uint32_t CKPT_HAS_ADAM = 1;
+
+// FNV-1a (64-bit) over the fields that give the parameters their meaning: the network
+// shape and the fixed pilot grid (each value folded in as 8 little-endian bytes).
+uint64_t config_hash(const conet_config& c) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  auto mix = [&](int64_t v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (uint64_t)((v >> (8 * i)) & 0xff);
+      h *= 0x100000001b3ull;
+    }
+  };
+  const int f[] = {c.n_rx, c.n_sym, c.n_sc, c.qam_bits, c.n_branches, c.depth, c.width,
+                   c.residual, c.norm, c.fuse_mask, c.resnet_baseline, c.n_pilot_syms, c.pilot_comb};
+  for (int v : f) mix(v);
+  for (int i = 0; i < c.n_pilot_syms && i < 4; ++i) mix(c.pilot_syms[i]);
+  mix((int64_t)c.pilot_seed);
+  return h;
+}
+
+size_t ckpt_bytes(const conet_s* h) { return sizeof(CkptHeader) + 3 * h->L.total * sizeof(float); }
+
+}  // namespace
+
+int conet_checkpoint_hash(const conet_config* cfg, uint64_t* hash) {
+  CONET_TRY(validate_config(cfg));
+  if (!hash) return fail(CONET_ERR_ARG, "hash is NULL");
+  *hash = config_hash(*cfg);
+  return CONET_OK;
+}
+
+int conet_checkpoint_bytes(conet_t h, size_t* bytes) {
+  if (!h || !bytes) return fail(CONET_ERR_ARG, "NULL argument");
+  *bytes = ckpt_bytes(h);
+  return CONET_OK;
+}
+
+int conet_save_checkpoint(conet_t h, uint64_t adam_step, void* host_buf, size_t bytes) {
+  if (!h || !host_buf) return fail(CONET_ERR_ARG, "NULL argument");
+  if (bytes != ckpt_bytes(h)) return fail(CONET_ERR_WEIGHTS, "checkpoint buffer has %zu bytes, needs %zu", bytes, ckpt_bytes(h));
+  CkptHeader hd = {};
+  memcpy(hd.magic, CKPT_MAGIC, sizeof(hd.magic));
+  hd.version = CKPT_VERSION;
+  hd.header_bytes = sizeof(CkptHeader);
+  hd.config_hash = config_hash(h->cfg);
+  hd.n_params = h->L.total;
+  hd.adam_step = adam_step;
+  hd.precision = (uint32_t)h->prec;
+  hd.flags = CKPT_HAS_ADAM;
+  uint8_t* out = static_cast<uint8_t*>(host_buf);
+  const size_t nb = h->L.total * sizeof(float);
+  CONET_CUDA(cudaDeviceSynchronize());
+  CONET_CUDA(cudaMemcpy(out + sizeof(CkptHeader), h->params, nb, cudaMemcpyDeviceToHost));
+  CONET_CUDA(cudaMemcpy(out + sizeof(CkptHeader) + nb, h->adam_m, nb, cudaMemcpyDeviceToHost));
+  CONET_CUDA(cudaMemcpy(out + sizeof(CkptHeader) + 2 * nb, h->adam_v, nb, cudaMemcpyDeviceToHost));
+  memcpy(out, &hd, sizeof(hd));
+  return CONET_OK;
+}
+
+int conet_load_checkpoint(conet_t h, const void* host_buf, size_t bytes, uint64_t* adam_step) {
+  if (!h || !host_buf) return fail(CONET_ERR_ARG, "NULL argument");
+  if (bytes < sizeof(CkptHeader)) return fail(CONET_ERR_WEIGHTS, "checkpoint of %zu bytes has no header", bytes);
+  CkptHeader hd;
+  memcpy(&hd, host_buf, sizeof(hd));
+  if (memcmp(hd.magic, CKPT_MAGIC, sizeof(hd.magic)) != 0) return fail(CONET_ERR_WEIGHTS, "not a CoNet checkpoint");
+  if (hd.version != CKPT_VERSION || hd.header_bytes != sizeof(CkptHeader) || !(hd.flags & CKPT_HAS_ADAM))
+    return fail(CONET_ERR_WEIGHTS, "checkpoint version %u (header %u bytes) is not readable by version %u", hd.version,
+                hd.header_bytes, CKPT_VERSION);
+  if (hd.config_hash != config_hash(h->cfg) || hd.n_params != h->L.total)
+    return fail(CONET_ERR_WEIGHTS, "checkpoint was written for a different network (hash %016llx, %llu parameters)",
+                (unsigned long long)hd.config_hash, (unsigned long long)hd.n_params);
+  if (bytes != ckpt_bytes(h)) return fail(CONET_ERR_WEIGHTS, "checkpoint has %zu bytes, needs %zu", bytes, ckpt_bytes(h));
+  const uint8_t* in = static_cast<const uint8_t*>(host_buf);
+  const size_t nb = h->L.total * sizeof(float);
+  CONET_CUDA(cudaDeviceSynchronize());
+  CONET_CUDA(cudaMemcpy(h->params, in + sizeof(CkptHeader), nb, cudaMemcpyHostToDevice));
+  CONET_CUDA(cudaMemcpy(h->adam_m, in + sizeof(CkptHeader) + nb, nb, cudaMemcpyHostToDevice));
+  CONET_CUDA(cudaMemcpy(h->adam_v, in + sizeof(CkptHeader) + 2 * nb, nb, cudaMemcpyHostToDevice));
+  CONET_TRY(net_weights_changed(h, 0));
+  CONET_CUDA(cudaDeviceSynchronize());
+  if (adam_step) *adam_step = hd.adam_step;
+  return CONET_OK;
 }
 
 int conet_train_step(conet_t h, const conet_sim_params* sim, uint64_t seed, uint64_t step, int B, float lr,

@@ -615,7 +615,9 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
 #pragma unroll
         for (int pp = 0; pp < EP; ++pp)
           sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
-        a.llr[m * a.Q + qq] = sum + lds1(par + PL::HEADB + qq);
+        const float v = sum + lds1(par + PL::HEADB + qq);
+        a.llr[m * a.Q + qq] = v;
+        if (!(fabsf(v) <= FLT_MAX)) *a.nonfinite = 1;
       }
     }
   }
@@ -897,7 +899,9 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const flo
 #pragma unroll
         for (int pp = 0; pp < EP; ++pp)
           sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
-        a.llr[m * a.Q + qq] = sum + lds1(par + PL::HEADB + qq);
+        const float v = sum + lds1(par + PL::HEADB + qq);
+        a.llr[m * a.Q + qq] = v;
+        if (!(fabsf(v) <= FLT_MAX)) *a.nonfinite = 1;
       }
     }
   }

@@ -141,7 +141,11 @@ __global__ void fuse_kernel(FuseArgs a) {
             if (c < C) s += __ldg(a.head_w + q * C + c) * x0.x[v][e];
           }
         s = warp_sum(s);
-        if (lane == 0) a.llr[m * a.Q + q] = s + __ldg(a.head_b + q);
+        if (lane == 0) {
+          const float v = s + __ldg(a.head_b + q);
+          a.llr[m * a.Q + q] = v;
+          if (!(fabsf(v) <= FLT_MAX)) *a.nonfinite = 1;
+        }
       }
     }
   }

@@ -100,6 +100,7 @@ struct FuseArgs {
   const float* head_w;
   const float* head_b;
   float* llr;
+  int* nonfinite;              // set to 1 when an LLR written is NaN or infinite
   int n_br, fuse, C, Q;
   long long M;
 };
@@ -211,6 +212,7 @@ struct TcConvArgs {
   float* llr;
   int Q;
   int* err;                    // device error word (first timed-out wait)
+  int* nonfinite;              // set to 1 when an LLR written is NaN or infinite
   // E4M3 path: accumulator column c of branch b is dequantised by dq[b][c] (= the input's
   // per-tensor scale x the weights' per-output-channel scale); nx_out[b] is written as
   // E4M3 of next / scale, with qinv[b] = 1 / scale (device scalars); amax[b], when set,

@@ -68,17 +68,22 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t pa
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; on timeout records `where` in *err
-// (first writer wins) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int where) {
+// Wait for the phase with the given parity for at most limit_ns; on timeout records `where`
+// in *err (first writer wins) and returns false.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* err, int where, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
     if (mbar_try_wait_suspend(bar, parity, WAIT_HINT_NS)) return true;
-    if (globaltimer_ns() - t0 > WAIT_NS) break;
+    if (globaltimer_ns() - t0 > limit_ns) break;
   }
   atomicCAS(err, 0, where);
   return false;
+}
+
+// The pipelines' bounded wait (WAIT_NS).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int where) {
+  return mbar_wait_for(bar, parity, err, where, WAIT_NS);
 }
 
 // 4-D / 3-D tiled TMA loads into shared memory, completing on an mbarrier (tx bytes).

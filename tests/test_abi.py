@@ -82,3 +82,26 @@ def test_host_side_argument_errors(lib):
     assert lib.conet_loss_ber(None, None, None, 1, 14, 72, 4, 0.0, None, None, None, None, None) == -1
     cfg = api.make_config(base)
     assert lib.conet_sim_generate(C.byref(cfg), None, 0, 0, 1, 0.0, None, None, None, None, None, None) == -1
+
+
+def test_checkpoint_hash_tracks_the_network_shape(lib):
+    """The checkpoint header's hash changes with every field that gives the parameters their
+    meaning and not with the workspace size or the train flag."""
+    from paper_2510_12739_gb300 import api
+    base = WORKLOADS["plain_14x72_b16_fp32"].net
+    h0 = api.checkpoint_hash(base)
+    assert h0 == api.checkpoint_hash(base)
+    for kw in (dict(n_rx=2), dict(n_sc=73), dict(qam_bits=6), dict(n_branches=3), dict(depth=5), dict(width=16),
+               dict(norm=1), dict(fuse_mask=0b11), dict(pilot_syms=(2, 12)), dict(pilot_comb=3),
+               dict(pilot_seed=1), dict(residual=1)):
+        assert api.checkpoint_hash(replace(base, **kw)) != h0, kw
+    cfg = api.make_config(base, max_batch=7, train=True)
+    h = C.c_uint64()
+    assert lib.conet_checkpoint_hash(C.byref(cfg), C.byref(h)) == 0 and h.value == h0
+    # NULL handles and buffers are rejected on the host
+    assert lib.conet_checkpoint_hash(C.byref(cfg), None) == -1
+    n = C.c_size_t()
+    assert lib.conet_checkpoint_bytes(None, C.byref(n)) == -1
+    assert lib.conet_save_checkpoint(None, 0, None, 0) == -1
+    assert lib.conet_load_checkpoint(None, None, 0, None) == -1
+    assert lib.conet_selftest_timeout(None, 1e-3, None) == -1
