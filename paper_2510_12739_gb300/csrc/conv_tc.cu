@@ -81,7 +81,7 @@ int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int c
 // Channels per K chunk and taps per stage of the instantiation for (kind, nb, cin, cout).
 int tc_chunk(int kind, int nb, int cin, int cout) { return tc_kc(kind, nb, cin, cout); }
 int tc_taps(int kind, int nb, int cin, int cout) { return tc_halo(kind, nb, cin, cout) ? 3 : 1; }
-int tc_wbox_rows(int kind, int nb, int cin, int cout) { return cout; }
+int tc_wbox_rows(int kind, int nb, int cin, int cout) { return cout / 2; }   // one CTA's half of a pair's B
 int tc_wbox_taps(int kind, int nb, int cin, int cout) { return tc_taps(kind, nb, cin, cout); }
 
 // [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] TF32 hi and FP32 lo = w - hi

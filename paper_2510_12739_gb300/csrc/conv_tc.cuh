@@ -9,12 +9,19 @@
 // which is exactly the conv's zero padding.  The B operand is the tap's [Cout][KC] weight
 // slice, both K-major.
 //
-// Warp roles (192 threads): warp 0 issues TMA loads into a ring of shared-memory stages,
-// warp 1 issues tcgen05.mma from one thread and commits each stage back to the producer,
-// warps 2-5 (one TMEM lane quarter each, one RE per thread) run the fused epilogue:
-// bias, residual add, ReLU / LayerNorm, the Hadamard fusion of the branches with its
-// LayerNorm, the next layer's pre-activation, and the 1x1 LLR head.  Two TMEM accumulator
-// sets (when they fit) let the epilogue of one tile overlap the MMAs of the next.
+// CTA pairs: the kernel runs in clusters of two CTAs that compute two tiles with one
+// tcgen05.mma.cta_group::2 of M = 256 per K step.  Each CTA TMA-loads its own tile's A box and
+// one half (Cout / 2 rows) of the weight slices; the MMA reads B across both CTAs' shared
+// memory, so L2 serves every weight byte once per pair and each SM holds half the weights.
+//
+// Warp roles: warp 0 of each CTA issues that CTA's TMA loads into a ring of shared-memory
+// stages (completion counted on the first CTA's barrier); warp 1 of the first CTA issues the
+// pair's MMAs from one thread and commits each stage back to both producers; the epilogue
+// warps of each CTA (4 TMEM lane quarters x 3 or 4 channel parts, one RE per thread) run the
+// fused epilogue on their own CTA's accumulators: bias, residual add, ReLU / LayerNorm, the
+// Hadamard fusion of the branches with its LayerNorm, the next layer's pre-activation, and
+// the 1x1 LLR head.  Two TMEM accumulator sets (when they fit) let the epilogue of one tile
+// overlap the MMAs of the next.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -68,10 +75,12 @@ __host__ __device__ constexpr int pow2_ceil(int x) {
 __host__ __device__ constexpr int elt_of(int kind) { return kind == 1 ? 4 : kind == 2 ? 1 : 2; }
 __host__ __device__ constexpr int nsplit_of(int kind) { return kind == 1 ? 2 : 1; }
 
-// Shared-memory bytes of one pipeline stage: per branch (and split part) an A box of
-// a_rows rows and `taps` weight slices of cout rows, rows of `row` bytes; 1 KB aligned.
+// Shared-memory bytes of one pipeline stage of one CTA of a pair: per branch (and split part)
+// an A box of a_rows rows and `taps` weight slices of this CTA's cout / 2 rows, rows of `row`
+// bytes; 1 KB aligned.
 __host__ __device__ constexpr size_t stage_bytes(int kind, int nb, int cout, int row, int a_rows, int taps) {
-  return ((size_t)nb * nsplit_of(kind) * ((size_t)a_rows * row + (size_t)taps * cout * row) + 1023) / 1024 * 1024;
+  return ((size_t)nb * nsplit_of(kind) * ((size_t)a_rows * row + (size_t)taps * (cout / 2) * row) + 1023) / 1024 *
+         1024;
 }
 
 __host__ __device__ constexpr int stages_fit(int kind, int nb, int cout, int row, int a_rows, int taps, int ep,
@@ -142,12 +151,13 @@ struct Cfg {
   static constexpr int TAPS = HALO ? 3 : 1;             // weight taps (subcarrier shifts) per stage
   static constexpr int A_BOX = HALO ? TILE_M + 2 : TILE_M;
   static constexpr int A_PART = (HALO ? HALO_ROWS : TILE_M) * ROW;
-  static constexpr int B_PART = TAPS * COUT * ROW;
+  static constexpr int B_ROWS = COUT / 2;               // weight rows (output channels) per CTA
+  static constexpr int B_PART = TAPS * B_ROWS * ROW;
   static constexpr int A_BYTES = NSPLIT * A_PART;
   static constexpr int B_BYTES = NSPLIT * B_PART;
   static constexpr int NG = tc_groups(KIND, NB, COUT); // branch groups per tile
   static constexpr int G = NB / NG;                     // branches per MMA unit (one stage holds G)
-  static constexpr int STAGE_TX = G * NSPLIT * (A_BOX * ROW + B_PART);
+  static constexpr int STAGE_TX = G * NSPLIT * (A_BOX * ROW + B_PART);   // bytes one CTA loads per stage
   static constexpr int STAGE = (int)stage_bytes(KIND, G, COUT, ROW, HALO ? HALO_ROWS : TILE_M, TAPS);
   static constexpr int K_ITERS = (9 / TAPS) * (CIN / KC);
   static constexpr int COLS = NG == 1 ? pow2_ceil(NB * COUT) : G * COUT;   // stride of accumulator sets
@@ -163,9 +173,10 @@ struct Cfg {
   static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR - PAR) / STAGE);
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR + PAR;
-  static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT);   // BF16 / TF32 / F16, E4M3
+  static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT, 256);   // BF16 / TF32 / F16, E4M3
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
   static_assert(COUT % 16 == 0 && COUT <= 256 && COUT % CW == 0, "MMA N");
+  static_assert(B_ROWS % 8 == 0, "each CTA's weight half holds whole swizzle atoms");
   static_assert(NB * COUT <= 512, "TMEM columns");
   static_assert(CIN % KC == 0, "K chunking");
   static_assert(A_PART % 1024 == 0 || (A_PART % 512 == 0 && ROW <= 64) || (A_PART % 256 == 0 && ROW == 32),
@@ -948,15 +959,21 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
   float* par = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256 + K::SCR);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // The pair computes tiles 2u and 2u + 1 of every pair-unit u it owns: this CTA (rank 0 or 1)
+  // the one of its rank.  Both CTAs walk the same units; a tile past the last one (odd tile
+  // counts) computes on zero-filled operands and stores nothing.
+  const uint32_t rank = tc::cluster_ctarank();
+  const int pair = (int)(blockIdx.x >> 1), n_pairs = (int)(gridDim.x >> 1);
+  const int pair_units = (a.n_tiles + 1) / 2 * K::NG;
   if (warp == 0) {
     if (lane == 0) {
       for (int s = 0; s < K::STAGES; ++s) {
-        tc::mbar_init(&full[s], 1);
-        tc::mbar_init(&empty[s], 1);
+        tc::mbar_init(&full[s], 1);    // the first CTA's producer; both CTAs' TMA bytes
+        tc::mbar_init(&empty[s], 1);   // the pair's MMA commit
       }
       for (int i = 0; i < 2; ++i) {
         tc::mbar_init(&tfull[i], 1);
-        tc::mbar_init(&tempty[i], K::EPI_WARPS);
+        tc::mbar_init(&tempty[i], 2 * K::EPI_WARPS);   // both CTAs' epilogue warps
       }
       tc::fence_mbar_init();
       for (int b = 0; b < NB; ++b) {
@@ -965,18 +982,19 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
       }
     }
     __syncwarp();
-    tc::tmem_alloc(tmem_slot, K::TMEM_COLS);
+    tc::tmem_alloc_pair(tmem_slot, K::TMEM_COLS);
   } else if (warp >= 2) {
     stage_params<KIND, NB, COUT>(a, par, threadIdx.x - 64, K::THREADS - 64);
   }
   tc::fence_before_sync();
-  __syncthreads();
+  tc::cluster_sync();   // both CTAs' barriers are initialised before any remote signal
   tc::fence_after_sync();
   const uint32_t tbase = *tmem_slot;
   int* err = a.err;
 
   if (warp == 0 && lane == 0) {
-    // ------------------------------------------------------------ TMA producer
+    // ------------------------------------------------------------ TMA producer (each CTA)
+    const uint32_t full0 = tc::mapa(tc::smem_u32(&full[0]), 0);   // the first CTA's full barriers
     int s = 0;
     uint32_t ph = 0;
     uint32_t last_par[8];
@@ -984,9 +1002,9 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
 #pragma unroll
     for (int i = 0; i < 8; ++i) used[i] = false;
     bool ok = true;
-    for (int unit = blockIdx.x * K::NG; ok && unit < a.n_tiles * K::NG;
-         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1) {
-      const int tile = unit / K::NG, g0 = (unit % K::NG) * K::G;   // tile and its branch group
+    for (int unit = pair * K::NG; ok && unit < pair_units;
+         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? n_pairs * K::NG - (K::NG - 1) : 1) {
+      const int tile = 2 * (unit / K::NG) + (int)rank, g0 = (unit % K::NG) * K::G;   // tile and branch group
       int slot, t, fb;
       decode_tile(tile, a.T, a.nfb, slot, t, fb);
       for (int k = 0; k < K::K_ITERS; ++k) {
@@ -994,23 +1012,25 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
           ok = false;
           break;
         }
-        tc::mbar_arrive_expect_tx(&full[s], K::STAGE_TX);
+        if (rank == 0) tc::mbar_arrive_expect_tx(&full[s], 2 * K::STAGE_TX);
+        const uint32_t fb_s = full0 + (uint32_t)(s * sizeof(uint64_t));
         // halo stage: symbol row t + dt, subcarriers from one before the tile, taps
         // (dt, -1..1); else one tap (dt, df) with the tile's rows shifted by df
         const int grp = k / (CIN / KC), ch = (k % (CIN / KC)) * KC;
         const int dt = HALO ? grp - 1 : grp / 3 - 1;
         const int f0 = HALO ? fb * TILE_M - 1 : fb * TILE_M + grp % 3 - 1;
         const int tap0 = HALO ? 3 * grp : grp;
+        const int r0 = (int)rank * K::B_ROWS;   // this CTA's half of the output channels
         uint8_t* st = smem + (size_t)s * K::STAGE;
 #pragma unroll
         for (int i = 0; i < K::G; ++i) {
           const int b = g0 + i;
           uint8_t* ab = st + i * K::A_BYTES;
           uint8_t* bb = st + K::G * K::A_BYTES + i * K::B_BYTES;
-          tc::tma_load_4d(ab, &maps.a[b], &full[s], ch, f0, t + dt, slot);
-          if constexpr (K::NSPLIT == 2) tc::tma_load_4d(ab + K::A_PART, &maps.a_lo[b], &full[s], ch, f0, t + dt, slot);
-          tc::tma_load_3d(bb, &maps.w[b], &full[s], ch, 0, tap0);
-          if constexpr (K::NSPLIT == 2) tc::tma_load_3d(bb + K::B_PART, &maps.w_lo[b], &full[s], ch, 0, tap0);
+          tc::tma_load_4d_pair(ab, &maps.a[b], fb_s, ch, f0, t + dt, slot);
+          if constexpr (K::NSPLIT == 2) tc::tma_load_4d_pair(ab + K::A_PART, &maps.a_lo[b], fb_s, ch, f0, t + dt, slot);
+          tc::tma_load_3d_pair(bb, &maps.w[b], fb_s, ch, r0, tap0);
+          if constexpr (K::NSPLIT == 2) tc::tma_load_3d_pair(bb + K::B_PART, &maps.w_lo[b], fb_s, ch, r0, tap0);
         }
         used[s] = true;
         last_par[s] = ph;
@@ -1020,17 +1040,18 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
         }
       }
     }
-    // drain: every issued load has landed before the CTA may exit
+    // drain: the pair's MMAs have released every stage this CTA filled (so every load into
+    // it has landed and been read, and every commit to it has arrived) before it may exit
     for (int i = 0; i < K::STAGES; ++i)
-      if (used[i]) tc::mbar_wait(&full[i], last_par[i], err, 9);
-  } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------------------ MMA issuer
+      if (used[i]) tc::mbar_wait(&empty[i], last_par[i], err, 9);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ------------------------------------------------------------ MMA issuer (first CTA)
     int s = 0;
     uint32_t ph = 0;
     int it = 0;
     bool ok = true;
-    for (int unit = blockIdx.x * K::NG; ok && unit < a.n_tiles * K::NG;
-         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1, ++it) {
+    for (int unit = pair * K::NG; ok && unit < pair_units;
+         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? n_pairs * K::NG - (K::NG - 1) : 1, ++it) {
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
       if (!tc::mbar_wait(&tempty[acc], aph ^ 1u, err, 2)) break;
@@ -1053,44 +1074,48 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
               // function of the shared-memory address, so a whole-row shift of the
               // descriptor's start selects the shifted rows
               const uint32_t aa = st + b * K::A_BYTES + d * K::ROW + 32 * j;
-              const uint32_t ba = st + K::G * K::A_BYTES + b * K::B_BYTES + d * COUT * K::ROW + 32 * j;
+              const uint32_t ba = st + K::G * K::A_BYTES + b * K::B_BYTES + d * K::B_ROWS * K::ROW + 32 * j;
               const uint64_t ad = tc::smem_desc(aa, K::ROW);
               const uint64_t bd = tc::smem_desc(ba, K::ROW);
-              tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, bd, K::IDESC, (k | d | j) != 0);
+              tc::mma_pair<KIND>(dcol + (uint32_t)(b * COUT), ad, bd, K::IDESC, (k | d | j) != 0);
               if constexpr (K::NSPLIT == 2) {
                 // FP32-accurate product from TF32 parts: hi*hi + hi*lo + lo*hi
-                tc::mma<KIND>(dcol + (uint32_t)(b * COUT), ad, tc::smem_desc(ba + K::B_PART, K::ROW), K::IDESC, 1u);
-                tc::mma<KIND>(dcol + (uint32_t)(b * COUT), tc::smem_desc(aa + K::A_PART, K::ROW), bd, K::IDESC, 1u);
+                tc::mma_pair<KIND>(dcol + (uint32_t)(b * COUT), ad, tc::smem_desc(ba + K::B_PART, K::ROW), K::IDESC,
+                                   1u);
+                tc::mma_pair<KIND>(dcol + (uint32_t)(b * COUT), tc::smem_desc(aa + K::A_PART, K::ROW), bd, K::IDESC,
+                                   1u);
               }
             }
           }
         }
-        tc::mma_commit(&empty[s]);
+        tc::mma_commit_pair(&empty[s]);   // the stage is free again in both CTAs
         if (++s == K::STAGES) {
           s = 0;
           ph ^= 1u;
         }
       }
-      tc::mma_commit(&tfull[acc]);
+      tc::mma_commit_pair(&tfull[acc]);     // both CTAs' accumulators are complete
     }
   } else if (warp >= 2) {
-    // ------------------------------------------------------------ fused epilogue
+    // ------------------------------------------------------------ fused epilogue (each CTA)
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
     const int part = (warp - 2) / 4;        // which share of the channels this warp handles
     const int row = 32 * q + lane;
     const bool prefetcher = warp == 2 && lane == 0;
-    if (prefetcher) prefetch_resid<K::G, COUT>(a, blockIdx.x, 0);
+    // the first CTA's tempty barriers, where both CTAs' epilogue warps report a drained set
+    const uint32_t tempty0 = tc::mapa(tc::smem_u32(&tempty[0]), 0);
+    if (prefetcher) prefetch_resid<K::G, COUT>(a, 2 * pair + (int)rank, 0);
     int it = 0;
-    for (int unit = blockIdx.x * K::NG; unit < a.n_tiles * K::NG;
-         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? (int)gridDim.x * K::NG - (K::NG - 1) : 1, ++it) {
-      const int tile = unit / K::NG, g = unit % K::NG;
+    for (int unit = pair * K::NG; unit < pair_units;
+         unit += (K::NG == 1 || unit % K::NG == K::NG - 1) ? n_pairs * K::NG - (K::NG - 1) : 1, ++it) {
+      const int tile = 2 * (unit / K::NG) + (int)rank, g = unit % K::NG;
       const int acc = it % K::N_ACC;
       const uint32_t aph = (uint32_t)(it / K::N_ACC) & 1u;
       if (prefetcher) {
         if (g + 1 < K::NG)
           prefetch_resid<K::G, COUT>(a, tile, (g + 1) * K::G);
         else
-          prefetch_resid<K::G, COUT>(a, tile + gridDim.x, 0);
+          prefetch_resid<K::G, COUT>(a, tile + 2 * n_pairs, 0);
       }
       const bool got = tc::mbar_wait(&tfull[acc], aph, err, 4);
       if (!barrier_all(1 + q, 32 * EP, got)) break;
@@ -1109,15 +1134,18 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
                                                           m, part, q, lane, scr_all);
       tc::fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+      if (lane == 0) tc::mbar_arrive_cluster(tempty0 + (uint32_t)(acc * sizeof(uint64_t)));
     }
   }
+  // neither CTA deallocates or leaves while the pair may still read its shared memory or
+  // TMEM or signal its barriers
   tc::fence_before_sync();
   __syncthreads();
+  tc::cluster_sync();
   if (warp == 0) {
     __syncwarp();
     tc::fence_after_sync();
-    tc::tmem_dealloc(tbase, K::TMEM_COLS);
+    tc::tmem_dealloc_pair(tbase, K::TMEM_COLS);
   }
 }
 
@@ -1125,19 +1153,32 @@ template <int KIND, int NB, int CIN, int COUT, int KC, int HALO, int MODE>
 int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
   using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
   auto* kern = conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO, MODE>;
-  // persistent grid: one CTA per SM (a CTA takes nearly all of an SM's shared memory)
-  static int max_ctas = 0;
-  if (!max_ctas) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(K::THREADS);
+  cfg.dynamicSmemBytes = K::SMEM;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // persistent grid: as many CTA pairs as can be resident at once (one CTA per SM)
+  static int max_pairs = 0;
+  if (!max_pairs) {
     CONET_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM));
-    int dev = 0, n_sm = 0, per_sm = 0;
+    int dev = 0, n_sm = 0, n_cl = 0;
     CONET_CUDA(cudaGetDevice(&dev));
     CONET_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    CONET_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::THREADS, K::SMEM));
-    if (per_sm < 1) return fail(CONET_ERR_CUDA, "conv_tc_kernel: a CTA does not fit an SM");
-    max_ctas = n_sm * per_sm;
+    cfg.gridDim = dim3((unsigned)(n_sm / 2 * 2));
+    CONET_CUDA(cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg));
+    if (n_cl < 1) return fail(CONET_ERR_CUDA, "conv_tc_kernel: no CTA pair fits an SM pair");
+    max_pairs = n_cl < n_sm / 2 ? n_cl : n_sm / 2;
   }
-  const int grid = a.n_tiles < max_ctas ? a.n_tiles : max_ctas;
-  conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO, MODE><<<grid, K::THREADS, K::SMEM, s>>>(maps, a);
+  const int want = (a.n_tiles + 1) / 2;
+  cfg.gridDim = dim3((unsigned)(2 * (want < max_pairs ? want : max_pairs)));
+  CONET_CUDA(cudaLaunchKernelEx(&cfg, kern, maps, a));
   return check_launch("conv_tc_kernel");
 }
 
