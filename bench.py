@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     p.add_argument("--no-variants", action="store_true", help="headline workload only")
+    p.add_argument("--no-ber", action="store_true", help="skip the trained-network BER table")
     p.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling runs)")
     p.add_argument("--precision", choices=["fp32", "bf16", "fp16", "tf32x3", "fp8"], default=None,
                    help="override the workload's conv precision")
@@ -83,6 +84,46 @@ def tensor_peak():
         return float(mp["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
     except (OSError, ValueError, KeyError):
         return 1700.0, "fallback sustained BF16 1.7 PFLOP/s (of fallback)"
+
+
+def measure_fp8_peak(torch, n=8192, burst=10, sustain_s=3.0):
+    """Dense E4M3 tensor throughput on this GPU, measured: cuBLASLt's FP8 GEMM
+    (torch._scaled_mm, unit scales, BF16 output) at n x n x n, 2 n^3 FLOP per call; burst =
+    best of `burst` single calls, sustained = back-to-back calls for sustain_s seconds.
+    An "unavailable" entry instead when this torch build has no FP8 GEMM for the device."""
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()     # column-major operand
+        one = torch.ones((), device="cuda")
+
+        def mm():
+            return torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+
+        for _ in range(3):
+            mm()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(burst):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mm()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        k = max(1, int(sustain_s / best))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            mm()
+        e1.record()
+        torch.cuda.synchronize()
+        sus = e0.elapsed_time(e1) / 1e3 / k
+        f = 2.0 * n ** 3
+        del a, b
+        return {"burst_tflops": f / best / 1e12, "sustained_tflops": f / sus / 1e12, "n": n,
+                "how": f"torch._scaled_mm e4m3 x e4m3 -> bf16, {n}^3, best of {burst} / {k} back to back"}
+    except (RuntimeError, AttributeError, TypeError) as e:
+        return {"unavailable": str(e).splitlines()[0][:200]}
 
 
 class ClockSampler:
@@ -234,6 +275,9 @@ class Ctx:
         return [a.elapsed_time(b) for a, b in evs]
 
 
+FP8_PEAK = {}   # filled by main() with measure_fp8_peak's result before the E4M3 variants
+
+
 def roofline_of(w, net, B, rx, steps, n_sm):
     from paper_2510_12739_gb300 import api
     conv_ms, conv_n = rx.profile_read(api.PROFILE_KINDS["conv"])
@@ -253,8 +297,12 @@ def roofline_of(w, net, B, rx, steps, n_sm):
             peak = peak * NOMINAL_TF32_OVER_BF16 / 3.0
             src += " x 1.1/2.25 (nominal TF32/BF16) / 3 MMAs per useful product (split TF32)"
         elif w.precision == "fp8":
-            peak = peak * NOMINAL_FP8_OVER_BF16
-            src += " x 4.5/2.25 (nominal FP8/BF16 dense)"
+            if FP8_PEAK.get("sustained_tflops"):
+                peak = FP8_PEAK["sustained_tflops"]
+                src = "measured dense E4M3 GEMM, sustained (" + FP8_PEAK["how"] + ") (of measured)"
+            else:
+                peak = peak * NOMINAL_FP8_OVER_BF16
+                src += " x 4.5/2.25 (nominal FP8/BF16 dense)"
         kname = (f"conv_tc_kernel<{w.precision},{net.n_branches},{net.width},{net.width}> "
                  f"(tcgen05 body 3x3 conv, {net.n_branches} branches per launch)")
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -363,6 +411,30 @@ def measure_training(ctx, w, steps, warmup):
             "precision": w.precision, "loss_after": loss}
 
 
+BER_GRIDS = {"plain_14x72": ("plain_14x72_b16_fp32", range(0, 21, 5)),
+             "train_14x72": ("train_14x72_b128_bf16", range(-5, 26, 5)),
+             "interf_14x72": ("interf_14x72_b512_fp8", range(0, 21, 5))}
+
+
+def measure_ber(steps=20_000):
+    """Matched BER: the 14 x 72 CoNet trained on device-simulated slots (BF16 training handle,
+    `steps` steps of 128 slots, Adam 1e-3), then FP32 / BF16 / FP16 / E4M3 and LS-LMMSE on the
+    same 2048 seeded held-out slots per grid point; BER and the gap to FP32 per receiver."""
+    from paper_2510_12739_gb300 import experiments as ex
+    w = WORKLOADS["train_14x72_b128_bf16"]
+    t0 = time.perf_counter()
+    params, losses = ex.train_receiver(w.net, w.sim, steps, batch=w.batch, precision="bf16", lr=1e-3,
+                                       log_every=steps // 4)
+    out = {"network": "14x72 plain CoNet, 2 branches x 4 conv x 32", "train_steps": steps, "batch": w.batch,
+           "train_s": time.perf_counter() - t0, "train_loss": losses, "slots_per_point": 2048, "grids": {}}
+    for name, (wl, snrs) in BER_GRIDS.items():
+        tab = ex.ber_table(w.net, WORKLOADS[wl].sim, params, list(snrs))
+        gap = ex.relative_gap(tab)
+        out["grids"][name] = {str(snr): {k: {"ber": e / n, "errors": e, "gap_vs_fp32": gap[snr][k]}
+                                         for k, (e, n) in row.items()} for snr, row in tab.items()}
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -387,6 +459,10 @@ def main():
     head = measure_inference(ctx, w, B, args.steps, args.warmup, clocks=True, e2e=not args.no_e2e)
 
     variants = {}
+    if (not args.no_variants and not args.batch) or w.precision == "fp8":
+        FP8_PEAK.update(measure_fp8_peak(torch))
+        if w.precision == "fp8":      # the headline's roofline used the nominal ratio: redo it
+            head = measure_inference(ctx, w, B, args.steps, args.warmup, clocks=True, e2e=not args.no_e2e)
     if not args.no_variants and not args.batch:
         for name, prec, steps in [("resid_14x624_b256_fp32", "tf32x3", 10), ("resid_14x624_b256_fp32", "bf16", 10),
                                   ("resid_14x624_b256_fp32", "fp16", 10), ("resnet_14x624_b256_fp32", "fp32", 5),
@@ -404,6 +480,10 @@ def main():
         for prec in ("bf16", "fp32"):
             tw = dataclasses.replace(WORKLOADS["train_14x72_b128_bf16"], precision=prec)
             variants[f"train_14x72_b128:{prec}"] = measure_training(ctx, tw, 20, 3)
+
+    ber = None
+    if rank == 0 and not args.no_ber and not args.batch:
+        ber = measure_ber()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -426,7 +506,7 @@ def main():
                            "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas{world}"},
                 "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head.get("e2e"),
                 "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "step_ms": head["step_ms"],
-                "variants": variants}
+                "fp8_peak": FP8_PEAK or None, "ber": ber, "variants": variants}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
