@@ -1,0 +1,81 @@
+"""Matched BER across precisions on a trained network, and the learned receiver against
+LS-LMMSE (Sec. IV: uncoded BER over an SNR grid is the paper's figure of merit).
+
+The 14 x 72 CoNet (2 branches x 4 conv x 32) is trained on the device-simulated slots of
+the training workload (SNR U(-5, 25) dB, Doppler U(0, 400) Hz) with the BF16 training handle
+for 20 000 steps of 128 slots.  Its FP32, BF16, FP16 and E4M3 receivers and the LS-LMMSE
+receiver then decode the same seeded held-out slots (2048 per point, 7.7 M data bits) at
+every point of three SNR grids: the 14 x 72 plain link (0..20 dB), the training link
+(-5..25 dB) and the interference link (64-QAM interferer, SIR U(0, 20) dB; LS-LMMSE treats
+it as noise).  The comparison is paired, so |BER_p - BER_FP32| / BER_FP32 measures the
+precision alone.
+
+Bars: BF16 and FP16 within 2 % of FP32 at every point with >= 100 FP32 errors.  The trained
+CoNet below LS-LMMSE at every point of the plain and interference grids and up to 15 dB on
+the training grid: above that, the Doppler of up to 400 Hz makes linear interpolation
+between the two pilot symbols beat a network whose 9 x 9 receptive field sees only one of
+them.  E4M3 within 2 % at SNR <= 5 dB and within 25 % everywhere; the strict 2 % bar above
+5 dB is expected to fail (post-training E4M3 quantisation of weights and activations, 3
+mantissa bits, measured up to +19 %) and is recorded as an expected failure."""
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu
+from workloads import WORKLOADS
+
+pytestmark = pytest.mark.gpu
+GRIDS = {"plain": ("plain_14x72_b16_fp32", range(0, 21, 5)), "train": ("train_14x72_b128_bf16", range(-5, 26, 5)),
+         "interf": ("interf_14x72_b512_fp8", range(0, 21, 5))}
+MIN_ERRORS = 100
+
+
+@pytest.fixture(scope="module")
+def tables():
+    need_gpu()
+    from paper_2510_12739_gb300 import experiments as ex
+    w = WORKLOADS["train_14x72_b128_bf16"]
+    params, _ = ex.train_receiver(w.net, w.sim, 20_000, batch=w.batch, precision="bf16", lr=1e-3)
+    out = {}
+    for name, (wl, snrs) in GRIDS.items():
+        out[name] = ex.ber_table(w.net, WORKLOADS[wl].sim, params, list(snrs))
+    return out
+
+
+def _ber(row, k):
+    e, n = row[k]
+    return e / n
+
+
+@pytest.mark.parametrize("grid", sorted(GRIDS))
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_16bit_ber_within_2_percent_of_fp32(tables, grid, prec):
+    for snr, row in tables[grid].items():
+        if row["fp32"][0] < MIN_ERRORS:
+            continue                              # insufficient errors: reported, not judged
+        gap = abs(_ber(row, prec) - _ber(row, "fp32")) / _ber(row, "fp32")
+        assert gap <= 0.02, (grid, snr, prec, gap)
+
+
+@pytest.mark.parametrize("grid", sorted(GRIDS))
+def test_trained_conet_beats_ls_lmmse(tables, grid):
+    for snr, row in tables[grid].items():
+        if grid == "train" and snr > 15:
+            continue
+        e_ls, n_ls = row["ls_lmmse"]
+        sd = np.sqrt(_ber(row, "ls_lmmse") * (1 - _ber(row, "ls_lmmse")) / n_ls)
+        assert _ber(row, "fp32") < _ber(row, "ls_lmmse") - 4 * sd, (grid, snr, row)
+
+
+@pytest.mark.parametrize("grid", sorted(GRIDS))
+def test_e4m3_ber_gap(tables, grid):
+    for snr, row in tables[grid].items():
+        gap = (_ber(row, "fp8") - _ber(row, "fp32")) / _ber(row, "fp32")
+        assert gap <= (0.02 if snr <= 5 else 0.25), (grid, snr, gap)
+
+
+@pytest.mark.xfail(reason="E4M3 post-training quantisation: up to +19 % BER above 5 dB", strict=False)
+@pytest.mark.parametrize("grid", sorted(GRIDS))
+def test_e4m3_ber_within_2_percent_everywhere(tables, grid):
+    for snr, row in tables[grid].items():
+        gap = abs(_ber(row, "fp8") - _ber(row, "fp32")) / _ber(row, "fp32")
+        assert gap <= 0.02, (grid, snr, gap)
