@@ -129,9 +129,12 @@ __device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
   return r;
 }
 
-// Arrive on an mbarrier given by its shared::cluster address (this CTA's or the peer's).
+// Arrive on an mbarrier given by its shared::cluster address (this CTA's or the peer's),
+// with the default CTA-scope release: the arrivals hand back TMEM columns, whose reads the
+// tcgen05 fences order, so no cluster-scope fence (which would wait for every global store
+// the warp still has in flight) is needed.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 
 // TMA tiled loads of one CTA of a pair: the box lands in this CTA's shared memory and its
