@@ -1,4 +1,5 @@
-"""FP64 emulation of the CoNet forward pass with 16-bit (BF16 or FP16) convolution operands.
+"""FP64 emulation of the CoNet forward pass with 16-bit (BF16 or FP16) convolution operands,
+and of the gradient of a 16-bit training step.
 
 TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU baseline use
 this package; the library never calls it.
@@ -9,6 +10,11 @@ accumulate the products in FP32; biases, LayerNorms, the Hadamard fusion, the re
 stream and the 1x1 head stay in FP32.  The emulation rounds exactly those operands to the
 16-bit format and computes everything else in FP64, so it differs from the GPU only by the
 GPU's FP32 rounding (and the rare 16-bit rounding decision that this flips).
+
+A 16-bit training step (grad_16) also runs each body conv's data gradient on 16-bit operands
+(the incoming gradient and the weights) and each conv's weight gradient on 16-bit operands
+(the incoming gradient and the conv's input), accumulating in FP32; the emulation rounds the
+same operands.
 
 Formats (round to nearest, ties to even):
   * BF16: 8 significant bits (1 implicit + 7 stored), FP32's exponent range; in the binade
@@ -52,6 +58,34 @@ class Round16:
 
     def weight(self, w):
         return round16(w, self.fmt)
+
+
+class Round16Train(Round16):
+    """Hooks of a 16-bit training step (oracle.net.conv3x3_rounded): conv inputs, weights and
+    the upstream gradients of every conv are rounded to the format, in the forward and in
+    both gradients.  identity=True rounds nothing (for pins)."""
+
+    def __init__(self, fmt: str = "bf16", identity: bool = False):
+        super().__init__(fmt)
+        self.identity = identity
+
+    def act(self, x):
+        return np.asarray(x, dtype=np.float64) if self.identity else super().act(x)
+
+    def weight(self, w):
+        return np.asarray(w, dtype=np.float64) if self.identity else super().weight(w)
+
+    def grad(self, g):
+        return np.asarray(g, dtype=np.float64) if self.identity else round16(g, self.fmt)
+
+
+def grad_16(cfg, flat, X0, dllr, fmt: str = "bf16"):
+    """Parameter gradient of a 16-bit training step for the upstream LLR gradient dllr:
+    forward on 16-bit conv operands, data and weight gradients from 16-bit gradients, weights
+    and inputs, everything else exact (FP64)."""
+    _, tape = onet.forward(cfg, flat, X0, keep_tape=True, quant=Round16Train(fmt))
+    g, _ = onet.backward(cfg, tape, dllr)
+    return g
 
 
 def forward_16(cfg, flat, X0, fmt: str = "bf16"):

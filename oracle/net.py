@@ -144,6 +144,36 @@ def conv3x3(tp, x, w, b):
     return tp.op(out, (x, w, b), grad)
 
 
+def conv3x3_rounded(tp, x, w, b, q, data_grad=True):
+    """The 3x3 conv of a 16-bit training step (the BF16 training recipe of the training
+    workload: all conv math on BF16 operands, FP32 everything else): the output uses the
+    rounded input and weight, q.act(x) and q.weight(w); the data gradient is the transposed
+    conv of the rounded upstream gradient q.grad(g) with the rounded weight; the weight
+    gradient correlates the rounded upstream gradient with the rounded input.  With identity
+    roundings this is conv3x3 exactly."""
+    X, W, bias = tp[x], tp[w], tp[b]
+    Xq, Wq = q.act(X), q.weight(W)
+    B, T, F, _ = X.shape
+    Xp, Xqp = _pad(X), _pad(Xq)
+    out = np.broadcast_to(bias, (B, T, F, W.shape[0])).copy()
+    for kh in range(3):
+        for kw in range(3):
+            out += Xqp[:, kh:kh + T, kw:kw + F, :] @ Wq[:, kh, kw, :].T
+
+    def grad(g):
+        gq = q.grad(g)
+        dXp = np.zeros_like(Xp)
+        dW = np.zeros_like(W)
+        for kh in range(3):
+            for kw in range(3):
+                if data_grad:
+                    dXp[:, kh:kh + T, kw:kw + F, :] += gq @ Wq[:, kh, kw, :]
+                dW[:, kh, kw, :] = np.einsum("btfo,btfi->oi", gq, Xqp[:, kh:kh + T, kw:kw + F, :])
+        return dXp[:, 1:T + 1, 1:F + 1, :], dW, g.sum(axis=(0, 1, 2))
+
+    return tp.op(out, (x, w, b), grad)
+
+
 def relu(tp, x):
     X = tp[x]
 
@@ -201,11 +231,15 @@ def head1x1(tp, x, w, b):
 
 
 # ----------------------------------------------------------------------------- network
-def forward(cfg, flat, X0, keep_tape=False, quant=None):
+def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
     """LLR [B, T, F, Q] of the CoNet described by ``cfg`` with flat parameters ``flat``.
 
-    ``quant`` (optional, inference only): an object whose ``act(x)`` and ``weight(w)``
-    replace every 3x3 conv's input and weight by their quantised values (oracle.fp8)."""
+    ``quant`` (optional): an object whose ``act(x)`` and ``weight(w)`` replace every 3x3
+    conv's input and weight by their quantised values (oracle.fp8, oracle.half).  When it
+    also has ``grad(g)`` (oracle.half.Round16Train), the convs stay differentiable as in
+    conv3x3_rounded; otherwise the quantised operands are tape leaves (inference only).
+    ``taps`` (optional dict): receives, per fusion point i followed by a LayerNorm, the
+    variance over channels of the fused product at every RE, taps[i] = [B, T, F]."""
     tp = Tape()
     P = unflatten(cfg, np.asarray(flat, dtype=np.float64))
     ids = {k: tp.leaf(v) for k, v in P.items()}
@@ -213,6 +247,8 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None):
     nb = cfg.n_branches
 
     def conv(x, w, b):
+        if quant is not None and hasattr(quant, "grad"):
+            return conv3x3_rounded(tp, x, w, b, quant, data_grad=x != x_in)
         if quant is not None:
             x = tp.leaf(quant.act(tp[x]))
             w = tp.leaf(quant.weight(tp[w]))
@@ -223,6 +259,8 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None):
             return list(acts)
         m = hadamard(tp, acts)
         if cfg.norm:
+            if taps is not None:
+                taps[i] = tp[m].var(axis=-1)
             m = layernorm(tp, m, ids[f"f{i}.g"], ids[f"f{i}.b"])
         return [m] + list(acts[1:])
 

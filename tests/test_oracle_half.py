@@ -72,3 +72,55 @@ def test_hook_rounds_only_conv_operands(fmt):
     assert not np.array_equal(L, exact) or net.depth == 1   # inner activations were rounded
     L_all = half.forward_16(net, flat, X0, fmt)
     assert np.max(np.abs(L_all - onet.forward(net, flat, X0))) <= 40 * unit * np.max(np.abs(L_all))
+
+
+def test_training_conv_reduces_to_the_exact_conv_pieces():
+    """conv3x3_rounded (a 16-bit training step's conv) is assembled from the brute-force-pinned
+    conv3x3: its output is conv3x3 of the rounded input and weight, its data gradient is
+    conv3x3's data gradient at the rounded weight for the rounded upstream gradient, and its
+    weight gradient is conv3x3's at the rounded input for the rounded upstream gradient."""
+    from oracle import net as onet
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((2, 4, 5, 3))
+    W = rng.standard_normal((6, 3, 3, 3))
+    bias = rng.standard_normal(6)
+    G = rng.standard_normal((2, 4, 5, 6))
+    q = half.Round16Train("bf16")
+    tp = onet.Tape()
+    x, w, b = tp.leaf(X), tp.leaf(W), tp.leaf(bias)
+    y = onet.conv3x3_rounded(tp, x, w, b, q)
+    dX, dW, db = tp.recs[y][1](G)
+    ref = onet.Tape()
+    xq, wq, bq = ref.leaf(half.round16(X)), ref.leaf(half.round16(W)), ref.leaf(bias)
+    yq = onet.conv3x3(ref, xq, wq, bq)
+    assert np.allclose(tp[y], ref[yq], rtol=1e-13, atol=1e-13)
+    dX_ref, dW_ref, _ = ref.recs[yq][1](half.round16(G))
+    assert np.allclose(dX, dX_ref, rtol=1e-13, atol=1e-13)
+    assert np.allclose(dW, dW_ref, rtol=1e-13, atol=1e-13) and np.allclose(db, G.sum(axis=(0, 1, 2)))
+    # the misreadings "weight gradient from the unrounded input or gradient" are distinguishable
+    ref2 = onet.Tape()
+    y2 = onet.conv3x3(ref2, ref2.leaf(X), ref2.leaf(W), ref2.leaf(bias))
+    _, dW_wrong, _ = ref2.recs[y2][1](G)
+    assert not np.allclose(dW, dW_wrong, rtol=1e-6)
+    _, dW_wrong2, _ = ref.recs[yq][1](G)
+    assert not np.allclose(dW, dW_wrong2, rtol=1e-6)
+
+
+def test_training_gradient_with_identity_rounding_is_the_exact_gradient():
+    """With roundings that change nothing, grad_16's hooks give the finite-difference-pinned
+    exact gradient of oracle.net (all layers, fusion, LayerNorm, head)."""
+    from oracle import net as onet
+    from workloads import tiny_net
+    for kw in (dict(), dict(norm=1), dict(residual=1, norm=1, n_branches=3)):
+        cfg = tiny_net(**kw)
+        rng = np.random.default_rng(5)
+        flat = onet.init_params(cfg, 2) + 0.1 * rng.standard_normal(onet.param_count(cfg))
+        X0 = rng.standard_normal((2, cfg.n_sym, cfg.n_sc, cfg.c_in))
+        L, tape = onet.forward(cfg, flat, X0, keep_tape=True)
+        dllr = rng.standard_normal(L.shape)
+        g_ref, _ = onet.backward(cfg, tape, dllr)
+        _, tape_i = onet.forward(cfg, flat, X0, keep_tape=True, quant=half.Round16Train(identity=True))
+        g_id, _ = onet.backward(cfg, tape_i, dllr)
+        assert np.allclose(g_id, g_ref, rtol=1e-12, atol=1e-14), kw
+        g16 = half.grad_16(cfg, flat, X0, dllr)
+        assert not np.allclose(g16, g_ref, rtol=1e-4)       # BF16 rounding does move it
