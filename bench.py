@@ -411,6 +411,24 @@ def measure_training(ctx, w, steps, warmup):
             "precision": w.precision, "loss_after": loss}
 
 
+def measure_depth(ctx):
+    """Sec. IV depth comparison (Fig. "InferenceD"): a 14-layer CoNet (4 branches x 64, input
+    + 6 RB/MRB + head) against a 24-layer ResNet (1 x 96, input + 11 RB + head), 1.80 M and
+    1.84 M parameters, on the 2-Rx 14 x 624 link in BF16: latency of one slot (B = 1) and
+    throughput at B = 256, with the library's kernels."""
+    out = {}
+    for name in ("conet_d14_14x624_bf16", "resnet_d24_14x624_bf16"):
+        w = WORKLOADS[name]
+        for B, steps in ((1, 50), (w.batch, 10)):
+            r = measure_inference(ctx, w, B, steps, 3)
+            out[f"{name}@B{B}"] = {"ms_per_step": r["ms_per_step"], "slots_per_s": r["value"]}
+    c1, r1 = out["conet_d14_14x624_bf16@B1"]["ms_per_step"], out["resnet_d24_14x624_bf16@B1"]["ms_per_step"]
+    c2, r2 = (out["conet_d14_14x624_bf16@B256"]["ms_per_step"], out["resnet_d24_14x624_bf16@B256"]["ms_per_step"])
+    out["latency_reduction_B1"] = 1.0 - c1 / r1
+    out["time_reduction_B256"] = 1.0 - c2 / r2
+    return out
+
+
 BER_GRIDS = {"plain_14x72": ("plain_14x72_b16_fp32", range(0, 21, 5)),
              "train_14x72": ("train_14x72_b128_bf16", range(-5, 26, 5)),
              "interf_14x72": ("interf_14x72_b512_fp8", range(0, 21, 5))}
@@ -480,6 +498,7 @@ def main():
         for prec in ("bf16", "fp32"):
             tw = dataclasses.replace(WORKLOADS["train_14x72_b128_bf16"], precision=prec)
             variants[f"train_14x72_b128:{prec}"] = measure_training(ctx, tw, 20, 3)
+        variants["depth_comparison"] = measure_depth(ctx)
 
     ber = None
     if rank == 0 and not args.no_ber and not args.batch:

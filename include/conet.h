@@ -76,6 +76,14 @@ typedef enum {
  *   pilot_syms[0..n_pilot_syms-1], pilot_comb, pilot_seed : the fixed pilot grid
  *       (Sec. II-A: pilots are fixed) -- QPSK pilots on symbols pilot_syms, every
  *       pilot_comb-th subcarrier starting at 0, drawn once from pilot_seed.
+ *   recompute        : residual training handles only: 1 = keep, per block, only the
+ *                      residual streams and recompute each block's inner activations (its
+ *                      pre-activation, first conv and normalisation) from them during the
+ *                      backward pass, per branch and block, instead of storing all four
+ *                      tensors of every block (about 3.5x less activation memory for one
+ *                      more fusion and conv launch per block).  The recomputation runs the
+ *                      same kernels on the same inputs, so gradients are bitwise those of
+ *                      recompute = 0.  Ignored by inference handles and plain networks.
  */
 typedef struct {
   int n_rx, n_sym, n_sc, qam_bits;
@@ -87,6 +95,7 @@ typedef struct {
   int n_pilot_syms;
   int pilot_comb;
   uint64_t pilot_seed;
+  int recompute;               /* 1 = recompute block activations in backward (training) */
 } conet_config;
 
 /*

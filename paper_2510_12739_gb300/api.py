@@ -17,7 +17,7 @@ from ._lib import check, conet_config, conet_sim_params, lib
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3, "tf32x3": 4}
 
 
-def make_config(net, max_batch: int = 1, train: bool = False) -> conet_config:
+def make_config(net, max_batch: int = 1, train: bool = False, recompute: bool = False) -> conet_config:
     c = conet_config()
     c.n_rx, c.n_sym, c.n_sc, c.qam_bits = net.n_rx, net.n_sym, net.n_sc, net.qam_bits
     c.n_branches, c.depth, c.width = net.n_branches, net.depth, net.width
@@ -27,6 +27,7 @@ def make_config(net, max_batch: int = 1, train: bool = False) -> conet_config:
     for i in range(4):
         c.pilot_syms[i] = ps[i] if i < len(ps) else -1
     c.n_pilot_syms, c.pilot_comb, c.pilot_seed = len(ps), net.pilot_comb, net.pilot_seed
+    c.recompute = int(bool(recompute))
     return c
 
 
@@ -70,10 +71,11 @@ class _DevView:
 class Receiver:
     """A CoNet receiver handle (conet_create ... conet_destroy)."""
 
-    def __init__(self, net, precision: str = "fp32", max_batch: int = 1, train: bool = False):
+    def __init__(self, net, precision: str = "fp32", max_batch: int = 1, train: bool = False,
+                 recompute: bool = False):
         self.net = net
         self.precision = precision
-        self.cfg = make_config(net, max_batch, train)
+        self.cfg = make_config(net, max_batch, train, recompute)
         h = C.c_void_p()
         check(lib().conet_create(C.byref(self.cfg), PRECISIONS[precision], C.byref(h)))
         self.h = h

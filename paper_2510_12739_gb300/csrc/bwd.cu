@@ -633,6 +633,12 @@ __global__ void __launch_bounds__(256) wgrad_reduce_rows_kernel(const float* __r
   }
 }
 
+int launch_wgrad_reduce(const float* part, int S, int n_br, int br, int cin, int cout, int cin_src, float* dW,
+                        cudaStream_t s) {
+  wgrad_reduce_rows_kernel<<<(9 * cin * cout + 31) / 32, 256, 0, s>>>(part, S, n_br, br, cin, cout, cin_src, dW);
+  return check_launch("wgrad_reduce_rows_kernel");
+}
+
 int launch_wgrad_tiled(const WgradArgs& a, cudaStream_t s) {
   const int S = wgrad_tiled_splits(a.M, a.n_br);
   int rc = CONET_ERR_UNSUPPORTED;

@@ -20,6 +20,10 @@ int launch_conv_tc_bf16(int nb, int cin, int cout, int mode, const TcMaps& maps,
   TC_CASE(0, 3, 32, 32)
   TC_CASE(0, 1, 16, 112)
   TC_CASE(0, 1, 112, 112)
+  TC_CASE(0, 4, 16, 64)
+  TC_CASE(0, 4, 64, 64)
+  TC_CASE(0, 1, 16, 96)
+  TC_CASE(0, 1, 96, 96)
   return fail(CONET_ERR_UNSUPPORTED, "tensor-core conv kind=%d branches=%d Cin=%d Cout=%d not instantiated", kind, nb,
               cin, cout);
 }

@@ -170,6 +170,18 @@ int launch_wgrad(const WgradArgs& a, cudaStream_t s);
 // wgrad_tiled_splits(M, n_br) * n_br * 9 * cin * cout floats.
 int launch_wgrad_tiled(const WgradArgs& a, cudaStream_t s);
 int wgrad_tiled_splits(long long M, int n_br);
+// Fixed-order sum over S split partials [S][n_br][9][cin][cout] of branch br into the master
+// layout dW [cout][3][3][cin_src].
+int launch_wgrad_reduce(const float* part, int S, int n_br, int br, int cin, int cout, int cin_src, float* dW,
+                        cudaStream_t s);
+// The weight gradient on the tensor cores from BF16 copies of the operands (wgrad_tc.cu):
+// shapes with F % 8 == 0 and (cin padded to 8, cout) in {8, 16, 32} x {32} or {8, 16, 64} x {64};
+// a.part needs wgrad_tc_splits(...) x n_br x 9 x cin_padded x cout floats, `scratch`
+// wgrad_tc_scratch_bytes(...) bytes.
+bool wgrad_tc_supported(int cin, int cout, int F);
+int wgrad_tc_splits(long long slots, int T, int F, int n_br);
+size_t wgrad_tc_scratch_bytes(long long slots, int T, int F, int cin_max, int cout);
+int launch_wgrad_tc(const WgradArgs& a, int slots, void* scratch, int* err, cudaStream_t s);
 
 int launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2, float eps,
                 float bc1, float bc2, cudaStream_t s);

@@ -43,10 +43,13 @@ void prof_end(conet_s* h, cudaStream_t s) {
 namespace {
 
 // Activation buffers.  Inference keeps two residual-stream buffers per branch (ping-pong)
-// plus the two conv inputs of a block; training keeps every layer's tensors for backward.
+// plus the two conv inputs of a block; training keeps every layer's tensors for backward,
+// or (residual networks with recompute) the streams of every block and one block's inner
+// tensors (H1, T1, H2), which the backward pass recomputes block by block.
 struct Acts {
   conet_s* h;
   bool train() const { return h->cfg.train != 0; }
+  bool rc() const { return train() && h->cfg.residual && h->cfg.recompute; }
   float* at(size_t i) const { return h->act[i]; }
   int nb() const { return h->nb; }
   int depth() const { return h->cfg.depth; }
@@ -59,10 +62,20 @@ struct Acts {
     return train() ? at(nb() + k) : at((size_t)(k & 1) * nb());
   }
   size_t rbase() const { return (size_t)nb() + depth() + 1; }
-  float* H1(int k, int b) const { return train() ? at(rbase() + ((size_t)k * 4 + 0) * nb() + b) : at(2 * nb() + b); }
-  float* T1(int k, int b) const { return train() ? at(rbase() + ((size_t)k * 4 + 1) * nb() + b) : nullptr; }
-  float* H2(int k, int b) const { return train() ? at(rbase() + ((size_t)k * 4 + 2) * nb() + b) : at(3 * nb() + b); }
-  float* U(int k, int b) const { return train() ? at(rbase() + ((size_t)k * 4 + 3) * nb() + b) : at((size_t)((k + 1) & 1) * nb() + b); }
+  float* H1(int k, int b) const {
+    return rc() ? at(rbase() + b) : train() ? at(rbase() + ((size_t)k * 4 + 0) * nb() + b) : at(2 * nb() + b);
+  }
+  float* T1(int k, int b) const {
+    return rc() ? at(rbase() + nb() + b) : train() ? at(rbase() + ((size_t)k * 4 + 1) * nb() + b) : nullptr;
+  }
+  float* H2(int k, int b) const {
+    return rc() ? at(rbase() + 2 * nb() + b) : train() ? at(rbase() + ((size_t)k * 4 + 2) * nb() + b) : at(3 * nb() + b);
+  }
+  float* U(int k, int b) const {
+    return rc()      ? at(rbase() + ((size_t)3 + k) * nb() + b)
+           : train() ? at(rbase() + ((size_t)k * 4 + 3) * nb() + b)
+                     : at((size_t)((k + 1) & 1) * nb() + b);
+  }
   float* XS(int k, int b) const {   // residual stream entering block k
     if (b == 0) return RXM(k);
     return k == 0 ? A0(b) : U(k - 1, b);
@@ -71,6 +84,7 @@ struct Acts {
     const int nb = h->nb, d = h->cfg.depth;
     const bool tc = h->prec != CONET_FP32;   // tensor-core inference keeps its conv inputs in 16 bits
     if (!h->cfg.residual) return h->cfg.train ? (size_t)d * nb + d : (tc ? 0 : 2 * (size_t)nb);
+    if (h->cfg.train && h->cfg.recompute) return (size_t)nb + d + 1 + (3 + (size_t)d) * nb;
     return h->cfg.train ? (size_t)nb + d + 1 + 4 * (size_t)d * nb : (tc ? 2 : 4) * (size_t)nb;
   }
 };
@@ -146,6 +160,9 @@ int net_setup(conet_s* h) {
     CONET_TRY(dev_alloc_t(h, &h->wd, wd ? wd : 1));
     h->tc_dgrad = h->prec == CONET_BF16;
     if (h->tc_dgrad) {
+      const int cinp0 = (h->c_pad + 7) / 8 * 8;
+      CONET_TRY(dev_alloc(h, &h->wg_tc,
+                          wgrad_tc_scratch_bytes(h->cfg.max_batch, h->T, h->F, h->C > cinp0 ? h->C : cinp0, h->C)));
       CONET_TRY(dev_alloc(h, &h->wd16, (wd ? wd : 1) * sizeof(uint16_t)));
       for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc(h, &h->g16[b], re * h->C * sizeof(uint16_t)));
       CONET_TRY(dev_alloc_t(h, &h->zero_c, (size_t)h->C));
@@ -164,6 +181,10 @@ int net_setup(conet_s* h) {
     CONET_TRY(dev_alloc_t(h, &h->llr, re * h->Q));
     CONET_TRY(dev_alloc_t(h, &h->dllr, re * h->Q));
   }
+  // device status words: [0] the site of the first timed-out pipeline wait, [1] set when a
+  // forward pass wrote a non-finite LLR (both read and cleared by conet_sync)
+  CONET_TRY(dev_alloc_t(h, &h->d_err, 2));
+  CONET_CUDA(cudaMemset(h->d_err, 0, 2 * sizeof(int)));
   CONET_TRY(tc_setup(h));
   CONET_CUDA(cudaDeviceSynchronize());
   return CONET_OK;
@@ -212,6 +233,7 @@ static FuseArgs fuse_args(conet_s* h, int B) {
   f.C = h->C;
   f.Q = h->Q;
   f.M = (long long)B * h->T * h->F;
+  f.nonfinite = h->d_err + 1;
   return f;
 }
 
@@ -278,6 +300,63 @@ int net_forward_replay(conet_s* h, const float* Y, const uint8_t* mask, int B, f
   return CONET_OK;
 }
 
+// One stage of the FP32 residual forward: the fusion after the input layer (k = 0) or after
+// block k-1, then block k's pre-activation (or the head after the last block).
+static int resid_fuse(conet_s* h, int k, int B, float* llr, cudaStream_t s) {
+  const Acts A{h};
+  const Layout& L = h->L;
+  const int nb = h->nb, depth = h->cfg.depth;
+  FuseArgs f = fuse_args(h, B);
+  for (int b = 0; b < nb; ++b) f.u[b] = k == 0 ? A.A0(b) : A.U(k - 1, b);
+  f.fuse = fused_at(h->cfg, k);
+  f.fuse_g = P(h, L.fg[k]);
+  f.fuse_b = P(h, L.fb[k]);
+  f.x0_out = A.RXM(k);
+  if (k < depth) {
+    for (int b = 0; b < nb; ++b) {
+      f.h_out[b] = A.H1(k, b);
+      f.ln1_g[b] = P(h, L.blk[b][k].ln1g);
+      f.ln1_b[b] = P(h, L.blk[b][k].ln1b);
+    }
+  } else {
+    f.head_w = P(h, L.hw);
+    f.head_b = P(h, L.hb);
+    f.llr = llr;
+  }
+  return fuse_stage(h, f, s);
+}
+
+// Block k's first conv (LN2 + ReLU epilogue) and second conv (residual add).
+static int resid_conv1(conet_s* h, int k, int B, cudaStream_t s) {
+  const Acts A{h};
+  const Layout& L = h->L;
+  ConvArgs c1 = conv_args(h, B);
+  for (int b = 0; b < h->nb; ++b) {
+    c1.in[b] = A.H1(k, b);
+    c1.w[b] = W(h, L.blk[b][k].c1w);
+    c1.bias[b] = P(h, L.blk[b][k].c1b);
+    c1.out0[b] = A.T1(k, b);
+    c1.out1[b] = A.H2(k, b);
+    c1.ln_g[b] = P(h, L.blk[b][k].ln2g);
+    c1.ln_b[b] = P(h, L.blk[b][k].ln2b);
+  }
+  return conv_layer(h, c1, h->C, s);
+}
+
+static int resid_conv2(conet_s* h, int k, int B, cudaStream_t s) {
+  const Acts A{h};
+  const Layout& L = h->L;
+  ConvArgs c2 = conv_args(h, B);
+  for (int b = 0; b < h->nb; ++b) {
+    c2.in[b] = A.H2(k, b);
+    c2.w[b] = W(h, L.blk[b][k].c2w);
+    c2.bias[b] = P(h, L.blk[b][k].c2b);
+    c2.resid[b] = A.XS(k, b);
+    c2.out0[b] = A.U(k, b);
+  }
+  return conv_layer(h, c2, h->C, s);
+}
+
 int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s) {
   if (h->prec == CONET_BF16 || h->prec == CONET_FP16 || h->prec == CONET_TF32X3 || h->prec == CONET_FP8E4M3)
     return net_forward_tc(h, Y, mask, B, llr, s);
@@ -323,47 +402,10 @@ int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* l
     c.relu0 = 1;
     CONET_TRY(conv_layer(h, c, h->c_pad, s));
     for (int k = 0; k <= depth; ++k) {
-      // fusion after the input layer (k = 0) or after block k-1, then the next block's
-      // pre-activation (or the head after the last block)
-      FuseArgs f = fuse_args(h, B);
-      for (int b = 0; b < nb; ++b) f.u[b] = k == 0 ? A.A0(b) : A.U(k - 1, b);
-      f.fuse = fused_at(h->cfg, k);
-      f.fuse_g = P(h, L.fg[k]);
-      f.fuse_b = P(h, L.fb[k]);
-      f.x0_out = A.RXM(k);
-      if (k < depth) {
-        for (int b = 0; b < nb; ++b) {
-          f.h_out[b] = A.H1(k, b);
-          f.ln1_g[b] = P(h, L.blk[b][k].ln1g);
-          f.ln1_b[b] = P(h, L.blk[b][k].ln1b);
-        }
-      } else {
-        f.head_w = P(h, L.hw);
-        f.head_b = P(h, L.hb);
-        f.llr = llr;
-      }
-      CONET_TRY(fuse_stage(h, f, s));
+      CONET_TRY(resid_fuse(h, k, B, llr, s));
       if (k == depth) break;
-      ConvArgs c1 = conv_args(h, B);
-      for (int b = 0; b < nb; ++b) {
-        c1.in[b] = A.H1(k, b);
-        c1.w[b] = W(h, L.blk[b][k].c1w);
-        c1.bias[b] = P(h, L.blk[b][k].c1b);
-        c1.out0[b] = A.T1(k, b);
-        c1.out1[b] = A.H2(k, b);
-        c1.ln_g[b] = P(h, L.blk[b][k].ln2g);
-        c1.ln_b[b] = P(h, L.blk[b][k].ln2b);
-      }
-      CONET_TRY(conv_layer(h, c1, h->C, s));
-      ConvArgs c2 = conv_args(h, B);
-      for (int b = 0; b < nb; ++b) {
-        c2.in[b] = A.H2(k, b);
-        c2.w[b] = W(h, L.blk[b][k].c2w);
-        c2.bias[b] = P(h, L.blk[b][k].c2b);
-        c2.resid[b] = A.XS(k, b);
-        c2.out0[b] = A.U(k, b);
-      }
-      CONET_TRY(conv_layer(h, c2, h->C, s));
+      CONET_TRY(resid_conv1(h, k, B, s));
+      CONET_TRY(resid_conv2(h, k, B, s));
     }
   }
   h->fwd_B = B;
@@ -433,7 +475,6 @@ int tc_setup(conet_s* h) {
   if (h->cin > cin0) return fail(CONET_ERR_UNSUPPORTED, "tensor-core path takes at most %d input channels", cin0);
   if (h->C % 16) return fail(CONET_ERR_UNSUPPORTED, "tensor-core path needs width %% 16 == 0");
   if (kind == 2 && h->C % 32) return fail(CONET_ERR_UNSUPPORTED, "E4M3 path needs width %% 32 == 0");
-  if (kind == 2 && h->cfg.train) return fail(CONET_ERR_UNSUPPORTED, "E4M3 handles are inference-only (train = 0)");
   const size_t re = (size_t)h->chunk * h->T * h->F;
   const size_t e = (size_t)tc_elt(kind);
   const bool split = kind == 1;
@@ -465,8 +506,6 @@ int tc_setup(conet_s* h) {
     CONET_TRY(dev_alloc_t(h, &h->fp8_amax, (size_t)n * h->nb));
     CONET_CUDA(cudaMemset(h->fp8_act, 0, (size_t)n * h->nb * (h->C + FP8_REC_PAD) * sizeof(float)));
   }
-  CONET_TRY(dev_alloc_t(h, &h->d_err, 1));
-  CONET_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
   h->tcmaps.resize(n);
   for (int idx = 0; idx < n; ++idx) {
     const int cin = idx == 0 ? cin0 : h->C;
@@ -516,6 +555,7 @@ static int tc_conv(conet_s* h, int idx, TcConvArgs& a, int B, cudaStream_t s) {
   a.n_tiles = B * h->T * a.nfb;
   a.Q = h->Q;
   a.err = h->d_err;
+  a.nonfinite = h->d_err + 1;
   const int cin = idx == 0 ? tc_cin0(tc_kind(h)) : h->C;
   prof_begin(h, idx == 0 ? PK_CONV_IN : PK_CONV, s);
   const int rc = launch_conv_tc(tc_kind(h), h->nb, cin, h->C, h->tcmaps[idx], a, s);
@@ -710,7 +750,10 @@ struct Bwd {
     w.F = h->F;
     w.M = M;
     prof_begin(h, PK_BACKWARD, s);
-    const int rc = launch_wgrad_tiled(w, s);
+    // BF16 training: BF16 operands on the tensor cores where the shape is instantiated
+    const int rc = h->tc_dgrad && wgrad_tc_supported(cin_pad, h->C, h->F)
+                       ? launch_wgrad_tc(w, (int)(M / ((long long)h->T * h->F)), h->wg_tc, h->d_err, s)
+                       : launch_wgrad_tiled(w, s);
     prof_end(h, s);
     CONET_TRY(rc);
     for (int b = 0; b < h->nb; ++b) CONET_TRY(bias(g[b], b_off[b]));
@@ -750,6 +793,7 @@ struct Bwd {
       a.n_tiles = (int)(M / ((long long)h->T * h->F)) * h->T * a.nfb;
       a.Q = h->Q;
       a.err = h->d_err;
+      a.nonfinite = h->d_err + 1;
       for (int b = 0; b < h->nb; ++b) {
         a.bias[b] = h->zero_c;
         a.t_out[b] = out[b];
@@ -812,8 +856,7 @@ struct Bwd {
 }  // namespace
 
 int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
-  if (h->prec != CONET_FP32 &&
-      ((h->prec != CONET_BF16 && h->prec != CONET_FP16 && h->prec != CONET_TF32X3) || h->cfg.residual))
+  if (h->prec != CONET_FP32 && h->cfg.residual)
     return fail(CONET_ERR_UNSUPPORTED, "precision %d backward of this network not built yet", h->prec);
   const Acts A{h};
   const Layout& L = h->L;
@@ -858,6 +901,12 @@ int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
     float* const* gxs = nulw;
     for (int k = depth; k >= 1; --k) {
       const int blk = k - 1;
+      if (A.rc()) {
+        // this block's pre-activation, first conv and normalisation again, from the stored
+        // streams, by the forward's own kernels (bitwise the forward's values)
+        CONET_TRY(resid_fuse(h, blk, B, nullptr, s));
+        CONET_TRY(resid_conv1(h, blk, B, s));
+      }
       const float* u[MAX_BR];
       for (int b = 0; b < nb; ++b) u[b] = A.U(blk, b);
       CONET_TRY(bw.fuse(u, G0[0], gxs, G1, k, 0));                       // G1 = d u

@@ -64,6 +64,7 @@ struct conet_s {
   float* G[3][conet::MAX_BR] = {};           // gradient buffers (train), max_batch*T*F*C each
   float* ew_part = nullptr;                  // partial sums of the elementwise backward kernels
   float* wg_part = nullptr;                  // split partials of the weight gradient
+  void* wg_tc = nullptr;                     // BF16 training: transposed operand copies of the tensor-core wgrad
   int n_pilot_re = 0;
   // tensor-core (BF16) path
   void* X0b = nullptr;                       // assembled input, BF16 [B][T][F][16]

@@ -55,6 +55,10 @@ int main() {
   check_plan<2, 3, 64, 64>();
   check_plan<2, 4, 96, 96>();
   check_plan<2, 2, 32, 32>();
+  check_plan<0, 4, 16, 64>();
+  check_plan<0, 4, 64, 64>();
+  check_plan<0, 1, 16, 96>();
+  check_plan<0, 1, 96, 96>();
 
   static float buf[64];
   // conv1 of a residual block: LN2 + ReLU, next input only

@@ -53,3 +53,15 @@ def test_resnet_matches_the_conet_parameter_count():
     assert resnet.resnet_baseline and resnet.n_branches == 1 and resnet.depth == conet.depth
     ratio = _n_params(resnet) / _n_params(conet)
     assert abs(ratio - 1) < 0.05, ratio
+
+
+def test_depth_comparison_networks():
+    """The 14-layer CoNet and the 24-layer ResNet of the depth comparison (Sec. IV, Fig.
+    "InferenceD"): sequential layers = input conv + 2 per block + head, both near 1.9 M
+    parameters and within 5 % of each other."""
+    c = WORKLOADS["conet_d14_14x624_bf16"].net
+    r = WORKLOADS["resnet_d24_14x624_bf16"].net
+    assert 1 + 2 * c.depth + 1 == 14 and 1 + 2 * r.depth + 1 == 24
+    assert c.n_branches > 1 and r.resnet_baseline and r.n_branches == 1
+    nc, nr = _n_params(c), _n_params(r)
+    assert 1.7e6 < nc < 2.1e6 and 1.7e6 < nr < 2.1e6 and abs(nc / nr - 1) < 0.05, (nc, nr)

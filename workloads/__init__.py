@@ -103,6 +103,13 @@ _SIM4 = replace(_SIM2, snr_lo=0.0, snr_hi=30.0)
 
 _SIM5 = replace(_SIM3, interferer=1, sir_lo=0.0, sir_hi=20.0, iqam_bits=6)
 
+# Depth comparison of Sec. IV (Fig. "InferenceD"): a CoNet of 14 sequential layers (input
+# conv, 6 RB / MRB blocks of two convs, 1x1 head) against a single-branch pre-activation
+# ResNet of 24 (input conv, 11 blocks, head), both near 1.9 M parameters, on the 14 x 624 link.
+_NET_D14 = NetConfig(n_rx=2, n_sc=624, qam_bits=6, n_branches=4, depth=6, width=64, residual=1, norm=1)
+_NET_D24 = NetConfig(n_rx=2, n_sc=624, qam_bits=6, n_branches=1, depth=11, width=96, residual=1, norm=1,
+                     resnet_baseline=1)
+
 WORKLOADS = {
     "plain_14x72_b16_fp32": Workload(
         "plain_14x72_b16_fp32", _NET1, _SIM1, 16, "fp32",
@@ -122,6 +129,12 @@ WORKLOADS = {
     "interf_14x72_b512_fp8": Workload(
         "interf_14x72_b512_fp8", _NET1, _SIM5, 512, "fp8",
         description="14x72 plain CoNet with a co-channel 64-QAM interferer, SIR U(0,20) dB"),
+    "conet_d14_14x624_bf16": Workload(
+        "conet_d14_14x624_bf16", _NET_D14, _SIM2, 256, "bf16",
+        description="14-layer CoNet, 4 branches x (input + 6 RB/MRB) x 64, 1.78 M parameters"),
+    "resnet_d24_14x624_bf16": Workload(
+        "resnet_d24_14x624_bf16", _NET_D24, _SIM2, 256, "bf16",
+        description="24-layer pre-activation ResNet, 1 branch x (input + 11 RB) x 96, 1.83 M parameters"),
 }
 
 
