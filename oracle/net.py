@@ -221,6 +221,13 @@ def add(tp, x, y):
     return tp.op(tp[x] + tp[y], (x, y), lambda g: (g, g))
 
 
+def add_all(tp, xs):
+    out = xs[0]
+    for x in xs[1:]:
+        out = add(tp, out, x)
+    return out
+
+
 def head1x1(tp, x, w, b):
     X, W, bias = tp[x], tp[w], tp[b]
 
@@ -255,13 +262,18 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
         return conv3x3(tp, x, w, b)
 
     def fuse(i, acts):
+        # fusion point i: the main activation becomes the interaction of all branches' (the
+        # product, or the sum, reading the interaction operations of Sec. III), normalised;
+        # supports keep their own activation, plus the main's with Example II's feedback
         if not cfg.fused(i):
             return list(acts)
-        m = hadamard(tp, acts)
+        m = add_all(tp, acts) if getattr(cfg, "fuse_op", 0) == 1 else hadamard(tp, acts)
         if cfg.norm:
             if taps is not None:
                 taps[i] = tp[m].var(axis=-1)
             m = layernorm(tp, m, ids[f"f{i}.g"], ids[f"f{i}.b"])
+        if getattr(cfg, "feedback", 0):
+            return [m] + [add(tp, a, acts[0]) for a in acts[1:]]
         return [m] + list(acts[1:])
 
     acts = [relu(tp, conv(x_in, ids[f"b{b}.in.w"], ids[f"b{b}.in.b"])) for b in range(nb)]

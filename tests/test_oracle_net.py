@@ -117,6 +117,43 @@ def test_support_branches_commute(residual):
     assert not np.allclose(onet.forward(cfg, flat, X0), onet.forward(cfg, M, X0))
 
 
+def test_sum_fusion_with_silent_supports_leaves_the_main_net():
+    """Sum interaction (fuse_op = 1): support branches whose activations are 0 (weights and
+    biases 0, so ReLU gives 0) add nothing, and the CoNet is the main net alone."""
+    cfg = tiny_net(n_branches=3, depth=3, width=4, fuse_op=1)
+    single = replace(cfg, n_branches=1)
+    flat = onet.init_params(cfg, 5)
+    for b in (1, 2):
+        for l in range(cfg.depth):
+            key = "in" if l == 0 else f"l{l}"
+            _set(cfg, flat, f"b{b}.{key}.w", 0.0)
+            _set(cfg, flat, f"b{b}.{key}.b", 0.0)
+    P = onet.unflatten(cfg, flat)
+    flat1 = np.concatenate([P[n].ravel() for n, _ in onet.param_layout(single)])
+    X0, _, _ = _inputs(cfg, 3)
+    assert np.allclose(onet.forward(cfg, flat, X0), onet.forward(single, flat1, X0), atol=1e-12)
+
+
+def test_sum_fusion_and_feedback_by_hand():
+    """One fused input layer (depth 1 would fuse once and feed the head): with two branches
+    and brute-force convs, x_main = a0 + a1 (sum interaction) or a0 * a1, and after a second
+    layer Example II's support input is a1 + a0 (feedback) rather than a1."""
+    for fuse_op in (0, 1):
+        for feedback in (0, 1):
+            cfg = tiny_net(n_branches=2, depth=2, width=3, fuse_op=fuse_op, feedback=feedback)
+            flat = onet.init_params(cfg, 21) + 0.05
+            P = onet.unflatten(cfg, flat)
+            X0, _, _ = _inputs(cfg, 22)
+            a = [np.maximum(brute_conv(X0, P[f"b{b}.in.w"], P[f"b{b}.in.b"]), 0) for b in range(2)]
+            x0 = a[0] + a[1] if fuse_op else a[0] * a[1]
+            x1 = a[1] + a[0] if feedback else a[1]
+            c = [np.maximum(brute_conv(x0, P["b0.l1.w"], P["b0.l1.b"]), 0),
+                 np.maximum(brute_conv(x1, P["b1.l1.w"], P["b1.l1.b"]), 0)]
+            y0 = c[0] + c[1] if fuse_op else c[0] * c[1]
+            want = y0 @ P["head.w"].T + P["head.b"]
+            assert np.allclose(onet.forward(cfg, flat, X0), want, atol=1e-10), (fuse_op, feedback)
+
+
 def test_identity_residual_blocks_reduce_to_fused_input_layer():
     cfg = tiny_net(n_branches=2, depth=2, width=4, residual=1, norm=1)
     flat = onet.init_params(cfg, 9)
@@ -149,6 +186,9 @@ FD_CASES = [
     dict(residual=1, norm=1, n_branches=3, depth=1),
     dict(n_branches=1, residual=1, norm=1, resnet_baseline=1, width=4),
     dict(fuse_mask=0b01),
+    dict(fuse_op=1, norm=1, n_branches=3),
+    dict(feedback=1, n_branches=3),
+    dict(feedback=1, fuse_op=1, residual=1, norm=1),
 ]
 
 

@@ -33,6 +33,10 @@ class NetConfig:
     fuse_mask: bit i set = Hadamard fusion after layer/block i (bit 0 = input layer).
     resnet_baseline: 1 = a single pre-activation ResNet branch, no fusion (the
         DeepRx-style comparison network).
+    fuse_op: the interaction operation at a fusion point (Sec. III lists multiplication,
+        addition and concatenation): 0 = element-wise product, 1 = element-wise sum.
+    feedback: 1 = Example II (Sec. III, Fig. "conet2"): at every fusion point each support
+        net continues with its own activation plus the main net's (before the fusion).
     """
     n_rx: int
     n_sc: int
@@ -44,6 +48,8 @@ class NetConfig:
     norm: int = 0
     fuse_mask: int = -1
     resnet_baseline: int = 0
+    fuse_op: int = 0
+    feedback: int = 0
     n_sym: int = 14
     pilot_syms: tuple = (2, 11)
     pilot_comb: int = 2
