@@ -45,9 +45,15 @@ def param_layout(cfg):
             for k in range(cfg.depth):
                 if b >= 1 or cfg.resnet_baseline:
                     out += [(f"b{b}.k{k}.ln1.g", (C,)), (f"b{b}.k{k}.ln1.b", (C,))]
-                out += [(f"b{b}.k{k}.c1.w", (C, 3, 3, C)), (f"b{b}.k{k}.c1.b", (C,)),
-                        (f"b{b}.k{k}.ln2.g", (C,)), (f"b{b}.k{k}.ln2.b", (C,)),
-                        (f"b{b}.k{k}.c2.w", (C, 3, 3, C)), (f"b{b}.k{k}.c2.b", (C,))]
+                if getattr(cfg, "depthwise", 0):
+                    # depthwise-separable convs: a per-channel 3x3 then a 1x1 with bias
+                    out += [(f"b{b}.k{k}.c1.dw", (C, 3, 3)), (f"b{b}.k{k}.c1.w", (C, C)), (f"b{b}.k{k}.c1.b", (C,)),
+                            (f"b{b}.k{k}.ln2.g", (C,)), (f"b{b}.k{k}.ln2.b", (C,)),
+                            (f"b{b}.k{k}.c2.dw", (C, 3, 3)), (f"b{b}.k{k}.c2.w", (C, C)), (f"b{b}.k{k}.c2.b", (C,))]
+                else:
+                    out += [(f"b{b}.k{k}.c1.w", (C, 3, 3, C)), (f"b{b}.k{k}.c1.b", (C,)),
+                            (f"b{b}.k{k}.ln2.g", (C,)), (f"b{b}.k{k}.ln2.b", (C,)),
+                            (f"b{b}.k{k}.c2.w", (C, 3, 3, C)), (f"b{b}.k{k}.c2.b", (C,))]
     if cfg.norm:
         n_points = cfg.depth + 1 if cfg.residual else cfg.depth
         for i in range(n_points):
@@ -77,7 +83,9 @@ def init_params(cfg, seed: int) -> np.ndarray:
     g = np.random.default_rng(seed)
     parts = []
     for name, shape in param_layout(cfg):
-        if name.endswith(".w"):
+        if name.endswith(".dw"):
+            parts.append(g.standard_normal(shape).ravel() * np.sqrt(2.0 / 9.0))
+        elif name.endswith(".w"):
             fan_in = int(np.prod(shape[1:]))
             parts.append(g.standard_normal(shape).ravel() * np.sqrt(2.0 / fan_in))
         elif name.endswith(".g"):
@@ -172,6 +180,29 @@ def conv3x3_rounded(tp, x, w, b, q, data_grad=True):
         return dXp[:, 1:T + 1, 1:F + 1, :], dW, g.sum(axis=(0, 1, 2))
 
     return tp.op(out, (x, w, b), grad)
+
+
+def dwconv3x3(tp, x, w):
+    """Depthwise 3x3 'same' conv: out[..., c] = sum over (kh, kw) of x shifted by (kh - 1,
+    kw - 1) (zero outside) times w[c, kh, kw]; no bias (the following 1x1 conv has one)."""
+    X, W = tp[x], tp[w]
+    B, T, F, _ = X.shape
+    Xp = _pad(X)
+    out = np.zeros_like(X)
+    for kh in range(3):
+        for kw in range(3):
+            out += Xp[:, kh:kh + T, kw:kw + F, :] * W[:, kh, kw]
+
+    def grad(g):
+        dXp = np.zeros_like(Xp)
+        dW = np.zeros_like(W)
+        for kh in range(3):
+            for kw in range(3):
+                dXp[:, kh:kh + T, kw:kw + F, :] += g * W[:, kh, kw]
+                dW[:, kh, kw] = np.einsum("btfc,btfc->c", g, Xp[:, kh:kh + T, kw:kw + F, :])
+        return dXp[:, 1:T + 1, 1:F + 1, :], dW
+
+    return tp.op(out, (x, w), grad)
 
 
 def relu(tp, x):
@@ -276,6 +307,13 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
             return [m] + [add(tp, a, acts[0]) for a in acts[1:]]
         return [m] + list(acts[1:])
 
+    def block_conv(x, name):
+        # a residual block's conv: standard 3x3, or depthwise-separable (per-channel 3x3, then
+        # 1x1 with bias: "depthwise convolutions" of Sec. II-A / III)
+        if getattr(cfg, "depthwise", 0):
+            return head1x1(tp, dwconv3x3(tp, x, ids[name + ".dw"]), ids[name + ".w"], ids[name + ".b"])
+        return conv(x, ids[name + ".w"], ids[name + ".b"])
+
     acts = [relu(tp, conv(x_in, ids[f"b{b}.in.w"], ids[f"b{b}.in.b"])) for b in range(nb)]
     x = fuse(0, acts)
     if not cfg.residual:
@@ -292,9 +330,9 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
                     h1 = relu(tp, layernorm(tp, x[b], ids[p + "ln1.g"], ids[p + "ln1.b"]))
                 else:
                     h1 = relu(tp, x[b])
-                t1 = conv(h1, ids[p + "c1.w"], ids[p + "c1.b"])
+                t1 = block_conv(h1, p + "c1")
                 h2 = relu(tp, layernorm(tp, t1, ids[p + "ln2.g"], ids[p + "ln2.b"]))
-                u.append(add(tp, x[b], conv(h2, ids[p + "c2.w"], ids[p + "c2.b"])))
+                u.append(add(tp, x[b], block_conv(h2, p + "c2")))
             x = fuse(k + 1, u)
     llr = head1x1(tp, x[0], ids["head.w"], ids["head.b"])
     if keep_tape:

@@ -189,6 +189,7 @@ FD_CASES = [
     dict(fuse_op=1, norm=1, n_branches=3),
     dict(feedback=1, n_branches=3),
     dict(feedback=1, fuse_op=1, residual=1, norm=1),
+    dict(depthwise=1, residual=1, norm=1, width=4),
 ]
 
 
@@ -255,3 +256,38 @@ def test_cropped_receptive_field_is_exact(name, kw):
     for f in (0, 1, net.n_sc // 2, net.n_sc - 1):
         crop = oracle_llr_at(net, p, ref["Y32"][0], ref["pilot_sym"], ref["pilot_mask"], f)
         assert np.max(np.abs(crop - full[0, :, f, :])) < 1e-12
+
+
+def test_depthwise_conv_matches_brute_force():
+    g = np.random.default_rng(31)
+    X = g.standard_normal((2, 4, 5, 3))
+    W = g.standard_normal((3, 3, 3))
+    tp = onet.Tape()
+    y = tp[onet.dwconv3x3(tp, tp.leaf(X), tp.leaf(W))]
+    want = np.zeros_like(X)
+    for b, t, f, c in itertools.product(range(2), range(4), range(5), range(3)):
+        for kh in range(3):
+            for kw in range(3):
+                tt, ff = t + kh - 1, f + kw - 1
+                if 0 <= tt < 4 and 0 <= ff < 5:
+                    want[b, t, f, c] += X[b, tt, ff, c] * W[c, kh, kw]
+    assert np.allclose(y, want, atol=1e-12)
+    # a depthwise conv equals the standard conv whose weight is diagonal in the channels
+    Wfull = np.zeros((3, 3, 3, 3))
+    for c in range(3):
+        Wfull[c, :, :, c] = W[c]
+    assert np.allclose(y, brute_conv(X, Wfull, np.zeros(3)), atol=1e-12)
+
+
+def test_depthwise_block_is_the_separable_composition():
+    """A depthwise residual network's block conv is the per-channel 3x3 then the 1x1 with
+    bias: with the 1x1 weight the identity and zero bias, the block conv is the depthwise
+    conv alone; the parameter count is 9 C + C^2 + C per block conv."""
+    cfg = tiny_net(residual=1, norm=1, depthwise=1, width=4)
+    std = replace(cfg, depthwise=0)
+    C = cfg.width
+    per_conv_dw, per_conv_std = 9 * C + C * C + C, 9 * C * C + C
+    n_convs = 2 * cfg.depth * cfg.n_branches
+    assert onet.param_count(std) - onet.param_count(cfg) == n_convs * (per_conv_std - per_conv_dw)
+    names = [n for n, _ in onet.param_layout(cfg)]
+    assert "b0.k0.c1.dw" in names and "b1.k1.c2.w" in names

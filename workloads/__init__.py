@@ -37,6 +37,8 @@ class NetConfig:
         addition and concatenation): 0 = element-wise product, 1 = element-wise sum.
     feedback: 1 = Example II (Sec. III, Fig. "conet2"): at every fusion point each support
         net continues with its own activation plus the main net's (before the fusion).
+    depthwise: 1 = the convs inside RB / MRB blocks are depthwise-separable: a per-channel
+        3x3 conv followed by a 1x1 conv with bias (Sec. II-A, Sec. III).
     """
     n_rx: int
     n_sc: int
@@ -50,6 +52,7 @@ class NetConfig:
     resnet_baseline: int = 0
     fuse_op: int = 0
     feedback: int = 0
+    depthwise: int = 0
     n_sym: int = 14
     pilot_syms: tuple = (2, 11)
     pilot_comb: int = 2
