@@ -84,6 +84,20 @@ typedef enum {
  *                      more fusion and conv launch per block).  The recomputation runs the
  *                      same kernels on the same inputs, so gradients are bitwise those of
  *                      recompute = 0.  Ignored by inference handles and plain networks.
+ *   fuse_op          : the interaction at a fusion point (Sec. III: multiplication,
+ *                      addition or concatenation of the subnets' activations): 0 = the
+ *                      element-wise product (default), 1 = the element-wise sum.
+ *   feedback         : 1 = Example II (Sec. III, Fig. "conet2"): at every fusion point each
+ *                      support net continues with its own activation plus the main net's
+ *                      (taken before the fusion).
+ *   fuse_op = 1 and feedback = 1 are inference-only (train = 1 returns
+ *   CONET_ERR_UNSUPPORTED), and on the tensor-core paths need a network whose accumulators
+ *   fit TMEM twice (not the 4 x 96 network).
+ *   depthwise        : residual networks: 1 = every conv inside an RB / MRB is depthwise-
+ *                      separable (Sec. II-A, Sec. III): a per-channel 3x3 'same' conv without
+ *                      bias, then a 1x1 conv with bias.  Flat layout of such a conv: depthwise
+ *                      W [C][3][3], then 1x1 W [C][C], bias [C] (in place of W, bias below).
+ *                      FP32 inference handles only (else CONET_ERR_UNSUPPORTED).
  */
 typedef struct {
   int n_rx, n_sym, n_sc, qam_bits;
@@ -96,6 +110,9 @@ typedef struct {
   int pilot_comb;
   uint64_t pilot_seed;
   int recompute;               /* 1 = recompute block activations in backward (training) */
+  int fuse_op;                 /* 0 = product, 1 = sum at every fusion point */
+  int feedback;                /* 1 = Example II: supports add the main net's activation */
+  int depthwise;               /* 1 = depthwise-separable convs inside RB / MRB blocks */
 } conet_config;
 
 /*

@@ -28,6 +28,9 @@ def make_config(net, max_batch: int = 1, train: bool = False, recompute: bool = 
         c.pilot_syms[i] = ps[i] if i < len(ps) else -1
     c.n_pilot_syms, c.pilot_comb, c.pilot_seed = len(ps), net.pilot_comb, net.pilot_seed
     c.recompute = int(bool(recompute))
+    c.fuse_op = int(getattr(net, "fuse_op", 0))
+    c.feedback = int(getattr(net, "feedback", 0))
+    c.depthwise = int(getattr(net, "depthwise", 0))
     return c
 
 

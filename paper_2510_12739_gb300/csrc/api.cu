@@ -71,7 +71,14 @@ Layout build_layout(const conet_config& c) {
   auto conv = [&](int ci, int co, long* w, long* b) {
     *w = take((size_t)co * 9 * ci, 0, sqrtf(2.0f / (9.0f * ci)));
     *b = take((size_t)co, 2, 0.f);
-    L.convs.push_back({(size_t)*w, co, ci});
+    L.convs.push_back({(size_t)*w, co, ci, 9});
+  };
+  // depthwise-separable: per-channel 3x3 [C][3][3] (He, fan-in 9), then 1x1 [C][C] + bias
+  auto sep_conv = [&](long* d, long* w, long* b) {
+    *d = take((size_t)C * 9, 0, sqrtf(2.0f / 9.0f));
+    *w = take((size_t)C * C, 0, sqrtf(2.0f / C));
+    *b = take((size_t)C, 2, 0.f);
+    L.convs.push_back({(size_t)*w, C, C, 1});
   };
   auto ln = [&](long* g, long* b) {
     *g = take((size_t)C, 1, 0.f);
@@ -90,9 +97,11 @@ Layout build_layout(const conet_config& c) {
       for (int k = 0; k < c.depth; ++k) {
         BlockOff B;
         if (b >= 1 || c.resnet_baseline) ln(&B.ln1g, &B.ln1b);
-        conv(C, C, &B.c1w, &B.c1b);
+        if (c.depthwise) sep_conv(&B.c1d, &B.c1w, &B.c1b);
+        else conv(C, C, &B.c1w, &B.c1b);
         ln(&B.ln2g, &B.ln2b);
-        conv(C, C, &B.c2w, &B.c2b);
+        if (c.depthwise) sep_conv(&B.c2d, &B.c2w, &B.c2b);
+        else conv(C, C, &B.c2w, &B.c2b);
         L.blk[b].push_back(B);
       }
     }
@@ -127,6 +136,9 @@ static int validate_config(const conet_config* c) {
     if (i && c->pilot_syms[i] <= c->pilot_syms[i - 1]) return fail(CONET_ERR_ARG, "pilot symbols must increase");
   }
   if (c->pilot_comb < 1) return fail(CONET_ERR_ARG, "pilot_comb %d < 1", c->pilot_comb);
+  if (c->fuse_op < 0 || c->fuse_op > 1) return fail(CONET_ERR_ARG, "fuse_op %d not in {0, 1}", c->fuse_op);
+  if (c->feedback < 0 || c->feedback > 1) return fail(CONET_ERR_ARG, "feedback %d not in {0, 1}", c->feedback);
+  if (c->depthwise < 0 || c->depthwise > 1) return fail(CONET_ERR_ARG, "depthwise %d not in {0, 1}", c->depthwise);
   return CONET_OK;
 }
 
@@ -465,7 +477,8 @@ uint64_t config_hash(const conet_config& c) {
     }
   };
   const int f[] = {c.n_rx, c.n_sym, c.n_sc, c.qam_bits, c.n_branches, c.depth, c.width,
-                   c.residual, c.norm, c.fuse_mask, c.resnet_baseline, c.n_pilot_syms, c.pilot_comb};
+                   c.residual, c.norm, c.fuse_mask, c.resnet_baseline, c.n_pilot_syms, c.pilot_comb,
+                   c.fuse_op, c.feedback, c.depthwise};
   for (int v : f) mix(v);
   for (int i = 0; i < c.n_pilot_syms && i < 4; ++i) mix(c.pilot_syms[i]);
   mix((int64_t)c.pilot_seed);

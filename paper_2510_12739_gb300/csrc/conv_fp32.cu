@@ -35,12 +35,14 @@ __device__ __forceinline__ void fma2(unsigned long long& d, unsigned long long a
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
 
-template <int CIN, int COUT, int KC>
+// TAPS = 9: the 3x3 conv; TAPS = 1: a 1x1 conv (the pointwise half of a depthwise-separable
+// conv), the same GEMM with only the centre tap and weights [1][Cin][Cout].
+template <int CIN, int COUT, int KC, int TAPS = 9>
 __global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_kernel(ConvArgs a) {
   constexpr int NT = COUT * 2;            // (COUT/8) channel groups x 16 RE groups
   constexpr int CG = COUT / 8;
   constexpr int HC = COUT / 2;
-  constexpr int NCH = 9 * (CIN / KC);     // K chunks
+  constexpr int NCH = TAPS * (CIN / KC);  // K chunks
   constexpr int A_F4 = TM * KC / 4;
   constexpr int A_PER_T = (A_F4 + NT - 1) / NT;
   constexpr int B_F4 = KC * COUT / 4;
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_k
   float4 ra[A_PER_T], rb[B_PER_T];
 
   auto load_chunk = [&](int c) {
-    const int tap = c / (CIN / KC), ci0 = (c % (CIN / KC)) * KC;
+    const int wtap = c / (CIN / KC), ci0 = (c % (CIN / KC)) * KC;   // tap index in the weights
+    const int tap = TAPS == 9 ? wtap : 4;                           // grid shift (4 = centre)
     const int dt = tap / 3 - 1, df = tap % 3 - 1;
 #pragma unroll
     for (int j = 0; j < A_PER_T; ++j) {
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_k
 #pragma unroll
     for (int j = 0; j < B_PER_T; ++j) {
       const int idx = tid + j * NT;
-      if (idx < B_F4) rb[j] = __ldg(reinterpret_cast<const float4*>(w + (size_t)(tap * CIN + ci0) * COUT) + idx);
+      if (idx < B_F4) rb[j] = __ldg(reinterpret_cast<const float4*>(w + (size_t)(wtap * CIN + ci0) * COUT) + idx);
     }
   };
   auto store_chunk = [&](int buf) {
@@ -220,25 +223,67 @@ __global__ void __launch_bounds__(COUT * 2, (COUT <= 64 ? 4 : 2)) conv3x3_fp32_k
   }
 }
 
-template <int CIN, int COUT, int KC>
+template <int CIN, int COUT, int KC, int TAPS = 9>
 int launch_t(const ConvArgs& a, int n_br, cudaStream_t s) {
   constexpr size_t main_smem = (size_t)(2 * KC * TM + 2 * KC * COUT) * sizeof(float);
   constexpr size_t epi_smem = (size_t)TM * (COUT + 4) * sizeof(float);
   constexpr size_t smem = main_smem > epi_smem ? main_smem : epi_smem;
   static bool attr = false;
   if (!attr) {
-    CONET_CUDA(cudaFuncSetAttribute(conv3x3_fp32_kernel<CIN, COUT, KC>,
+    CONET_CUDA(cudaFuncSetAttribute(conv3x3_fp32_kernel<CIN, COUT, KC, TAPS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   dim3 grid((unsigned)((a.M + TM - 1) / TM), n_br);
-  conv3x3_fp32_kernel<CIN, COUT, KC><<<grid, COUT * 2, smem, s>>>(a);
-  return check_launch("conv3x3_fp32_kernel");
+  conv3x3_fp32_kernel<CIN, COUT, KC, TAPS><<<grid, COUT * 2, smem, s>>>(a);
+  return check_launch(TAPS == 9 ? "conv3x3_fp32_kernel" : "conv1x1_fp32_kernel");
+}
+
+// Depthwise 3x3 'same' conv of every branch (the first half of a depthwise-separable conv):
+// out[m][c] = sum over the 9 taps of w[c][tap] x[m + shift(tap)][c] (zero outside the grid).
+// One thread per RE and 4 channels; the 9 neighbour rows come through L1 / L2.
+__global__ void dwconv3x3_kernel(DwArgs a, int n_br) {
+  const int q = a.C / 4;
+  const long long total = a.M * q * n_br;
+  const int TF = a.T * a.F;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = 4 * (int)(i % q);
+    const long long rest = i / q;
+    const long long m = rest % a.M;
+    const int b = (int)(rest / a.M);
+    const int r = (int)(m % TF), t = r / a.F, f = r % a.F;
+    const float* w = a.w[b];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int tt = t + tap / 3 - 1, ff = f + tap % 3 - 1;
+      if (tt < 0 || tt >= a.T || ff < 0 || ff >= a.F) continue;
+      const long long mm = m + (long long)(tap / 3 - 1) * a.F + (tap % 3 - 1);
+      const float4 x = __ldg(reinterpret_cast<const float4*>(a.in[b] + mm * a.C + c));
+      acc.x = fmaf(__ldg(w + (c + 0) * 9 + tap), x.x, acc.x);
+      acc.y = fmaf(__ldg(w + (c + 1) * 9 + tap), x.y, acc.y);
+      acc.z = fmaf(__ldg(w + (c + 2) * 9 + tap), x.z, acc.z);
+      acc.w = fmaf(__ldg(w + (c + 3) * 9 + tap), x.w, acc.w);
+    }
+    *reinterpret_cast<float4*>(a.out[b] + m * a.C + c) = acc;
+  }
 }
 
 }  // namespace
 
 int launch_conv3x3_fp32(const ConvArgs& a, int n_br, int cin, int cout, cudaStream_t s) {
+  if (a.taps == 1) {   // the 1x1 of a depthwise-separable conv (C -> C)
+#define PW_CASE(C) \
+  if (cin == C && cout == C) return launch_t<C, C, 8, 1>(a, n_br, s);
+    PW_CASE(16)
+    PW_CASE(32)
+    PW_CASE(64)
+    PW_CASE(96)
+    PW_CASE(112)
+#undef PW_CASE
+    return fail(CONET_ERR_UNSUPPORTED, "FP32 1x1 conv with Cin=%d Cout=%d is not instantiated", cin, cout);
+  }
 #define CONV_CASE(CI, CO, KC) \
   if (cin == CI && cout == CO) return launch_t<CI, CO, KC>(a, n_br, s);
   CONV_CASE(8, 32, 8)
@@ -251,24 +296,34 @@ int launch_conv3x3_fp32(const ConvArgs& a, int n_br, int cin, int cout, cudaStre
   CONV_CASE(96, 96, 8)
   CONV_CASE(8, 16, 8)
   CONV_CASE(16, 16, 8)
+  CONV_CASE(8, 88, 8)
+  CONV_CASE(88, 88, 8)
 #undef CONV_CASE
   return fail(CONET_ERR_UNSUPPORTED, "FP32 conv3x3 with Cin=%d Cout=%d is not instantiated", cin, cout);
 }
 
-// [Cout][3][3][cin_src] -> [9][cin_dst][Cout], zero rows for cin_src <= ci < cin_dst
-__global__ void weights_tap_major_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+// [Cout][taps][cin_src] -> [taps][cin_dst][Cout], zero rows for cin_src <= ci < cin_dst
+// (taps = 9 for a 3x3 conv, 1 for a 1x1 conv)
+__global__ void weights_tap_major_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst, int taps,
                                          float* __restrict__ out) {
-  const int n = 9 * cin_dst * cout;
+  const int n = taps * cin_dst * cout;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int co = i % cout, rem = i / cout, ci = rem % cin_dst, tap = rem / cin_dst;
-    out[i] = ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f;
+    out[i] = ci < cin_src ? w[((size_t)co * taps + tap) * cin_src + ci] : 0.f;
   }
 }
 
-int launch_weights_to_tap_major(const float* w, int cout, int cin_src, int cin_dst, float* out, cudaStream_t s) {
-  weights_tap_major_kernel<<<grid_for((long long)cout * 9 * cin_dst, 256, 512), 256, 0, s>>>(w, cout, cin_src,
-                                                                                             cin_dst, out);
+int launch_weights_to_tap_major(const float* w, int cout, int cin_src, int cin_dst, float* out, cudaStream_t s,
+                                int taps) {
+  weights_tap_major_kernel<<<grid_for((long long)cout * taps * cin_dst, 256, 512), 256, 0, s>>>(w, cout, cin_src,
+                                                                                                cin_dst, taps, out);
   return check_launch("weights_tap_major_kernel");
+}
+
+int launch_dwconv3x3(const DwArgs& a, int n_br, cudaStream_t s) {
+  if (a.C % 4) return fail(CONET_ERR_UNSUPPORTED, "depthwise conv needs C %% 4 == 0");
+  dwconv3x3_kernel<<<grid_for(a.M * (a.C / 4) * n_br, 256, 152 * 16), 256, 0, s>>>(a, n_br);
+  return check_launch("dwconv3x3_kernel");
 }
 
 }  // namespace conet

@@ -78,6 +78,8 @@ int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int c
   return CONET_OK;
 }
 
+int tc_branch_groups(int kind, int nb, int cout) { return tc_groups(kind, nb, cout); }
+
 // Channels per K chunk and taps per stage of the instantiation for (kind, nb, cin, cout).
 int tc_chunk(int kind, int nb, int cin, int cout) { return tc_kc(kind, nb, cin, cout); }
 int tc_taps(int kind, int nb, int cin, int cout) { return tc_halo(kind, nb, cin, cout) ? 3 : 1; }

@@ -440,24 +440,28 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
 #pragma unroll
           for (int c = 0; c < CW; ++c) v[b][c] = fmaxf(v[b][c], 0.f);
       }
+      // run-time layers with the sum interaction or Example II's feedback: the fused
+      // statistic is over the sum of the a_b, and a support's (LN1) statistic over a_b + a_0
+      const bool sum_op = MODE == 0 && a.op == 1, fb = MODE == 0 && a.feedback && LY::fuse(a);
       if (j == j_lo) {
-        float p0 = 1.f;
+        float p0 = sum_op ? 0.f : 1.f;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          k_b[b] = v[b][0];
-          p0 *= v[b][0];
+          k_b[b] = fb && b > 0 ? v[b][0] + v[0][0] : v[b][0];
+          p0 = sum_op ? p0 + v[b][0] : p0 * v[b][0];
         }
         k_p = p0;
       }
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
-        float p = 1.f;
+        float p = sum_op ? 0.f : 1.f;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          const float d = v[b][c] - k_b[b];
+          const float x_b = fb && b > 0 ? v[b][c] + v[0][c] : v[b][c];
+          const float d = x_b - k_b[b];
           s1_b[b] += d;
           s2_b[b] = fmaf(d, d, s2_b[b]);
-          p *= v[b][c];
+          p = sum_op ? p + v[b][c] : p * v[b][c];
         }
         if (fuse_ln) {
           const float d = p - k_p;
@@ -533,12 +537,27 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
 #pragma unroll
     for (int b = 0; b < NB; ++b)
       if (valid && LY::a_out(a, b)) stg8(a.a_out[b] + m * COUT + c0, v[b]);
-    // x_0 = fused (and normalised) product, or a_0; it replaces v[0] from here on
+    // x_0 = fused (and normalised) product or sum, or a_0; it replaces v[0] from here on;
+    // with Example II's feedback the supports continue with a_b + a_0
     if (LY::fuse(a)) {
+      if constexpr (MODE == 0) {
+        const bool sum_op = a.op == 1;
 #pragma unroll
-      for (int c = 0; c < CW; ++c) {
+        for (int c = 0; c < CW; ++c) {
+          const float a0 = v[0][c];
 #pragma unroll
-        for (int b = 1; b < NB; ++b) v[0][c] *= v[b][c];
+          for (int b = 1; b < NB; ++b) v[0][c] = sum_op ? v[0][c] + v[b][c] : v[0][c] * v[b][c];
+          if (a.feedback) {
+#pragma unroll
+            for (int b = 1; b < NB; ++b) v[b][c] += a0;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+#pragma unroll
+          for (int b = 1; b < NB; ++b) v[0][c] *= v[b][c];
+        }
       }
       if (fuse_ln) {
         float g[CW], be[CW];
@@ -1184,7 +1203,7 @@ int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
 
 // The compile-time layer shape (Lay) that a launch's arguments match, 0 if none.
 int tc_mode(int kind, int nb, const TcConvArgs& a) {
-  if (a.measure || a.head_w || nb < 2) return 0;
+  if (a.measure || a.head_w || nb < 2 || a.op || a.feedback) return 0;
   bool m1 = a.pre == 2 && !a.fuse, m2 = a.pre == 0 && a.fuse && a.lnf_g, m3 = a.pre == 1 && a.fuse && a.lnf_g;
   for (int b = 0; b < nb; ++b) {
     if (a.t_out[b] || a.a_out[b] || !a.nx_out[b] || a.amax[b]) return 0;

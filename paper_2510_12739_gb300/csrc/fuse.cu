@@ -98,6 +98,7 @@ __global__ void fuse_kernel(FuseArgs a) {
     }
     L x0;
     if (a.fuse) {
+      // the interaction: product (op 0) or sum (op 1) of all branches
       L p = u[0];
 #pragma unroll
       for (int b = 1; b < MAX_BR; ++b)
@@ -105,12 +106,25 @@ __global__ void fuse_kernel(FuseArgs a) {
 #pragma unroll
           for (int v = 0; v < NV; ++v)
 #pragma unroll
-            for (int e = 0; e < VW; ++e) p.x[v][e] *= u[b].x[v][e];
+            for (int e = 0; e < VW; ++e) p.x[v][e] = a.op ? p.x[v][e] + u[b].x[v][e] : p.x[v][e] * u[b].x[v][e];
         }
       if (a.fuse_g)
         layer_norm(p, lane, C, a.fuse_g, a.fuse_b, x0);
       else
         x0 = p;
+      if (a.feedback) {
+        // Example II: each support continues with its activation plus the main's, written
+        // back over its own row (its stream / next input)
+#pragma unroll
+        for (int b = 1; b < MAX_BR; ++b) {
+          if (b >= a.n_br) continue;
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) u[b].x[v][e] += u[0].x[v][e];
+          store_row(const_cast<float*>(a.u[b]) + m * C, lane, C, u[b]);
+        }
+      }
     } else {
       x0 = u[0];
     }

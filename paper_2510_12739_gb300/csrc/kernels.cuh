@@ -82,8 +82,19 @@ struct ConvArgs {
   const float* ln_b[MAX_BR];
   int relu0;
   int M, T, F;                 // M = B * T * F resource elements
+  int taps;                    // 0 or 9: 3x3 conv; 1: 1x1 conv (w = [1][Cin][Cout])
 };
 int launch_conv3x3_fp32(const ConvArgs& a, int n_br, int cin, int cout, cudaStream_t s);
+
+// Depthwise 3x3 'same' conv per branch: out[m][c] = sum_tap w[c][tap] in[m + shift][c].
+struct DwArgs {
+  const float* in[MAX_BR];
+  const float* w[MAX_BR];      // [C][3][3]
+  float* out[MAX_BR];
+  int C, T, F;
+  long long M;
+};
+int launch_dwconv3x3(const DwArgs& a, int n_br, cudaStream_t s);
 
 // ---------------------------------------------------------------- fusion / LN / head
 // Per RE (one warp): x0 = fuse ? LN?(prod_b u_b) : u_0 (written to x0_out);
@@ -102,6 +113,8 @@ struct FuseArgs {
   float* llr;
   int* nonfinite;              // set to 1 when an LLR written is NaN or infinite
   int n_br, fuse, C, Q;
+  int op;                      // interaction: 0 = product, 1 = sum
+  int feedback;                // Example II: u[b] += u[0] (in place) for the supports
   long long M;
 };
 int launch_fuse(const FuseArgs& a, cudaStream_t s);
@@ -233,6 +246,8 @@ struct TcConvArgs {
   const float* qinv[MAX_BR];
   unsigned* amax[MAX_BR];
   int measure;
+  int op;                      // fused layers: 0 = product, 1 = sum of the branches
+  int feedback;                // fused layers, Example II: supports continue with a_b + a_0
 };
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
 // TMA maps of one conv operand: activations [slots][T][F][C] read in boxes of kc channels x
@@ -241,6 +256,7 @@ int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, cons
 int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc, int taps);
 int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps);
 int tc_chunk(int kind, int nb, int cin, int cout);
+int tc_branch_groups(int kind, int nb, int cout);   // branch groups per tile (1: all branches at once)
 // BF16 tensor-core dgrad operands: Wd[tap'][o][i] = W[i][8 - tap'][o] (the kernel rotated by
 // 180 degrees, input and output channels exchanged; input channel fastest) from the FP32
 // master [C][9][C]; and the BF16 copies of n values of each of nb gradient tensors.
@@ -277,6 +293,7 @@ int launch_fp8_scales(const Fp8ScaleArgs& a, int nb, int cout, float margin, cud
 // ---------------------------------------------------------------- weights
 // Re-layout of the FP32 master conv weights [Cout][3][3][cin_src] into the kernels'
 // [9][cin_dst][Cout] order (input channels zero-padded to cin_dst).
-int launch_weights_to_tap_major(const float* w, int cout, int cin_src, int cin_dst, float* out, cudaStream_t s);
+int launch_weights_to_tap_major(const float* w, int cout, int cin_src, int cin_dst, float* out, cudaStream_t s,
+                                int taps = 9);
 
 }  // namespace conet

@@ -99,6 +99,10 @@ int tc_weights_changed(conet_s* h, cudaStream_t s);
 int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
 
 int net_setup(conet_s* h) {
+  if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train)
+    return fail(CONET_ERR_UNSUPPORTED, "sum interaction and Example II feedback are inference-only");
+  if (h->cfg.depthwise && (h->cfg.train || h->prec != CONET_FP32 || !h->cfg.residual))
+    return fail(CONET_ERR_UNSUPPORTED, "depthwise-separable convs: FP32 inference of residual networks only");
   const size_t n = h->L.total;
   CONET_TRY(dev_alloc_t(h, &h->params, n));
   CONET_TRY(dev_alloc_t(h, &h->grads, n));
@@ -108,7 +112,7 @@ int net_setup(conet_s* h) {
   for (const auto& c : h->L.convs) {
     const int cin_dst = c.cin == h->cin ? h->c_pad : c.cin;
     h->wt_off[c.off] = wt;
-    wt += (size_t)9 * cin_dst * c.cout;
+    wt += (size_t)c.taps * cin_dst * c.cout;
   }
   h->wt_total = wt;
   CONET_TRY(dev_alloc_t(h, &h->wt, wt));
@@ -130,6 +134,8 @@ int net_setup(conet_s* h) {
   CONET_TRY(dev_alloc_t(h, &h->X0, need_x0 ? re * h->c_pad : 4));
   h->act.resize(na);
   for (size_t i = 0; i < na; ++i) CONET_TRY(dev_alloc_t(h, &h->act[i], re * h->C));
+  if (h->cfg.depthwise)
+    for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->dw_out[b], re * h->C));
   CONET_TRY(dev_alloc_t(h, &h->d_loss, 1));
   CONET_TRY(dev_alloc_t(h, &h->d_cnt, 2));
   CONET_CUDA(cudaMemset(h->params, 0, n * sizeof(float)));
@@ -193,8 +199,9 @@ int net_setup(conet_s* h) {
 int net_weights_changed(conet_s* h, cudaStream_t s) {
   for (const auto& c : h->L.convs) {
     const int cin_dst = c.cin == h->cin ? h->c_pad : c.cin;
-    CONET_TRY(launch_weights_to_tap_major(h->params + c.off, c.cout, c.cin, cin_dst, h->wt + h->wt_off.at(c.off), s));
-    if (h->cfg.train && c.cin != h->cin) {
+    CONET_TRY(launch_weights_to_tap_major(h->params + c.off, c.cout, c.cin, cin_dst, h->wt + h->wt_off.at(c.off), s,
+                                          c.taps));
+    if (h->cfg.train && c.cin != h->cin && c.taps == 9) {
       if (h->tc_dgrad)
         CONET_TRY(launch_weights_dgrad_bf16(h->params + c.off, c.cout,
                                             static_cast<uint16_t*>(h->wd16) + h->wd_off.at(c.off), s));
@@ -234,6 +241,8 @@ static FuseArgs fuse_args(conet_s* h, int B) {
   f.Q = h->Q;
   f.M = (long long)B * h->T * h->F;
   f.nonfinite = h->d_err + 1;
+  f.op = h->cfg.fuse_op;
+  f.feedback = h->cfg.feedback;
   return f;
 }
 
@@ -326,13 +335,42 @@ static int resid_fuse(conet_s* h, int k, int B, float* llr, cudaStream_t s) {
   return fuse_stage(h, f, s);
 }
 
+// A depthwise-separable block conv's per-channel 3x3 (into dw_out); the 1x1 that follows
+// runs as the block conv itself with taps = 1 (same epilogue).
+static int resid_dw(conet_s* h, int B, float* const* in, const long* dw_off, cudaStream_t s) {
+  DwArgs d = {};
+  for (int b = 0; b < h->nb; ++b) {
+    d.in[b] = in[b];
+    d.w[b] = P(h, dw_off[b]);
+    d.out[b] = h->dw_out[b];
+  }
+  d.C = h->C;
+  d.T = h->T;
+  d.F = h->F;
+  d.M = (long long)B * h->T * h->F;
+  prof_begin(h, PK_CONV, s);
+  const int rc = launch_dwconv3x3(d, h->nb, s);
+  prof_end(h, s);
+  return rc;
+}
+
 // Block k's first conv (LN2 + ReLU epilogue) and second conv (residual add).
 static int resid_conv1(conet_s* h, int k, int B, cudaStream_t s) {
   const Acts A{h};
   const Layout& L = h->L;
   ConvArgs c1 = conv_args(h, B);
+  if (h->cfg.depthwise) {
+    float* in[MAX_BR];
+    long d[MAX_BR];
+    for (int b = 0; b < h->nb; ++b) {
+      in[b] = A.H1(k, b);
+      d[b] = L.blk[b][k].c1d;
+    }
+    CONET_TRY(resid_dw(h, B, in, d, s));
+    c1.taps = 1;
+  }
   for (int b = 0; b < h->nb; ++b) {
-    c1.in[b] = A.H1(k, b);
+    c1.in[b] = h->cfg.depthwise ? h->dw_out[b] : A.H1(k, b);
     c1.w[b] = W(h, L.blk[b][k].c1w);
     c1.bias[b] = P(h, L.blk[b][k].c1b);
     c1.out0[b] = A.T1(k, b);
@@ -347,8 +385,18 @@ static int resid_conv2(conet_s* h, int k, int B, cudaStream_t s) {
   const Acts A{h};
   const Layout& L = h->L;
   ConvArgs c2 = conv_args(h, B);
+  if (h->cfg.depthwise) {
+    float* in[MAX_BR];
+    long d[MAX_BR];
+    for (int b = 0; b < h->nb; ++b) {
+      in[b] = A.H2(k, b);
+      d[b] = L.blk[b][k].c2d;
+    }
+    CONET_TRY(resid_dw(h, B, in, d, s));
+    c2.taps = 1;
+  }
   for (int b = 0; b < h->nb; ++b) {
-    c2.in[b] = A.H2(k, b);
+    c2.in[b] = h->cfg.depthwise ? h->dw_out[b] : A.H2(k, b);
     c2.w[b] = W(h, L.blk[b][k].c2w);
     c2.bias[b] = P(h, L.blk[b][k].c2b);
     c2.resid[b] = A.XS(k, b);
@@ -475,6 +523,9 @@ int tc_setup(conet_s* h) {
   if (h->cin > cin0) return fail(CONET_ERR_UNSUPPORTED, "tensor-core path takes at most %d input channels", cin0);
   if (h->C % 16) return fail(CONET_ERR_UNSUPPORTED, "tensor-core path needs width %% 16 == 0");
   if (kind == 2 && h->C % 32) return fail(CONET_ERR_UNSUPPORTED, "E4M3 path needs width %% 32 == 0");
+  if (kind == 2 && h->cfg.train) return fail(CONET_ERR_UNSUPPORTED, "E4M3 handles are inference-only (train = 0)");
+  if ((h->cfg.fuse_op || h->cfg.feedback) && tc_branch_groups(kind, h->nb, h->C) > 1)
+    return fail(CONET_ERR_UNSUPPORTED, "sum interaction / feedback on a branch-group network (%d x %d)", h->nb, h->C);
   const size_t re = (size_t)h->chunk * h->T * h->F;
   const size_t e = (size_t)tc_elt(kind);
   const bool split = kind == 1;
@@ -583,6 +634,8 @@ static TcConvArgs tc_args(conet_s* h, int idx, float* llr) {
     if (train) a.xs_out[0] = A.XM(l);
     a.pre = 1;
     a.fuse = fused_at(h->cfg, l);
+    a.op = a.fuse ? h->cfg.fuse_op : 0;
+    a.feedback = a.fuse ? h->cfg.feedback : 0;
     a.lnf_g = P(h, L.fg[l]);
     a.lnf_b = P(h, L.fb[l]);
     if (l == depth - 1) {
@@ -621,6 +674,8 @@ static TcConvArgs tc_args(conet_s* h, int idx, float* llr) {
       }
       a.pre = idx == 0 ? 1 : 0;
       a.fuse = fused_at(h->cfg, point);
+      a.op = a.fuse ? h->cfg.fuse_op : 0;
+      a.feedback = a.fuse ? h->cfg.feedback : 0;
       a.lnf_g = P(h, L.fg[point]);
       a.lnf_b = P(h, L.fb[point]);
       if (point == depth) {
@@ -856,7 +911,7 @@ struct Bwd {
 }  // namespace
 
 int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
-  if (h->prec != CONET_FP32 && h->cfg.residual)
+  if (h->prec != CONET_FP32 && (h->prec == CONET_FP8E4M3 || h->cfg.residual))
     return fail(CONET_ERR_UNSUPPORTED, "precision %d backward of this network not built yet", h->prec);
   const Acts A{h};
   const Layout& L = h->L;

@@ -13,6 +13,7 @@ namespace conet {
 
 struct BlockOff {
   long ln1g = -1, ln1b = -1, c1w = -1, c1b = -1, ln2g = -1, ln2b = -1, c2w = -1, c2b = -1;
+  long c1d = -1, c2d = -1;   // depthwise 3x3 weights [C][3][3] of depthwise-separable convs
 };
 
 struct Seg {
@@ -24,6 +25,7 @@ struct Seg {
 struct ConvT {
   size_t off;
   int cout, cin;
+  int taps;      // 9 = a 3x3 conv [Cout][3][3][Cin]; 1 = the 1x1 of a depthwise-separable conv [Cout][Cin]
 };
 
 // Offsets (in floats) of every tensor in the flat parameter vector; -1 = absent.
@@ -64,6 +66,7 @@ struct conet_s {
   float* G[3][conet::MAX_BR] = {};           // gradient buffers (train), max_batch*T*F*C each
   float* ew_part = nullptr;                  // partial sums of the elementwise backward kernels
   float* wg_part = nullptr;                  // split partials of the weight gradient
+  float* dw_out[conet::MAX_BR] = {};         // depthwise-separable convs: the depthwise output
   void* wg_tc = nullptr;                     // BF16 training: transposed operand copies of the tensor-core wgrad
   int n_pilot_re = 0;
   // tensor-core (BF16) path

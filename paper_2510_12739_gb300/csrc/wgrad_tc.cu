@@ -179,52 +179,79 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_tc_kernel(const __grid_co
 }
 
 // x [M][x_ld] FP32 (channels cin_src used, CIN written with zero padding), g [M][COUT] FP32 ->
-// XT[3][CIN][slots][ld] and GT[COUT][slots][ld] BF16 (ld >= T F).  One thread per RE and
-// channel quad.
+// XT[3][CIN][slots][ld] and GT[COUT][slots][ld] BF16 (ld >= T F).  One CTA per 64 consecutive
+// REs of one slot's flattened (t, f) axis: it stages the 66 input rows around them (one RE of
+// halo on each side for the subcarrier shifts) and their 64 gradient rows in shared memory with
+// coalesced row reads, then writes every channel's 64 REs as one contiguous 128-byte run of each
+// output plane.
+constexpr int OP_MAXC = 64;
+
 struct WgOpArgs {
-  const float* x[MAX_BR];
-  const float* g[MAX_BR];
-  __nv_bfloat16* xt[MAX_BR];
-  __nv_bfloat16* gt[MAX_BR];
+  const float* x;
+  const float* g;
+  __nv_bfloat16* xt;
+  __nv_bfloat16* gt;
   int x_ld, cin_src, cin, cout, slots, T, F, ld;
 };
 
-__global__ void wgrad_operands_kernel(WgOpArgs a, int n_br) {
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) wgrad_operands_kernel(WgOpArgs a) {
+  static_assert(CIN % 4 == 0 && COUT % 4 == 0 && CIN <= OP_MAXC && COUT <= OP_MAXC, "operand tile");
+  __shared__ float xs[WK + 2][CIN + 1];
+  __shared__ float gs[WK][COUT + 1];
   const int TF = a.T * a.F;
-  const long long M = (long long)a.slots * TF;
-  const int q_in = a.cin / 4, q_out = a.cout / 4, nq = q_in + q_out;
-  const long long total = M * nq * n_br;
-  const size_t plane = (size_t)a.slots * a.ld;           // one channel's [slots][ld] plane
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long m = i % M;                            // consecutive threads: consecutive REs
-    const long long rest = i / M;
-    const int qd = (int)(rest % nq), b = (int)(rest / nq);
-    const int slot = (int)(m / TF), tf = (int)(m % TF), f = tf % a.F;
-    const size_t col = (size_t)slot * a.ld + tf;
-    if (qd >= q_in) {                                     // gradient: GT[co][slot][tf]
-      const int c0 = 4 * (qd - q_in);
-      const float4 v = *reinterpret_cast<const float4*>(a.g[b] + m * a.cout + c0);
-      __nv_bfloat16* o = a.gt[b] + (size_t)c0 * plane + col;
-      o[0] = __float2bfloat16_rn(v.x);
-      o[plane] = __float2bfloat16_rn(v.y);
-      o[2 * plane] = __float2bfloat16_rn(v.z);
-      o[3 * plane] = __float2bfloat16_rn(v.w);
-      continue;
+  const int nmc = (TF + WK - 1) / WK;
+  const int slot = blockIdx.x / nmc, m0 = (blockIdx.x % nmc) * WK;
+  const long long base = (long long)slot * TF;
+  // stage rows m0 - 1 .. m0 + WK of x (inside the slot) and m0 .. m0 + WK - 1 of g, four
+  // channels per thread per step
+  for (int i = threadIdx.x; i < (WK + 2) * (CIN / 4); i += blockDim.x) {
+    const int r = i / (CIN / 4), c = 4 * (i % (CIN / 4)), m = m0 - 1 + r;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (m >= 0 && m < TF) {
+      const float* src = a.x + (base + m) * a.x_ld + c;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = c + k < a.cin_src ? src[k] : 0.f;
     }
-    // input: XT[df][ci][slot][tf] = x[slot][t][f + df][ci] (0 outside the grid)
-    const int c0 = 4 * qd;
 #pragma unroll
-    for (int df = -1; df <= 1; ++df) {
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      if (f + df >= 0 && f + df < a.F) {
-        const float* src = a.x[b] + (m + df) * a.x_ld;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = c0 + k < a.cin_src ? src[c0 + k] : 0.f;
-      }
-      __nv_bfloat16* o = a.xt[b] + ((size_t)(df + 1) * a.cin + c0) * plane + col;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) o[k * plane] = __float2bfloat16_rn(v[k]);
+    for (int k = 0; k < 4; ++k) xs[r][c + k] = v[k];
+  }
+  for (int i = threadIdx.x; i < WK * (COUT / 4); i += blockDim.x) {
+    const int r = i / (COUT / 4), c = 4 * (i % (COUT / 4)), m = m0 + r;
+    const float4 v = m < TF ? *reinterpret_cast<const float4*>(a.g + (base + m) * COUT + c) : make_float4(0, 0, 0, 0);
+    gs[r][c] = v.x;
+    gs[r][c + 1] = v.y;
+    gs[r][c + 2] = v.z;
+    gs[r][c + 3] = v.w;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)a.slots * a.ld;
+  const size_t col0 = (size_t)slot * a.ld + m0;
+  const int n = m0 + WK <= TF ? WK : TF - m0;           // REs of this chunk inside the slot
+  // one warp per output row (df, c): each lane writes two consecutive REs (4 bytes), so a
+  // warp stores the row's 64 REs as one 128-byte run
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = 2 * lane;
+  const int f0 = (m0 + r) % a.F, f1 = (m0 + r + 1) % a.F;
+  for (int row = warp; row < 3 * CIN + COUT; row += blockDim.x / 32) {
+    float v0, v1;
+    __nv_bfloat16* dst;
+    if (row < 3 * CIN) {
+      // XT[df][c][slot][m] = x[m + df] when the shifted subcarrier stays in the symbol, else 0
+      const int df = row / CIN - 1, c = row % CIN;
+      v0 = (f0 + df >= 0 && f0 + df < a.F) ? xs[r + 1 + df][c] : 0.f;
+      v1 = (f1 + df >= 0 && f1 + df < a.F) ? xs[r + 2 + df][c] : 0.f;
+      dst = a.xt + (size_t)row * plane + col0 + r;
+    } else {
+      const int c = row - 3 * CIN;
+      v0 = gs[r][c];
+      v1 = gs[r + 1][c];
+      dst = a.gt + (size_t)c * plane + col0 + r;
+    }
+    if (r + 1 < n) {
+      *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(v0, v1);
+    } else if (r < n) {
+      dst[0] = __float2bfloat16_rn(v0);
     }
   }
 }
@@ -290,7 +317,7 @@ int wgrad_tc_splits(long long slots, int T, int F, int n_br) {
 
 bool wgrad_tc_supported(int cin, int cout, int F) {
   const int cinp = (cin + 7) / 8 * 8;
-  if (F % 8 != 0) return false;
+  if (F % 8 != 0 || cinp > OP_MAXC || cout > OP_MAXC) return false;
   if (cout == 32) return cinp == 8 || cinp == 16 || cinp == 32;
   if (cout == 64) return cinp == 8 || cinp == 16 || cinp == 64;
   return false;
@@ -312,10 +339,10 @@ int launch_wgrad_tc(const WgradArgs& a, int slots, void* scratch, int* err, cuda
     __nv_bfloat16* xt = static_cast<__nv_bfloat16*>(scratch);
     __nv_bfloat16* gt = xt + (size_t)3 * cinp * plane;
     WgOpArgs o = {};
-    o.x[0] = a.x[b];
-    o.g[0] = a.g[b];
-    o.xt[0] = xt;
-    o.gt[0] = gt;
+    o.x = a.x[b];
+    o.g = a.g[b];
+    o.xt = xt;
+    o.gt = gt;
     o.x_ld = a.cin;
     o.cin_src = a.cin_src[b];
     o.cin = cinp;
@@ -324,7 +351,13 @@ int launch_wgrad_tc(const WgradArgs& a, int slots, void* scratch, int* err, cuda
     o.T = a.T;
     o.F = a.F;
     o.ld = ld;
-    wgrad_operands_kernel<<<grid_for(a.M * (cinp + a.cout) / 4, 256, 152 * 16), 256, 0, s>>>(o, 1);
+    const int grid = slots * ((TF + WK - 1) / WK);
+    if (cinp == 8 && a.cout == 32) wgrad_operands_kernel<8, 32><<<grid, 256, 0, s>>>(o);
+    else if (cinp == 16 && a.cout == 32) wgrad_operands_kernel<16, 32><<<grid, 256, 0, s>>>(o);
+    else if (cinp == 32 && a.cout == 32) wgrad_operands_kernel<32, 32><<<grid, 256, 0, s>>>(o);
+    else if (cinp == 8 && a.cout == 64) wgrad_operands_kernel<8, 64><<<grid, 256, 0, s>>>(o);
+    else if (cinp == 16 && a.cout == 64) wgrad_operands_kernel<16, 64><<<grid, 256, 0, s>>>(o);
+    else wgrad_operands_kernel<64, 64><<<grid, 256, 0, s>>>(o);
     CONET_LAUNCHED("wgrad_operands_kernel");
     WgMaps maps = {};
     for (int df = 0; df < 3; ++df)

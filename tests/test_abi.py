@@ -52,6 +52,7 @@ def test_param_count_matches_oracle_layout(lib, name):
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(norm=1), dict(residual=1, norm=1, n_branches=3),
+                                dict(residual=1, norm=1, depthwise=1),
                                 dict(n_branches=1, residual=1, norm=1, resnet_baseline=1),
                                 dict(fuse_mask=0b01, norm=1)])
 def test_param_count_tiny(lib, kw):
@@ -93,7 +94,7 @@ def test_checkpoint_hash_tracks_the_network_shape(lib):
     assert h0 == api.checkpoint_hash(base)
     for kw in (dict(n_rx=2), dict(n_sc=73), dict(qam_bits=6), dict(n_branches=3), dict(depth=5), dict(width=16),
                dict(norm=1), dict(fuse_mask=0b11), dict(pilot_syms=(2, 12)), dict(pilot_comb=3),
-               dict(pilot_seed=1), dict(residual=1)):
+               dict(pilot_seed=1), dict(residual=1), dict(fuse_op=1), dict(feedback=1)):
         assert api.checkpoint_hash(replace(base, **kw)) != h0, kw
     cfg = api.make_config(base, max_batch=7, train=True)
     h = C.c_uint64()

@@ -1,0 +1,105 @@
+"""GPU parity of the other interaction operations of Sec. III (f2): the element-wise sum at
+the fusion points (fuse_op = 1) and Example II's feedback (Fig. "conet2": every support net
+continues with its own activation plus the main net's), on the FP32 fusion stage and the
+tensor-core run-time epilogue, against the oracle (FP64, and its 16-bit / E4M3 emulations
+for the reduced-precision paths).  Bars as in the product-fusion tests: FP32 1e-4 normwise
+against FP64; 16-bit 1e-3 against the emulation on plain networks and the He-init
+LayerNorm bars on residual ones; E4M3 1e-2 against its emulation on plain networks."""
+import numpy as np
+import pytest
+
+from gpu_util import dev, need_gpu, normwise, oracle_inputs
+from workloads import WORKLOADS, replace
+
+pytestmark = pytest.mark.gpu
+VARIANTS = [dict(fuse_op=1), dict(feedback=1), dict(fuse_op=1, feedback=1)]
+EMU_MAX_LN = {"bf16": 0.1, "fp16": 3e-2}
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _run(net, sim, B, precision, wseed=2, perturb=0.02):
+    from oracle import fp8, half, net as onet, rx as orx
+    from paper_2510_12739_gb300 import api
+    ref = oracle_inputs(net, sim, 1, 0, B)
+    params = onet.init_params(net, wseed)
+    params = (params + perturb * np.random.default_rng(wseed).standard_normal(params.size)).astype(np.float32)
+    rx = api.Receiver(net, precision=precision, max_batch=B)
+    rx.load_weights(params)
+    L = rx.forward(dev(ref["Y32"]), dev(ref["pilot_mask"])).cpu().numpy()
+    rx.sync()
+    Yd = ref["Y32"][..., 0].astype(np.float64) + 1j * ref["Y32"][..., 1]
+    X0 = orx.assemble_input(Yd, ref["pilot_sym"], ref["pilot_mask"])
+    p64 = params.astype(np.float64)
+    if precision == "fp32":
+        R = onet.forward(net, p64, X0)
+    elif precision == "fp8":
+        R = fp8.forward_fp8(net, p64, X0)
+    else:
+        R = half.forward_16(net, p64, X0, precision)
+    return L, R
+
+
+@pytest.mark.parametrize("kw", VARIANTS)
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16", "fp8"])
+def test_plain_network(kw, precision):
+    w = WORKLOADS["plain_14x72_b16_fp32"]
+    net = replace(w.net, n_branches=3, depth=3, n_sc=40, **kw)
+    L, R = _run(net, w.sim, 2, precision)
+    err = normwise(L, R)
+    print(f"plain {kw} {precision}: {err:.2e}")
+    assert np.all(np.isfinite(L)) and err < {"fp32": 1e-4, "bf16": 1e-3, "fp16": 1e-3, "fp8": 1e-2}[precision], err
+
+
+@pytest.mark.parametrize("kw", VARIANTS)
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_residual_network(kw, precision):
+    w = WORKLOADS["resid_14x624_b256_fp32"]
+    net = replace(w.net, n_sc=37, depth=2, **kw)
+    L, R = _run(net, w.sim, 2, precision)
+    err = normwise(L, R)
+    print(f"residual {kw} {precision}: {err:.2e}")
+    assert np.all(np.isfinite(L)) and err < {"fp32": 1e-4, **EMU_MAX_LN}[precision], err
+
+
+def test_unsupported_combinations_are_refused():
+    from paper_2510_12739_gb300 import api
+    from paper_2510_12739_gb300._lib import ConetError
+    w = WORKLOADS["resid_14x3276_b1024_bf16"]
+    with pytest.raises(ConetError) as e:                  # branch-group network on the tensor cores
+        api.Receiver(replace(w.net, n_sc=29, feedback=1), "bf16", max_batch=1)
+    assert e.value.code == -8
+    with pytest.raises(ConetError) as e:                  # training with the sum interaction
+        api.Receiver(replace(WORKLOADS["plain_14x72_b16_fp32"].net, fuse_op=1), "fp32", max_batch=1, train=True)
+    assert e.value.code == -8
+
+
+@pytest.mark.parametrize("key,kw", [("resid_14x624_b256_fp32", dict(n_sc=37, depth=2)),
+                                    ("resid_14x624_b256_fp32", dict(n_sc=130, depth=1, n_branches=2, width=32)),
+                                    ("resnet_14x624_b256_fp32", dict(n_sc=21, depth=2))])
+def test_depthwise_separable_blocks_fp32(key, kw):
+    """Depthwise-separable RB / MRB convs (f3: per-channel 3x3, then 1x1 with bias) on the FP32
+    path (depthwise kernel + the implicit-GEMM kernel with only the centre tap), against the
+    FP64 oracle at 1e-4 normwise; also with the sum interaction and Example II feedback."""
+    w = WORKLOADS[key]
+    for extra in (dict(), dict(fuse_op=1, feedback=1)):
+        if extra and w.net.resnet_baseline:
+            continue
+        net = replace(w.net, depthwise=1, **kw, **extra)
+        L, R = _run(net, w.sim, 2, "fp32")
+        err = normwise(L, R)
+        print(f"depthwise {key} {kw} {extra}: {err:.2e}")
+        assert np.all(np.isfinite(L)) and err < 1e-4, err
+
+
+def test_depthwise_refused_outside_fp32_inference():
+    from paper_2510_12739_gb300 import api
+    from paper_2510_12739_gb300._lib import ConetError
+    net = replace(WORKLOADS["resid_14x624_b256_fp32"].net, depthwise=1, n_sc=37, depth=1)
+    for prec, train in (("bf16", False), ("fp32", True)):
+        with pytest.raises(ConetError) as e:
+            api.Receiver(net, prec, max_batch=1, train=train)
+        assert e.value.code == -8
