@@ -55,6 +55,7 @@ SIGNATURES = {
     "conet_params_updated": (I, [P, P]),
     "conet_forward": (I, [P, P, P, P, I, P, P]),
     "conet_graphs": (I, [P, I]),
+    "conet_whole_network": (I, [P, I, C.POINTER(I)]),
     "conet_calibrate": (I, [P, P, P, I, F32, P]),
     "conet_backward": (I, [P, P, I, P]),
     "conet_adam_step": (I, [P, F32, I, P]),

@@ -149,6 +149,16 @@ class Receiver:
                                   _stream(stream)))
         return llr
 
+    def whole_network(self, mode=True) -> bool:
+        """Single-kernel path for small plain BF16 / E4M3 networks: True or "always" runs
+        every forward through it, "auto" (the default) forward calls of at least
+        CONET_WHOLE_NET_MIN_SLOTS slots, False never.  Returns whether this handle's network
+        qualifies for it."""
+        m = {False: 0, True: 2, "never": 0, "auto": 1, "always": 2}[mode]
+        avail = C.c_int()
+        check(lib().conet_whole_network(self.h, m, C.byref(avail)))
+        return bool(avail.value)
+
     def graphs(self, enable: bool = True):
         """CUDA-graph replay of repeated identical forward calls (on by default)."""
         check(lib().conet_graphs(self.h, int(bool(enable))))

@@ -303,6 +303,15 @@ int conet_forward(conet_t h, const float* Y, const uint8_t* pilot_mask, const fl
   return net_forward_replay(h, Y, pilot_mask, B, llr, (cudaStream_t)stream);
 }
 
+int conet_whole_network(conet_t h, int enable, int* available) {
+  if (!h) return fail(CONET_ERR_ARG, "handle is NULL");
+  net_graph_reset(h);
+  if (enable < 0 || enable > 2) return fail(CONET_ERR_ARG, "enable = %d outside 0..2", enable);
+  h->whole_net = enable;
+  if (available) *available = h->sn ? 1 : 0;
+  return CONET_OK;
+}
+
 int conet_graphs(conet_t h, int enable) {
   if (!h) return fail(CONET_ERR_ARG, "handle is NULL");
   net_graph_reset(h);

@@ -290,6 +290,32 @@ struct Fp8ScaleArgs {
 };
 int launch_fp8_scales(const Fp8ScaleArgs& a, int nb, int cout, float margin, cudaStream_t s);
 
+// ---------------------------------------------------------------- whole-network kernel
+// Small plain CoNets (2 branches x 32 channels, T (F + 1) <= 1024): every layer of a slot in
+// one persistent kernel, activations in shared memory (smallnet_tc.cu).
+constexpr int SN_MAX_LAYERS = 8;
+struct SmallNetArgs {
+  const float* bias[SN_MAX_LAYERS][2];
+  const float* lnf_g[SN_MAX_LAYERS];   // LayerNorm after the fusion of layer l, or NULL
+  const float* lnf_b[SN_MAX_LAYERS];
+  int fuse[SN_MAX_LAYERS];
+  const float* head_w;
+  const float* head_b;
+  const float* dq[SN_MAX_LAYERS][2];   // E4M3: dequantisation [32] of layer l's accumulators
+  const float* qinv[SN_MAX_LAYERS][2]; // E4M3: 1 / scale of layer l's input (device scalar)
+  float* llr;
+  int* err;
+  int* nonfinite;
+  int B, T, F, Q, depth;
+};
+// kind: 0 BF16, 2 E4M3
+bool smallnet_eligible(int kind, int T, int F, int nb, int C, int depth, int Q);
+size_t smallnet_input_bytes(int slots, int T, int F);   // the padded input grid
+int make_smallnet_input_map(CUtensorMap* map, int kind, const void* xp, int slots, int T, int F);
+int launch_smallnet_pad(const void* x, void* xp, int slots, int T, int F, cudaStream_t s);
+int launch_smallnet(int kind, const CUtensorMap& x0_map, const CUtensorMap (*w_maps)[2], const SmallNetArgs& a,
+                    cudaStream_t s);
+
 // ---------------------------------------------------------------- weights
 // Re-layout of the FP32 master conv weights [Cout][3][3][cin_src] into the kernels'
 // [9][cin_dst][Cout] order (input channels zero-padded to cin_dst).

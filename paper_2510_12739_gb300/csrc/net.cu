@@ -557,6 +557,22 @@ int tc_setup(conet_s* h) {
     CONET_TRY(dev_alloc_t(h, &h->fp8_amax, (size_t)n * h->nb));
     CONET_CUDA(cudaMemset(h->fp8_act, 0, (size_t)n * h->nb * (h->C + FP8_REC_PAD) * sizeof(float)));
   }
+  // the whole-network kernel for small plain BF16 / E4M3 inference networks
+  h->sn = (kind == 0 || kind == 2) && !h->cfg.train && !h->cfg.residual && !h->cfg.fuse_op && !h->cfg.feedback &&
+          smallnet_eligible(kind, h->T, h->F, h->nb, h->C, h->cfg.depth, h->Q);
+  if (h->sn) {
+    const size_t xb = smallnet_input_bytes(h->chunk, h->T, h->F);
+    CONET_TRY(dev_alloc(h, &h->sn_x, xb));
+    CONET_CUDA(cudaMemset(h->sn_x, 0, xb));   // padding rows stay zero
+    CONET_TRY(make_smallnet_input_map(&h->sn_xmap, kind, h->sn_x, h->chunk, h->T, h->F));
+    for (int l = 0; l < h->cfg.depth; ++l)
+      for (int b = 0; b < h->nb; ++b) {
+        const int cin = l == 0 ? cin0 : h->C;
+        const size_t woff = h->wb_off.at((size_t)tc_conv_w(h, l, b));
+        CONET_TRY(make_weight_map(&h->sn_wmaps[l][b], kind, static_cast<const uint8_t*>(h->wb) + woff * e, cin, h->C,
+                                  cin, h->C, 9));
+      }
+  }
   h->tcmaps.resize(n);
   for (int idx = 0; idx < n; ++idx) {
     const int cin = idx == 0 ? cin0 : h->C;
@@ -730,6 +746,40 @@ static int net_forward_tc_chunk(conet_s* h, const float* Y, const uint8_t* mask,
     CONET_TRY(launch_assemble_16(kind, Y, mask, h->psym, B, h->N, h->T, h->F, tc_cin0(kind), h->X0b, s));
   }
   if (train) CONET_TRY(launch_assemble(Y, mask, h->psym, B, h->N, h->T, h->F, h->c_pad, h->X0, s));
+  if (h->sn && llr && !calibrate && (h->whole_net == 2 || (h->whole_net == 1 && B >= CONET_WHOLE_NET_MIN_SLOTS))) {
+    CONET_TRY(launch_smallnet_pad(h->X0b, h->sn_x, B, h->T, h->F, s));
+    prof_end(h, s);
+    // every layer and the head in one persistent kernel
+    const Layout& L = h->L;
+    SmallNetArgs sa = {};
+    for (int l = 0; l < h->cfg.depth; ++l) {
+      for (int b = 0; b < h->nb; ++b) sa.bias[l][b] = P(h, l == 0 ? L.in_b[b] : L.lb[b][l - 1]);
+      sa.fuse[l] = fused_at(h->cfg, l);
+      sa.lnf_g[l] = P(h, L.fg[l]);
+      sa.lnf_b[l] = P(h, L.fb[l]);
+      if (kind == 2)
+        for (int b = 0; b < h->nb; ++b) {
+          sa.dq[l][b] = fp8_dq(h, l, b);
+          if (l > 0) sa.qinv[l][b] = fp8_qinv(h, l, b);
+        }
+    }
+    sa.head_w = P(h, L.hw);
+    sa.head_b = P(h, L.hb);
+    sa.llr = llr;
+    sa.err = h->d_err;
+    sa.nonfinite = h->d_err + 1;
+    sa.B = B;
+    sa.T = h->T;
+    sa.F = h->F;
+    sa.Q = h->Q;
+    sa.depth = h->cfg.depth;
+    prof_begin(h, PK_CONV, s);
+    const int rc = launch_smallnet(kind, h->sn_xmap, h->sn_wmaps, sa, s);
+    prof_end(h, s);
+    CONET_TRY(rc);
+    h->fwd_B = B;
+    return CONET_OK;
+  }
   prof_end(h, s);
   for (int idx = 0; idx < n; ++idx) {
     TcConvArgs a = tc_args(h, idx, llr);

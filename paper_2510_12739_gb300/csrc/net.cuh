@@ -108,6 +108,12 @@ struct conet_s {
   // runs eagerly, the second identical call captures its launches into a graph (on an
   // internal stream), later identical calls launch that graph on the caller's stream.
   bool graphs = true;                        // conet_graphs
+  // whole-network kernel (small plain BF16 networks): padded input grid and its tensor maps
+  bool sn = false;                           // the handle's network qualifies
+  int whole_net = 1;                         // conet_whole_network: 0 never, 1 automatic, 2 always
+  void* sn_x = nullptr;
+  CUtensorMap sn_xmap;
+  CUtensorMap sn_wmaps[conet::SN_MAX_LAYERS][2];
   cudaGraphExec_t g_exec = nullptr;
   cudaStream_t g_stream = nullptr;           // capture stream
   const void* g_Y = nullptr;

@@ -186,6 +186,7 @@ def test_calibration_rules():
     a.init_he(1)
     La = a.forward(s["Y"], mask)
     b = api.Receiver(net, precision="fp8", max_batch=8)
+    b.whole_network(False)     # bitwise comparisons: the same (layer-by-layer) kernels as a's calibrating pass
     b.load_weights(a.save_weights())
     b.calibrate(s["Y"], mask, margin=2.0)
     assert torch.equal(b.forward(s["Y"], mask), La)
