@@ -85,6 +85,26 @@ int tc_chunk(int kind, int nb, int cin, int cout) { return tc_kc(kind, nb, cin, 
 int tc_taps(int kind, int nb, int cin, int cout) { return tc_halo(kind, nb, cin, cout) ? 3 : 1; }
 int tc_wbox_rows(int kind, int nb, int cin, int cout) { return cout / 2; }   // one CTA's half of a pair's B
 int tc_wbox_taps(int kind, int nb, int cin, int cout) { return tc_taps(kind, nb, cin, cout); }
+int tc_store_cols(int kind, int nb, int cin, int cout) {
+  return staged_ok(kind, nb, cin, cout) ? part_width(kind, nb, cout) : 0;
+}
+
+int make_out_map(CUtensorMap* map, int out_kind, void* base, int C, int F, int symbols, int cols) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return fail(CONET_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const int e = out_kind < 0 ? 4 : elt_of(out_kind);
+  const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)F, (cuuint64_t)symbols};
+  const cuuint64_t strides[2] = {(cuuint64_t)C * e, (cuuint64_t)F * C * e};
+  const cuuint32_t box[3] = {(cuuint32_t)cols, 32, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const int rb = cols * e;
+  const CUtensorMapSwizzle sw = rb == 16 ? CU_TENSOR_MAP_SWIZZLE_NONE : swizzle_of(rb);
+  const CUresult r = enc(map, out_kind < 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : dtype_of(out_kind), 3, base, dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CONET_ERR_CUDA, "output tensor map encode failed (%d)", (int)r);
+  return CONET_OK;
+}
 
 // [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] TF32 hi and FP32 lo = w - hi
 __global__ void weights_split_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,

@@ -118,11 +118,48 @@ __host__ __device__ constexpr int epi_parts(int kind, int nb, int cout) {
   return (tc_groups(kind, nb, cout) == 1 && kind == 2 && nb >= 3) || tc_groups(kind, nb, cout) > 1 ? 3 : 4;
 }
 
+// Staged output stores of the fixed layer shapes (MODE 1..3, below): each epilogue warp
+// writes its 32 rows x PW channels (PW = Cout / channel parts) of one output branch -- the
+// FP32 stream and the next conv's input -- into two swizzled shared-memory boxes that two
+// TMA stores write out, instead of storing 32 row segments 1 to 3 lines apart per store
+// instruction (measured on the 14x3276 network: the scattered stream and next-input stores
+// cost a third of the body convs' time).  Needs equal parts whose rows span 16, 32, 64 or
+// 128 bytes in both types; not on the split-TF32 path (its next input has two FP32 parts).
+__host__ __device__ constexpr int part_width(int kind, int nb, int cout) {
+  return (cout / CW) % epi_parts(kind, nb, cout) == 0 ? cout / epi_parts(kind, nb, cout) : 0;
+}
+__host__ __device__ constexpr bool box_row_ok(int bytes) {
+  return bytes == 16 || bytes == 32 || bytes == 64 || bytes == 128;
+}
+// the layer shapes with fixed-shape epilogues: residual-block body convs and the input
+// layers of residual networks of three or more branches
+__host__ __device__ constexpr bool fixed_shapes(int nb, int cin, int cout) {
+  return (cin == cout && nb >= 2) || (cin != cout && nb >= 3);
+}
+__host__ __device__ constexpr bool staged_ok(int kind, int nb, int cin, int cout) {
+  return kind != 1 && fixed_shapes(nb, cin, cout) && part_width(kind, nb, cout) > 0 &&
+         box_row_ok(part_width(kind, nb, cout) * 4) && box_row_ok(part_width(kind, nb, cout) * elt_of(kind));
+}
+__host__ __device__ constexpr size_t kb_ceil(size_t x) { return (x + 1023) / 1024 * 1024; }
+// per epilogue warp: the FP32 box, then the next-input box, each 1 KB aligned
+__host__ __device__ constexpr size_t stg_xs_bytes(int kind, int nb, int cout) {
+  return kb_ceil((size_t)32 * part_width(kind, nb, cout) * 4);
+}
+__host__ __device__ constexpr size_t stg_nx_bytes(int kind, int nb, int cout) {
+  return kb_ceil((size_t)32 * part_width(kind, nb, cout) * elt_of(kind));
+}
+__host__ __device__ constexpr size_t stg_bytes(int kind, int nb, int cin, int cout) {
+  return staged_ok(kind, nb, cin, cout)
+             ? (size_t)4 * epi_parts(kind, nb, cout) * (stg_xs_bytes(kind, nb, cout) + stg_nx_bytes(kind, nb, cout))
+             : 0;
+}
+
 __host__ __device__ constexpr int tc_plan(int kind, int nb_all, int cin, int cout, bool want_halo) {
   // returns KC for the requested stage shape, 0 if none fits; a stage holds one branch group
   const int nb = nb_all / tc_groups(kind, nb_all, cout);
   const int ep = epi_parts(kind, nb_all, cout);
-  const size_t par = par_bytes(nb_all, cout);
+  const size_t stg = stg_bytes(kind, nb_all, cin, cout);
+  const size_t par = par_bytes(nb_all, cout) + (stg ? 1024 + stg : 0);
   for (int row = 128; row >= 32; row >>= 1) {
     const int kc = row / elt_of(kind);
     if (kc < kc_min(kind) || cin % kc) continue;
@@ -141,7 +178,7 @@ __host__ __device__ constexpr int tc_kc(int kind, int nb, int cin, int cout) {
   return tc_halo(kind, nb, cin, cout) ? tc_plan(kind, nb, cin, cout, true) : tc_plan(kind, nb, cin, cout, false);
 }
 
-template <int KIND, int NB, int CIN, int COUT, int KC, int HALO>
+template <int KIND, int NB, int CIN, int COUT, int KC, int HALO, int MODE = 0>
 struct Cfg {
   static constexpr int ELT = elt_of(KIND);
   static constexpr int ROW = KC * ELT;                  // bytes per operand row (= swizzle span)
@@ -170,9 +207,16 @@ struct Cfg {
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr size_t SCR = scr_bytes(EP);
   static constexpr size_t PAR = par_bytes(NB, COUT);
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - 1024 - 256 - SCR - PAR) / STAGE);
+  // staged output stores (fixed layer shapes only); their boxes start 1 KB aligned
+  static constexpr bool STAGED = MODE != 0 && staged_ok(KIND, NB, CIN, COUT);
+  static constexpr int PW = part_width(KIND, NB, COUT);
+  static constexpr size_t XS_B = stg_xs_bytes(KIND, NB, COUT), NX_B = stg_nx_bytes(KIND, NB, COUT);
+  static constexpr size_t STG = STAGED ? (size_t)EPI_WARPS * (XS_B + NX_B) : 0;
+  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - (STAGED ? 2048 : 1024) - 256 - SCR - PAR - STG) / STAGE);
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + SCR + PAR;
+  static constexpr size_t STG_OFF =
+      STAGED ? kb_ceil((size_t)STAGES * STAGE + 256 + SCR + PAR) : (size_t)STAGES * STAGE + 256 + SCR + PAR;
+  static constexpr size_t SMEM = 1024 + STG_OFF + STG;
   static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT, 256);   // BF16 / TF32 / F16, E4M3
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
   static_assert(COUT % 16 == 0 && COUT <= 256 && COUT % CW == 0, "MMA N");
@@ -393,6 +437,101 @@ __device__ __forceinline__ void part_chunks(int p, int& first, int& count) {
   count = base + (p < rem ? 1 : 0);
 }
 
+// A warp's staged output boxes (fixed layer shapes): its two shared-memory boxes, the
+// output tensors' maps ([symbols][F][Cout] per branch) and the boxes' coordinates there
+// (first channel, first subcarrier, symbol).  ok = false: a tile past the last one or rows
+// wholly past the grid edge, nothing to store.  Rows past F inside a box are clipped by TMA.
+struct StoreBox {
+  uint8_t* xs;
+  uint8_t* nx;
+  const CUtensorMap* xs_map;
+  const CUtensorMap* nx_map;
+  int c0, f0, st;
+  bool ok;
+};
+
+// Address of 16-byte chunk k of row r of a 1 KB-aligned box with rows of rb bytes, laid
+// out in TMA's swizzle for that row length: the chunk index XOR row bits 0-2 (128-byte
+// rows), 1-2 (64), 2 (32), none (16).  A warp writing one chunk column of 32 rows then
+// touches every bank group evenly.
+__device__ __forceinline__ uint8_t* box_chunk(uint8_t* box, int rb, int r, int k) {
+  const int x = rb == 128 ? (r & 7) : rb == 64 ? ((r >> 1) & 3) : rb == 32 ? ((r >> 2) & 1) : 0;
+  return box + r * rb + 16 * (k ^ x);
+}
+
+// Chunk jj (8 channels) of row r of a warp's boxes: FP32 stream values (two 16-byte chunks)
+// and next-input values (16-bit: one 16-byte chunk; E4M3 of value x qinv: half of one).
+template <int PW>
+__device__ __forceinline__ void stage_xs8(uint8_t* box, int r, int jj, const float (&y)[CW]) {
+  *reinterpret_cast<float4*>(box_chunk(box, PW * 4, r, 2 * jj)) = make_float4(y[0], y[1], y[2], y[3]);
+  *reinterpret_cast<float4*>(box_chunk(box, PW * 4, r, 2 * jj + 1)) = make_float4(y[4], y[5], y[6], y[7]);
+}
+template <int KIND, int PW>
+__device__ __forceinline__ void stage_nx8(uint8_t* box, int r, int jj, const float (&o)[CW], float qinv) {
+  if constexpr (KIND == 2)
+    store8_e4m3(box_chunk(box, PW, r, jj >> 1) + 8 * (jj & 1), o, qinv);
+  else if constexpr (KIND == 3)
+    store8_h(reinterpret_cast<__half*>(box_chunk(box, PW * 2, r, jj)), o);
+  else
+    store8_h(reinterpret_cast<__nv_bfloat16*>(box_chunk(box, PW * 2, r, jj)), o);
+}
+
+// a_b = pre(v_b) of the fixed layer shapes: relu(LN2_b(v_b)) (MODE 1), relu(v_b) (MODE 3),
+// v_b (MODE 2); chunk c0 of branch b, LN2 statistics (mu, rs).
+template <int MODE, int COUT>
+__device__ __forceinline__ void pre_fixed(const float* par, int b, int c0, float mu, float rs, float (&v)[CW]) {
+  using PL = ParLayout<COUT>;
+  if constexpr (MODE == 1) {
+    float g[CW], be[CW];
+    lds8(par + PL::at(b, PF_LN2G) + c0, g);
+    lds8(par + PL::at(b, PF_LN2B) + c0, be);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) v[c] = fmaxf((v[c] - mu) * rs * g[c] + be[c], 0.f);
+  } else if constexpr (MODE == 3) {
+#pragma unroll
+    for (int c = 0; c < CW; ++c) v[c] = fmaxf(v[c], 0.f);
+  }
+}
+
+// next_b = post(x_b) of the fixed layer shapes: x_b (MODE 1); relu(x_0) for the fused main
+// branch and relu(LN1_b(x_b)) for a support (MODE 2, 3), LN1 statistics (mu, rs).
+template <int MODE, int COUT>
+__device__ __forceinline__ void post_fixed(const float* par, int b, int c0, float mu, float rs, const float (&x)[CW],
+                                           float (&o)[CW]) {
+  using PL = ParLayout<COUT>;
+  if constexpr (MODE == 1) {
+#pragma unroll
+    for (int c = 0; c < CW; ++c) o[c] = x[c];
+  } else if (b == 0) {
+#pragma unroll
+    for (int c = 0; c < CW; ++c) o[c] = fmaxf(x[c], 0.f);
+  } else {
+    float g[CW], be[CW];
+    lds8(par + PL::at(b, PF_LN1G) + c0, g);
+    lds8(par + PL::at(b, PF_LN1B) + c0, be);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) o[c] = fmaxf((x[c] - mu) * rs * g[c] + be[c], 0.f);
+  }
+}
+
+// Before a warp rewrites its boxes: the TMA stores issued from them have read them.
+__device__ __forceinline__ void boxes_free(int lane) {
+  if (lane == 0) tc::bulk_wait_read();
+  __syncwarp();
+}
+
+// After the warp has written its boxes: make the writes visible to TMA and store branch b's
+// boxes (has_xs: the stream box too).
+__device__ __forceinline__ void boxes_store(const StoreBox& sb, int b, bool has_xs, int lane) {
+  tc::fence_proxy_async();
+  __syncwarp();
+  if (lane == 0 && sb.ok) {
+    if (has_xs) tc::tma_store_3d(sb.xs_map + b, sb.xs, sb.c0, sb.f0, sb.st);
+    tc::tma_store_3d(sb.nx_map + b, sb.nx, sb.c0, sb.f0, sb.st);
+    tc::bulk_commit();
+  }
+}
+
 // The fused epilogue for one RE (this thread's TMEM lane) and one part of its channels.
 // Pass 1 (when a LayerNorm is applied) folds each branch's values, and the fused product,
 // into shifted first and second moments; the parts of a lane quarter publish theirs in
@@ -401,9 +540,10 @@ __device__ __forceinline__ void part_chunks(int p, int& first, int& count) {
 // residual-added) values back into TMEM.  Pass 2 applies the pre-activation, the Hadamard
 // fusion and its LayerNorm, writes the residual stream and the next conv's input, and
 // accumulates the head's partial sums, which part 0 reduces through the scratch.
-template <int KIND, int NB, int COUT, int EP, int MODE>
+template <int KIND, int NB, int COUT, int EP, int MODE, int PW>
 __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* par, uint32_t tacc, bool valid,
-                                            long long m, int part, int quarter, int lane, float* scr_all) {
+                                            long long m, int part, int quarter, int lane, float* scr_all,
+                                            const StoreBox& sb) {
   constexpr int QMAX = HEAD_QMAX;
   using PL = ParLayout<COUT>;
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
@@ -502,6 +642,51 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
       }
     }
     named_barrier(1 + quarter, 32 * EP);   // scratch free for the stores
+  }
+
+  if constexpr (PW > 0) {
+    // pass 2 of the fixed layer shapes, staged (PW channels per part): one output branch at
+    // a time through the warp's boxes.  Their statistics pass wrote v_b back to TMEM; they
+    // have no head and measure nothing.
+    static_assert(MODE != 0, "staged stores serve the fixed layer shapes");
+#pragma unroll
+    for (int ob = 0; ob < NB; ++ob) {
+      const bool has_xs = LY::xs_out(a, ob);
+      const float qinv = KIND == 2 ? lds1(par + PL::QINV + ob) : 0.f;
+      boxes_free(lane);
+      for (int j = j_lo; j < j_hi; ++j) {
+        float v[NB][CW];
+        __syncwarp();
+        load_chunk<KIND, NB, COUT, MODE>(a, par, tacc, 0, j, valid, m, v, false);
+        const int c0 = CW * j;
+        float x[CW];
+        if (LY::fuse(a) && ob == 0) {
+          // x_0 = LN_f(prod_b a_b)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) pre_fixed<MODE, COUT>(par, b, c0, mean_b[b], rstd_b[b], v[b]);
+          float g[CW], be[CW];
+          lds8(par + PL::LNFG + c0, g);
+          lds8(par + PL::LNFB + c0, be);
+#pragma unroll
+          for (int c = 0; c < CW; ++c) {
+            float p = v[0][c];
+#pragma unroll
+            for (int b = 1; b < NB; ++b) p *= v[b][c];
+            x[c] = (p - mean_p) * rstd_p * g[c] + be[c];
+          }
+        } else {
+          pre_fixed<MODE, COUT>(par, ob, c0, mean_b[ob], rstd_b[ob], v[ob]);
+#pragma unroll
+          for (int c = 0; c < CW; ++c) x[c] = v[ob][c];
+        }
+        if (has_xs) stage_xs8<PW>(sb.xs, lane, j - j_lo, x);
+        float o[CW];
+        post_fixed<MODE, COUT>(par, ob, c0, mean_b[ob], rstd_b[ob], x, o);
+        stage_nx8<KIND, PW>(sb.nx, lane, j - j_lo, o, qinv);
+      }
+      boxes_store(sb, ob, has_xs, lane);
+    }
+    return;
   }
 
   float hq[QMAX];
@@ -662,10 +847,10 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
 // which also accumulates the head.  Statistics are merged across the lane quarter's parts
 // as in tc_epilogue.  Fused layers have pre-activation none or ReLU, so the product can be
 // formed in the statistics pass.
-template <int KIND, int NB, int COUT, int G, int EP, int MODE>
+template <int KIND, int NB, int COUT, int G, int EP, int MODE, int PW>
 __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const float* par, uint32_t tacc,
                                                   uint32_t tstash, int g, bool valid, long long m, int part,
-                                                  int quarter, int lane, float* scr_all) {
+                                                  int quarter, int lane, float* scr_all, const StoreBox& sb) {
   constexpr int QMAX = HEAD_QMAX;
   using PL = ParLayout<COUT>;
   constexpr int NG = NB / G;
@@ -770,6 +955,45 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const flo
       }
     }
     named_barrier(1 + quarter, 32 * EP);
+  }
+
+  if constexpr (PW > 0) {
+    // pass 2 of the fixed layer shapes, staged: the group's support branches, then branch 0
+    // where it is formed, one at a time through the warp's boxes (statistics were taken:
+    // TMEM holds v_b and, in the last group of a fused layer, the stash the product)
+    static_assert(MODE != 0, "staged stores serve the fixed layer shapes");
+#pragma unroll
+    for (int ob = 0; ob <= G; ++ob) {
+      const bool is_main = ob == G;
+      const int b = is_main ? 0 : b0 + ob;
+      if (is_main ? !main_here : b == 0) continue;
+      const int si = is_main ? 0 : ob;   // statistics slot (not fused: branch 0 is slot 0 of group 0)
+      const bool has_xs = LY::xs_out(a, b);
+      const float qinv = KIND == 2 ? lds1(par + PL::QINV + b) : 0.f;
+      boxes_free(lane);
+      for (int j = j_lo; j < j_hi; ++j) {
+        const int c0 = CW * j;
+        float x[CW];
+        __syncwarp();
+        if (is_main && fuse) {
+          tmem_get8(tstash + (uint32_t)c0, x);   // the fused product
+          float gm[CW], be[CW];
+          lds8(par + PL::LNFG + c0, gm);
+          lds8(par + PL::LNFB + c0, be);
+#pragma unroll
+          for (int c = 0; c < CW; ++c) x[c] = (x[c] - mean_p) * rstd_p * gm[c] + be[c];
+        } else {
+          tmem_get8(tacc + (uint32_t)(si * COUT + c0), x);
+          pre_fixed<MODE, COUT>(par, b, c0, mean_b[si], rstd_b[si], x);
+        }
+        if (has_xs) stage_xs8<PW>(sb.xs, lane, j - j_lo, x);
+        float o[CW];
+        post_fixed<MODE, COUT>(par, b, c0, mean_b[si], rstd_b[si], x, o);
+        stage_nx8<KIND, PW>(sb.nx, lane, j - j_lo, o, qinv);
+      }
+      boxes_store(sb, b, has_xs, lane);
+    }
+    return;
   }
 
   float hq[QMAX];
@@ -965,7 +1189,7 @@ template <int KIND, int NB, int CIN, int COUT, int KC, int HALO, int MODE>
 // (up to 96 registers each).  MODE: the epilogue's layer shape (Lay).
 __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS), 1)
     conv_tc_kernel(const __grid_constant__ TcMaps maps, TcConvArgs a) {
-  using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
+  using K = Cfg<KIND, NB, CIN, COUT, KC, HALO, MODE>;
   constexpr int EP = K::EP;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1146,15 +1370,30 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
       const long long m = ((long long)slot * a.T + t) * a.F + f;
       const uint32_t lanes = (uint32_t)(32 * q) << 16;
       const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + lanes;
+      StoreBox sb = {};
+      if constexpr (K::STAGED) {
+        sb.xs = smem + K::STG_OFF + (size_t)(warp - 2) * (K::XS_B + K::NX_B);
+        sb.nx = sb.xs + K::XS_B;
+        sb.xs_map = maps.xs;
+        sb.nx_map = maps.nx;
+        sb.c0 = part * K::PW;
+        sb.f0 = fb * TILE_M + 32 * q;
+        sb.st = slot * a.T + t;
+        sb.ok = tile < a.n_tiles && sb.f0 < a.F;
+      }
+      constexpr int PW = K::STAGED ? K::PW : 0;
       if constexpr (K::NG == 1)
-        tc_epilogue<KIND, NB, COUT, EP, MODE>(a, par, tacc, valid, m, part, q, lane, scr_all);
+        tc_epilogue<KIND, NB, COUT, EP, MODE, PW>(a, par, tacc, valid, m, part, q, lane, scr_all, sb);
       else
-        tc_epilogue_group<KIND, NB, COUT, K::G, EP, MODE>(a, par, tacc, tbase + (uint32_t)K::STASH + lanes, g, valid,
-                                                          m, part, q, lane, scr_all);
+        tc_epilogue_group<KIND, NB, COUT, K::G, EP, MODE, PW>(a, par, tacc, tbase + (uint32_t)K::STASH + lanes, g,
+                                                              valid, m, part, q, lane, scr_all, sb);
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive_cluster(tempty0 + (uint32_t)(acc * sizeof(uint64_t)));
     }
+    // the staged stores have written global memory and read the boxes before the CTA ends
+    if constexpr (K::STAGED)
+      if (lane == 0) tc::bulk_wait_all();
   }
   // neither CTA deallocates or leaves while the pair may still read its shared memory or
   // TMEM or signal its barriers
@@ -1170,7 +1409,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
 
 template <int KIND, int NB, int CIN, int COUT, int KC, int HALO, int MODE>
 int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
-  using K = Cfg<KIND, NB, CIN, COUT, KC, HALO>;
+  using K = Cfg<KIND, NB, CIN, COUT, KC, HALO, MODE>;
   auto* kern = conv_tc_kernel<KIND, NB, CIN, COUT, KC, HALO, MODE>;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

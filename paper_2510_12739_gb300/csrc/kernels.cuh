@@ -206,6 +206,10 @@ struct TcMaps {
   CUtensorMap w[MAX_BR];       // weights [9][Cout][Cin], box {KC, Cout, 1}
   CUtensorMap a_lo[MAX_BR];    // split-TF32 path: low parts of the same tensors
   CUtensorMap w_lo[MAX_BR];
+  // staged output stores of the fixed layer shapes: the FP32 stream xs_out[b] and the next
+  // input nx_out[b] as [slots x T][F][Cout], box {channels per epilogue part, 32, 1}
+  CUtensorMap xs[MAX_BR];
+  CUtensorMap nx[MAX_BR];
 };
 
 // Fused epilogue, per RE and branch b:
@@ -265,6 +269,12 @@ int launch_grads_bf16(const float* const* in, void* const* out, int nb, long lon
 int tc_taps(int kind, int nb, int cin, int cout);
 int tc_wbox_rows(int kind, int nb, int cin, int cout);   // output channels per weight box
 int tc_wbox_taps(int kind, int nb, int cin, int cout);   // taps per weight box
+// channels per epilogue part of the staged output stores of the fixed layer shapes, 0 when
+// the shape stores unstaged
+int tc_store_cols(int kind, int nb, int cin, int cout);
+// output map of a staged store: [slots x T][F][C] elements of `out_kind` (-1: FP32; else an
+// operand kind), box {cols, 32, 1}, swizzled for rows of cols elements
+int make_out_map(CUtensorMap* map, int out_kind, void* base, int C, int F, int symbols, int cols);
 int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s);
 int launch_weights_split(const float* w, int cout, int cin_src, int cin_dst, float* hi, float* lo, cudaStream_t s);
 int launch_assemble_split(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,

@@ -516,6 +516,8 @@ unsigned* fp8_amax(const conet_s* h, int idx, int b) { return h->fp8_amax + (siz
 
 }  // namespace
 
+static TcConvArgs tc_args(conet_s* h, int idx, float* llr);
+
 int tc_setup(conet_s* h) {
   if (tc_kind(h) < 0) return CONET_OK;
   const int kind = tc_kind(h);
@@ -589,6 +591,17 @@ int tc_setup(conet_s* h) {
         CONET_TRY(make_act_map(&h->tcmaps[idx].a_lo[b], kind, tc_conv_in_lo(h, idx, b), cin, h->F, h->T, h->chunk,
                                kc, taps));
         CONET_TRY(make_weight_map(&h->tcmaps[idx].w_lo[b], kind, h->wb_lo + woff, cin, h->C, kc, wrows, wtaps));
+      }
+    }
+    // the staged stores' output maps (used by the fixed layer shapes only)
+    const int cols = tc_store_cols(kind, h->nb, cin, h->C);
+    if (cols > 0) {
+      const TcConvArgs oa = tc_args(h, idx, nullptr);
+      for (int b = 0; b < h->nb; ++b) {
+        if (oa.xs_out[b])
+          CONET_TRY(make_out_map(&h->tcmaps[idx].xs[b], -1, oa.xs_out[b], h->C, h->F, h->chunk * h->T, cols));
+        if (oa.nx_out[b])
+          CONET_TRY(make_out_map(&h->tcmaps[idx].nx[b], kind, oa.nx_out[b], h->C, h->F, h->chunk * h->T, cols));
       }
     }
   }
