@@ -205,20 +205,32 @@ struct Cfg {
   static constexpr int EP = epi_parts(KIND, NB, COUT);  // channel parts per lane quarter
   static constexpr int EPI_WARPS = 4 * EP;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
-  static constexpr size_t SCR = scr_bytes(EP);
   static constexpr size_t PAR = par_bytes(NB, COUT);
-  // staged output stores (fixed layer shapes only); their boxes start 1 KB aligned
+  // Staged output stores (fixed layer shapes only): each epilogue warp owns a 1 KB-aligned
+  // region holding its FP32 box and its next-input box (conv1 of a block, MODE 1, writes no
+  // stream: no FP32 box).  The region also serves as the warp's LayerNorm-moment scratch,
+  // which is dead while the boxes are in use.
   static constexpr bool STAGED = MODE != 0 && staged_ok(KIND, NB, CIN, COUT);
   static constexpr int PW = part_width(KIND, NB, COUT);
-  static constexpr size_t XS_B = stg_xs_bytes(KIND, NB, COUT), NX_B = stg_nx_bytes(KIND, NB, COUT);
-  static constexpr size_t STG = STAGED ? (size_t)EPI_WARPS * (XS_B + NX_B) : 0;
-  static constexpr int STAGES_FIT = (int)((SMEM_LIMIT - (STAGED ? 2048 : 1024) - 256 - SCR - PAR - STG) / STAGE);
-  static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
-  static constexpr size_t STG_OFF =
-      STAGED ? kb_ceil((size_t)STAGES * STAGE + 256 + SCR + PAR) : (size_t)STAGES * STAGE + 256 + SCR + PAR;
+  static constexpr size_t XS_B = MODE == 1 ? 0 : stg_xs_bytes(KIND, NB, COUT), NX_B = stg_nx_bytes(KIND, NB, COUT);
+  static constexpr size_t REG_B =
+      kb_ceil(XS_B + NX_B > SCR_WARP_FLOATS * sizeof(float) ? XS_B + NX_B : SCR_WARP_FLOATS * sizeof(float));
+  static constexpr size_t SCR = STAGED ? 0 : scr_bytes(EP);
+  static constexpr int SCR_STRIDE = STAGED ? (int)(REG_B / sizeof(float)) : SCR_WARP_FLOATS;   // floats per warp
+  static constexpr size_t STG = STAGED ? (size_t)EPI_WARPS * REG_B : 0;
+  static constexpr size_t fixed_end(int st) {
+    return STAGED ? kb_ceil((size_t)st * STAGE + 256 + SCR + PAR) : (size_t)st * STAGE + 256 + SCR + PAR;
+  }
+  static constexpr int stages_max() {
+    int st = 1;
+    while (st < 8 && 1024 + fixed_end(st + 1) + STG <= SMEM_LIMIT) ++st;
+    return st;
+  }
+  static constexpr int STAGES = stages_max();
+  static constexpr size_t STG_OFF = fixed_end(STAGES);
   static constexpr size_t SMEM = 1024 + STG_OFF + STG;
   static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 1 : KIND == 1 ? 2 : 0, COUT, 256);   // BF16 / TF32 / F16, E4M3
-  static_assert(STAGES >= 2, "not enough shared memory for two stages");
+  static_assert(STAGES >= 2 && SMEM <= SMEM_LIMIT, "not enough shared memory for two stages");
   static_assert(COUT % 16 == 0 && COUT <= 256 && COUT % CW == 0, "MMA N");
   static_assert(B_ROWS % 8 == 0, "each CTA's weight half holds whole swizzle atoms");
   static_assert(NB * COUT <= 512, "TMEM columns");
@@ -540,13 +552,13 @@ __device__ __forceinline__ void boxes_store(const StoreBox& sb, int b, bool has_
 // residual-added) values back into TMEM.  Pass 2 applies the pre-activation, the Hadamard
 // fusion and its LayerNorm, writes the residual stream and the next conv's input, and
 // accumulates the head's partial sums, which part 0 reduces through the scratch.
-template <int KIND, int NB, int COUT, int EP, int MODE, int PW>
+template <int KIND, int NB, int COUT, int EP, int MODE, int PW, int SCR_STRIDE>
 __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* par, uint32_t tacc, bool valid,
                                             long long m, int part, int quarter, int lane, float* scr_all,
                                             const StoreBox& sb) {
   constexpr int QMAX = HEAD_QMAX;
   using PL = ParLayout<COUT>;
-  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
   int j_lo, n_ch;
   part_chunks<COUT, EP>(part, j_lo, n_ch);
   const int j_hi = j_lo + n_ch;
@@ -614,6 +626,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
     tc::tmem_wait_st();
     // publish (mean, M2) of this part, then fold all parts in order
     const float n_mine = (float)(CW * n_ch);
+    if constexpr (PW > 0) boxes_free(lane);   // the scratch shares the boxes of the last stores
 #pragma unroll
     for (int s = 0; s <= NB; ++s) {
       const float k = s < NB ? k_b[s] : k_p, s1 = s < NB ? s1_b[s] : s1_p, s2 = s < NB ? s2_b[s] : s2_p;
@@ -629,7 +642,7 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
       for (int pp = 0; pp < EP; ++pp) {
         int f0, cnt;
         part_chunks<COUT, EP>(pp, f0, cnt);
-        const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+        const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE;
         chan_fold(n, mu, M2, (float)(CW * cnt), o[(2 * s) * 32 + lane], o[(2 * s + 1) * 32 + lane]);
       }
       const float rs = rsqrtf(M2 / (float)COUT + 1e-5f);
@@ -829,12 +842,123 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
         float sum = 0.f;
 #pragma unroll
         for (int pp = 0; pp < EP; ++pp)
-          sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
+          sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE + qq * 32 + lane];
         const float v = sum + lds1(par + PL::HEADB + qq);
         a.llr[m * a.Q + qq] = v;
         if (!(fabsf(v) <= FLT_MAX)) *a.nonfinite = 1;
       }
     }
+  }
+}
+
+// Two 16-bit values of max(x, 0) in one register (lo in the low half).
+template <int KIND>
+__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
+  uint32_t r;
+  if constexpr (KIND == 3)
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  else
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// Epilogue of the first conv of a residual block (MODE 1) on the branch-group path, for a
+// warp whose part is 32 channels, 16-bit outputs: v_b = acc_b + bias_b, next_b =
+// relu(LN2_b(v_b)) for the G branches of the group.  The part's 32 columns of every branch
+// come out of TMEM with one wait and stay in registers through the moment exchange (no
+// write-back, no second read), and the arithmetic runs on two-lane FP32 instructions: a
+// quarter of the waits and half the FP32 instructions of the general epilogue, whose
+// per-group time otherwise exceeds the group's MMA time.
+template <int KIND, int G, int COUT, int EP, int SCR_STRIDE>
+__device__ __forceinline__ void conv1_group_part(const float* par, uint32_t tacc, int b0, int part, int quarter,
+                                                 int lane, float* scr_all, const StoreBox& sb) {
+  using PL = ParLayout<COUT>;
+  constexpr int PC = 32;
+  static_assert(COUT == EP * PC, "one 32-channel part per warp");
+  const int c0 = PC * part;
+  float v[G][PC];
+  {
+    uint32_t r[G][2][16];
+    __syncwarp();
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) tc::tmem_ld16_nowait(tacc + (uint32_t)(bb * COUT + c0 + 16 * h), r[bb][h]);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[bb][16 * h + i] = __uint_as_float(r[bb][h][i]);
+  }
+  // + bias; shifted moments of each branch over the part (shift: its first value), summed in
+  // two interleaved lanes
+  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
+  boxes_free(lane);   // the scratch shares the boxes of the last stores
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) {
+#pragma unroll
+    for (int k = 0; k < PC / CW; ++k) {
+      float x[CW];
+      lds8(par + PL::at(b0 + bb, PF_BIAS) + c0 + CW * k, x);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) v[bb][CW * k + c] += x[c];
+    }
+    const float k0 = v[bb][0];
+    const unsigned long long kk = tc::f2pack(k0, k0);
+    unsigned long long s1 = 0ull, s2 = 0ull;
+#pragma unroll
+    for (int c = 0; c < PC; c += 2) {
+      const unsigned long long d = tc::f2sub(tc::f2pack(v[bb][c], v[bb][c + 1]), kk);
+      s1 = tc::f2add(s1, d);
+      s2 = tc::f2fma(d, d, s2);
+    }
+    float a1, b1, a2, b2;
+    tc::f2unpack(s1, a1, b1);
+    tc::f2unpack(s2, a2, b2);
+    const float t1 = a1 + b1, t2 = a2 + b2, m1 = t1 / (float)PC;
+    scr[(2 * bb) * 32 + lane] = k0 + m1;
+    scr[(2 * bb + 1) * 32 + lane] = fmaxf(t2 - t1 * m1, 0.f);
+  }
+  named_barrier(1 + quarter, 32 * EP);
+  float mean[G], rstd[G];
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) {
+    float n = 0.f, mu = 0.f, M2 = 0.f;
+#pragma unroll
+    for (int pp = 0; pp < EP; ++pp) {
+      const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE;
+      chan_fold(n, mu, M2, (float)PC, o[(2 * bb) * 32 + lane], o[(2 * bb + 1) * 32 + lane]);
+    }
+    mean[bb] = mu;
+    rstd[bb] = rsqrtf(M2 / (float)COUT + 1e-5f);
+  }
+  named_barrier(1 + quarter, 32 * EP);
+  // next_b = relu((v_b - mu) * rs * g + beta), one branch at a time through the warp's box
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) {
+    const int b = b0 + bb;
+    const unsigned long long mu2 = tc::f2pack(mean[bb], mean[bb]), rs2 = tc::f2pack(rstd[bb], rstd[bb]);
+    boxes_free(lane);
+#pragma unroll
+    for (int k = 0; k < PC / CW; ++k) {
+      float gm[CW], be[CW];
+      lds8(par + PL::at(b, PF_LN2G) + c0 + CW * k, gm);
+      lds8(par + PL::at(b, PF_LN2B) + c0 + CW * k, be);
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = CW * k + 2 * e;
+        unsigned long long t = tc::f2mul(tc::f2sub(tc::f2pack(v[bb][c], v[bb][c + 1]), mu2), rs2);
+        t = tc::f2fma(t, tc::f2pack(gm[2 * e], gm[2 * e + 1]), tc::f2pack(be[2 * e], be[2 * e + 1]));
+        float lo, hi;
+        tc::f2unpack(t, lo, hi);
+        w[e] = relu_pack2<KIND>(lo, hi);
+      }
+      *reinterpret_cast<uint4*>(box_chunk(sb.nx, PC * 2, lane, k)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    boxes_store(sb, b, false, lane);
   }
 }
 
@@ -847,14 +971,18 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
 // which also accumulates the head.  Statistics are merged across the lane quarter's parts
 // as in tc_epilogue.  Fused layers have pre-activation none or ReLU, so the product can be
 // formed in the statistics pass.
-template <int KIND, int NB, int COUT, int G, int EP, int MODE, int PW>
+template <int KIND, int NB, int COUT, int G, int EP, int MODE, int PW, int SCR_STRIDE>
 __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const float* par, uint32_t tacc,
                                                   uint32_t tstash, int g, bool valid, long long m, int part,
                                                   int quarter, int lane, float* scr_all, const StoreBox& sb) {
   constexpr int QMAX = HEAD_QMAX;
   using PL = ParLayout<COUT>;
   constexpr int NG = NB / G;
-  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+  if constexpr (MODE == 1 && PW == 32 && KIND != 2) {
+    conv1_group_part<KIND, G, COUT, EP, SCR_STRIDE>(par, tacc, g * G, part, quarter, lane, scr_all, sb);
+    return;
+  }
+  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
   int j_lo, n_ch;
   part_chunks<COUT, EP>(part, j_lo, n_ch);
   const int j_hi = j_lo + n_ch;
@@ -927,6 +1055,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const flo
     __syncwarp();
     tc::tmem_wait_st();
     const float n_mine = (float)(CW * n_ch);
+    if constexpr (PW > 0) boxes_free(lane);   // the scratch shares the boxes of the last stores
 #pragma unroll
     for (int s = 0; s <= G; ++s) {
       const float k = s < G ? k_b[s] : k_p, s1 = s < G ? s1_b[s] : s1_p, s2 = s < G ? s2_b[s] : s2_p;
@@ -942,7 +1071,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const flo
       for (int pp = 0; pp < EP; ++pp) {
         int f0, cnt;
         part_chunks<COUT, EP>(pp, f0, cnt);
-        const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS;
+        const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE;
         chan_fold(n, mu, M2, (float)(CW * cnt), o[(2 * s) * 32 + lane], o[(2 * s + 1) * 32 + lane]);
       }
       const float rs = rsqrtf(M2 / (float)COUT + 1e-5f);
@@ -1152,7 +1281,7 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const flo
         float sum = 0.f;
 #pragma unroll
         for (int pp = 0; pp < EP; ++pp)
-          sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_WARP_FLOATS + qq * 32 + lane];
+          sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE + qq * 32 + lane];
         const float v = sum + lds1(par + PL::HEADB + qq);
         a.llr[m * a.Q + qq] = v;
         if (!(fabsf(v) <= FLT_MAX)) *a.nonfinite = 1;
@@ -1198,7 +1327,8 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
   uint64_t* tfull = empty + K::STAGES;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-  float* scr_all = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256);
+  // the LayerNorm-moment scratch: its own block, or (staged) inside the warps' box regions
+  float* scr_all = reinterpret_cast<float*>(smem + (K::STAGED ? K::STG_OFF : (size_t)K::STAGES * K::STAGE + 256));
   float* par = reinterpret_cast<float*>(smem + (size_t)K::STAGES * K::STAGE + 256 + K::SCR);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1372,7 +1502,7 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
       const uint32_t tacc = tbase + (uint32_t)(acc * K::COLS) + lanes;
       StoreBox sb = {};
       if constexpr (K::STAGED) {
-        sb.xs = smem + K::STG_OFF + (size_t)(warp - 2) * (K::XS_B + K::NX_B);
+        sb.xs = smem + K::STG_OFF + (size_t)(warp - 2) * K::REG_B;
         sb.nx = sb.xs + K::XS_B;
         sb.xs_map = maps.xs;
         sb.nx_map = maps.nx;
@@ -1383,10 +1513,10 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
       }
       constexpr int PW = K::STAGED ? K::PW : 0;
       if constexpr (K::NG == 1)
-        tc_epilogue<KIND, NB, COUT, EP, MODE, PW>(a, par, tacc, valid, m, part, q, lane, scr_all, sb);
+        tc_epilogue<KIND, NB, COUT, EP, MODE, PW, K::SCR_STRIDE>(a, par, tacc, valid, m, part, q, lane, scr_all, sb);
       else
-        tc_epilogue_group<KIND, NB, COUT, K::G, EP, MODE, PW>(a, par, tacc, tbase + (uint32_t)K::STASH + lanes, g,
-                                                              valid, m, part, q, lane, scr_all, sb);
+        tc_epilogue_group<KIND, NB, COUT, K::G, EP, MODE, PW, K::SCR_STRIDE>(
+            a, par, tacc, tbase + (uint32_t)K::STASH + lanes, g, valid, m, part, q, lane, scr_all, sb);
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive_cluster(tempty0 + (uint32_t)(acc * sizeof(uint64_t)));
