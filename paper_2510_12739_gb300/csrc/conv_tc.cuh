@@ -544,6 +544,303 @@ __device__ __forceinline__ void boxes_store(const StoreBox& sb, int b, bool has_
   }
 }
 
+// Two 16-bit values of max(x, 0) in one register (lo in the low half).
+template <int KIND>
+__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
+  uint32_t r;
+  if constexpr (KIND == 3)
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  else
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// Next-input values of chunk k (8 channels) of row r of a warp's box, max(o, 0) first:
+// 16-bit pairs packed with the ReLU in the conversion; E4M3 codes of value x qinv.
+template <int KIND, int PC>
+__device__ __forceinline__ void put_next8(uint8_t* box, int r, int k, const float (&o)[CW], float qinv) {
+  if constexpr (KIND == 2) {
+    float t[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) t[c] = fmaxf(o[c], 0.f);
+    store8_e4m3(box_chunk(box, PC, r, k >> 1) + 8 * (k & 1), t, qinv);
+  } else {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) w[e] = relu_pack2<KIND>(o[2 * e], o[2 * e + 1]);
+    *reinterpret_cast<uint4*>(box_chunk(box, PC * 2, r, k)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Epilogue of the first conv of a residual block (MODE 1), for a warp whose part is PC = 16
+// or 32 channels of G branches (a branch group, or all branches): v_b = acc_b (x dq_b,
+// E4M3) + bias_b, next_b = relu(LN2_b(v_b)).  The part's columns of every branch come out
+// of TMEM with one wait and stay in registers through the moment exchange (no write-back,
+// no second read), and the arithmetic runs on two-lane FP32 instructions: a quarter of the
+// waits and half the FP32 instructions of the general epilogue, whose per-group time
+// otherwise exceeds the group's MMA time.
+template <int KIND, int G, int COUT, int EP, int SCR_STRIDE, int PC>
+__device__ __forceinline__ void conv1_part(const float* par, uint32_t tacc, int b0, int part, int quarter, int lane,
+                                           float* scr_all, const StoreBox& sb) {
+  using PL = ParLayout<COUT>;
+  static_assert(COUT == EP * PC && (PC == 16 || PC == 32), "equal parts of 16 or 32 channels");
+  const int c0 = PC * part;
+  float v[G][PC];
+  {
+    uint32_t r[G][PC / 16][16];
+    __syncwarp();
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb)
+#pragma unroll
+      for (int h = 0; h < PC / 16; ++h) tc::tmem_ld16_nowait(tacc + (uint32_t)(bb * COUT + c0 + 16 * h), r[bb][h]);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb)
+#pragma unroll
+      for (int h = 0; h < PC / 16; ++h)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[bb][16 * h + i] = __uint_as_float(r[bb][h][i]);
+  }
+  // (dequantise,) + bias; shifted moments of each branch over the part (shift: its first
+  // value), summed in two interleaved lanes
+  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
+  boxes_free(lane);   // the scratch shares the boxes of the last stores
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) {
+#pragma unroll
+    for (int k = 0; k < PC / CW; ++k) {
+      float x[CW];
+      if constexpr (KIND == 2) {
+        lds8(par + PL::at(b0 + bb, PF_DQ) + c0 + CW * k, x);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) v[bb][CW * k + c] *= x[c];
+      }
+      lds8(par + PL::at(b0 + bb, PF_BIAS) + c0 + CW * k, x);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) v[bb][CW * k + c] += x[c];
+    }
+    const float k0 = v[bb][0];
+    const unsigned long long kk = tc::f2pack(k0, k0);
+    unsigned long long s1 = 0ull, s2 = 0ull;
+#pragma unroll
+    for (int c = 0; c < PC; c += 2) {
+      const unsigned long long d = tc::f2sub(tc::f2pack(v[bb][c], v[bb][c + 1]), kk);
+      s1 = tc::f2add(s1, d);
+      s2 = tc::f2fma(d, d, s2);
+    }
+    float a1, b1, a2, b2;
+    tc::f2unpack(s1, a1, b1);
+    tc::f2unpack(s2, a2, b2);
+    const float t1 = a1 + b1, t2 = a2 + b2, m1 = t1 / (float)PC;
+    scr[(2 * bb) * 32 + lane] = k0 + m1;
+    scr[(2 * bb + 1) * 32 + lane] = fmaxf(t2 - t1 * m1, 0.f);
+  }
+  named_barrier(1 + quarter, 32 * EP);
+  float mean[G], rstd[G];
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) {
+    float n = 0.f, mu = 0.f, M2 = 0.f;
+#pragma unroll
+    for (int pp = 0; pp < EP; ++pp) {
+      const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE;
+      chan_fold(n, mu, M2, (float)PC, o[(2 * bb) * 32 + lane], o[(2 * bb + 1) * 32 + lane]);
+    }
+    mean[bb] = mu;
+    rstd[bb] = rsqrtf(M2 / (float)COUT + 1e-5f);
+  }
+  named_barrier(1 + quarter, 32 * EP);
+  // next_b = relu((v_b - mu) * rs * g + beta), one branch at a time through the warp's box
+#pragma unroll
+  for (int bb = 0; bb < G; ++bb) {
+    const int b = b0 + bb;
+    const float qinv = KIND == 2 ? lds1(par + PL::QINV + b) : 0.f;
+    const unsigned long long mu2 = tc::f2pack(mean[bb], mean[bb]), rs2 = tc::f2pack(rstd[bb], rstd[bb]);
+    boxes_free(lane);
+#pragma unroll
+    for (int k = 0; k < PC / CW; ++k) {
+      float gm[CW], be[CW], o[CW];
+      lds8(par + PL::at(b, PF_LN2G) + c0 + CW * k, gm);
+      lds8(par + PL::at(b, PF_LN2B) + c0 + CW * k, be);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = CW * k + 2 * e;
+        unsigned long long t = tc::f2mul(tc::f2sub(tc::f2pack(v[bb][c], v[bb][c + 1]), mu2), rs2);
+        t = tc::f2fma(t, tc::f2pack(gm[2 * e], gm[2 * e + 1]), tc::f2pack(be[2 * e], be[2 * e + 1]));
+        tc::f2unpack(t, o[2 * e], o[2 * e + 1]);
+      }
+      put_next8<KIND, PC>(sb.nx, lane, k, o, qinv);
+    }
+    boxes_store(sb, b, false, lane);
+  }
+}
+
+// Epilogue of the second conv of a fused residual block (MODE 2), for a warp whose part is
+// PC = 16 or 32 channels of G branches b0 .. b0 + G - 1 (a branch group: first / last say
+// which; or all branches: both).  Pass 1: v_b = acc_b (x dq_b, E4M3) + bias_b + resid_b,
+// written back to TMEM; the running Hadamard product of the v_b in the TMEM stash; the LN1
+// moments of the support branches and, in the last group, those of the product.  Pass 2,
+// one output at a time through the warp's boxes: each support's stream x_b = v_b and next
+// input relu(LN1_b(v_b)); in the last group branch 0's stream x_0 = LN_f(product) and next
+// input relu(x_0).  Pass 1 goes in 8-column steps whose residual rows and TMEM loads are
+// all issued before the step's one wait (16-column steps spill at the 128-register budget
+// of a 14-warp CTA and measured 6 % slower); pass 2 reads 16 columns per wait; the
+// arithmetic runs on two-lane FP32 instructions.
+template <int KIND, int G, int COUT, int EP, int SCR_STRIDE, int PC>
+__device__ __forceinline__ void conv2_part(const TcConvArgs& a, const float* par, uint32_t tacc, uint32_t tstash,
+                                           int b0, bool first, bool last, bool valid, long long m, int part,
+                                           int quarter, int lane, float* scr_all, const StoreBox& sb) {
+  using PL = ParLayout<COUT>;
+  static_assert(COUT == EP * PC && (PC == 16 || PC == 32), "equal parts of 16 or 32 channels");
+  const int c0 = PC * part;
+  // shifted moments: slot bb < G for support branch b0 + bb, slot G for the product
+  float ks[G + 1];
+  unsigned long long s1[G + 1], s2[G + 1];
+#pragma unroll
+  for (int i = 0; i <= G; ++i) {
+    ks[i] = 0.f;
+    s1[i] = s2[i] = 0ull;
+  }
+#pragma unroll
+  for (int j = 0; j < PC / CW; ++j) {
+    const int ch = c0 + CW * j;
+    float r[G][CW];
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb) {
+      if (valid) {
+        ldg8(a.resid[b0 + bb] + m * COUT + ch, r[bb]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CW; ++c) r[bb][c] = 0.f;
+      }
+    }
+    uint32_t acc[G][CW], qr[CW];
+    __syncwarp();
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb) tc::tmem_ld8_nowait(tacc + (uint32_t)(bb * COUT + ch), acc[bb]);
+    if (!first) tc::tmem_ld8_nowait(tstash + (uint32_t)ch, qr);
+    tc::tmem_wait_ld();
+    unsigned long long q[CW / 2];
+#pragma unroll
+    for (int i = 0; i < CW / 2; ++i)
+      q[i] = first ? tc::f2pack(1.f, 1.f) : tc::f2pack(__uint_as_float(qr[2 * i]), __uint_as_float(qr[2 * i + 1]));
+    float bi[G][CW];
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb) lds8(par + PL::at(b0 + bb, PF_BIAS) + ch, bi[bb]);
+#pragma unroll
+    for (int bb = 0; bb < G; ++bb) {
+      float dq[CW];
+      if constexpr (KIND == 2) lds8(par + PL::at(b0 + bb, PF_DQ) + ch, dq);
+      float v[CW];
+#pragma unroll
+      for (int e = 0; e < CW / 2; ++e) {
+        unsigned long long t = tc::f2pack(__uint_as_float(acc[bb][2 * e]), __uint_as_float(acc[bb][2 * e + 1]));
+        if constexpr (KIND == 2) t = tc::f2mul(t, tc::f2pack(dq[2 * e], dq[2 * e + 1]));
+        t = tc::f2add(t, tc::f2pack(bi[bb][2 * e], bi[bb][2 * e + 1]));
+        t = tc::f2add(t, tc::f2pack(r[bb][2 * e], r[bb][2 * e + 1]));
+        tc::f2unpack(t, v[2 * e], v[2 * e + 1]);
+      }
+      tc::tmem_st8_nowait(tacc + (uint32_t)(bb * COUT + ch), v);
+      if (b0 + bb != 0) {
+        if (j == 0) ks[bb] = v[0];
+        const unsigned long long kk = tc::f2pack(ks[bb], ks[bb]);
+#pragma unroll
+        for (int i = 0; i < CW / 2; ++i) {
+          const unsigned long long d = tc::f2sub(tc::f2pack(v[2 * i], v[2 * i + 1]), kk);
+          s1[bb] = tc::f2add(s1[bb], d);
+          s2[bb] = tc::f2fma(d, d, s2[bb]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < CW / 2; ++i) q[i] = tc::f2mul(q[i], tc::f2pack(v[2 * i], v[2 * i + 1]));
+    }
+    float qf[CW];
+#pragma unroll
+    for (int i = 0; i < CW / 2; ++i) tc::f2unpack(q[i], qf[2 * i], qf[2 * i + 1]);
+    if (last) {
+      if (j == 0) ks[G] = qf[0];
+      const unsigned long long kk = tc::f2pack(ks[G], ks[G]);
+#pragma unroll
+      for (int i = 0; i < CW / 2; ++i) {
+        const unsigned long long d = tc::f2sub(q[i], kk);
+        s1[G] = tc::f2add(s1[G], d);
+        s2[G] = tc::f2fma(d, d, s2[G]);
+      }
+    }
+    tc::tmem_st8_nowait(tstash + (uint32_t)ch, qf);
+  }
+  __syncwarp();
+  tc::tmem_wait_st();
+  // publish, then merge over the quarter's parts (Chan), the slots in use
+  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
+  boxes_free(lane);   // the scratch shares the boxes of the last stores
+#pragma unroll
+  for (int i = 0; i <= G; ++i) {
+    if (i < G ? b0 + i == 0 : !last) continue;
+    float a1, c1, a2, c2;
+    tc::f2unpack(s1[i], a1, c1);
+    tc::f2unpack(s2[i], a2, c2);
+    const float t1 = a1 + c1, t2 = a2 + c2, m1 = t1 / (float)PC;
+    scr[(2 * i) * 32 + lane] = ks[i] + m1;
+    scr[(2 * i + 1) * 32 + lane] = fmaxf(t2 - t1 * m1, 0.f);
+  }
+  named_barrier(1 + quarter, 32 * EP);
+  float mean[G + 1], rstd[G + 1];
+#pragma unroll
+  for (int i = 0; i <= G; ++i) {
+    mean[i] = 0.f;
+    rstd[i] = 1.f;
+    if (i < G ? b0 + i == 0 : !last) continue;
+    float n = 0.f, mu = 0.f, M2 = 0.f;
+#pragma unroll
+    for (int pp = 0; pp < EP; ++pp) {
+      const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE;
+      chan_fold(n, mu, M2, (float)PC, o[(2 * i) * 32 + lane], o[(2 * i + 1) * 32 + lane]);
+    }
+    mean[i] = mu;
+    rstd[i] = rsqrtf(M2 / (float)COUT + 1e-5f);
+  }
+  named_barrier(1 + quarter, 32 * EP);
+  // pass 2: the supports of the group, then (last group) branch 0
+#pragma unroll
+  for (int ob = 0; ob <= G; ++ob) {
+    const bool is_main = ob == G;
+    const int b = is_main ? 0 : b0 + ob;
+    if (is_main ? !last : b == 0) continue;
+    const float qinv = KIND == 2 ? lds1(par + PL::QINV + b) : 0.f;
+    const unsigned long long mu2 = tc::f2pack(mean[ob], mean[ob]), rs2 = tc::f2pack(rstd[ob], rstd[ob]);
+    boxes_free(lane);
+#pragma unroll
+    for (int h = 0; h < PC / 16; ++h) {
+      const int ch = c0 + 16 * h;
+      uint32_t xr[16];
+      __syncwarp();
+      tc::tmem_ld16_nowait(is_main ? tstash + (uint32_t)ch : tacc + (uint32_t)(ob * COUT + ch), xr);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int cc = ch + CW * k;
+        float gm[CW], be[CW], y[CW], o[CW];
+        lds8(par + (is_main ? PL::LNFG : PL::at(b, PF_LN1G)) + cc, gm);
+        lds8(par + (is_main ? PL::LNFB : PL::at(b, PF_LN1B)) + cc, be);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c = CW * k + 2 * e;
+          const unsigned long long x2 = tc::f2pack(__uint_as_float(xr[c]), __uint_as_float(xr[c + 1]));
+          // LayerNorm: of the product for branch 0 (its stream), of v_b for a support (its
+          // next input); a support's stream is v_b itself
+          unsigned long long t = tc::f2mul(tc::f2sub(x2, mu2), rs2);
+          t = tc::f2fma(t, tc::f2pack(gm[2 * e], gm[2 * e + 1]), tc::f2pack(be[2 * e], be[2 * e + 1]));
+          tc::f2unpack(is_main ? t : x2, y[2 * e], y[2 * e + 1]);
+          tc::f2unpack(t, o[2 * e], o[2 * e + 1]);
+        }
+        stage_xs8<PC>(sb.xs, lane, (cc - c0) / CW, y);
+        put_next8<KIND, PC>(sb.nx, lane, (cc - c0) / CW, o, qinv);
+      }
+    }
+    boxes_store(sb, b, true, lane);
+  }
+}
+
 // The fused epilogue for one RE (this thread's TMEM lane) and one part of its channels.
 // Pass 1 (when a LayerNorm is applied) folds each branch's values, and the fused product,
 // into shifted first and second moments; the parts of a lane quarter publish theirs in
@@ -558,6 +855,18 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
                                             const StoreBox& sb) {
   constexpr int QMAX = HEAD_QMAX;
   using PL = ParLayout<COUT>;
+  // the fixed residual-block shapes with equal 16- or 32-channel parts (conv1: when the
+  // part's columns of all branches fit the 96 registers of an 18-warp CTA beside the rest;
+  // conv2: when the accumulator set's unused columns can hold the product)
+  if constexpr (MODE == 1 && (PW == 16 || PW == 32) && NB * PW <= 48) {
+    conv1_part<KIND, NB, COUT, EP, SCR_STRIDE, PW>(par, tacc, 0, part, quarter, lane, scr_all, sb);
+    return;
+  }
+  if constexpr (MODE == 2 && (PW == 16 || PW == 32) && pow2_ceil(NB * COUT) >= NB * COUT + COUT) {
+    conv2_part<KIND, NB, COUT, EP, SCR_STRIDE, PW>(a, par, tacc, tacc + (uint32_t)(NB * COUT), 0, true, true, valid,
+                                                   m, part, quarter, lane, scr_all, sb);
+    return;
+  }
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
   int j_lo, n_ch;
   part_chunks<COUT, EP>(part, j_lo, n_ch);
@@ -851,284 +1160,6 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
   }
 }
 
-// Two 16-bit values of max(x, 0) in one register (lo in the low half).
-template <int KIND>
-__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
-  uint32_t r;
-  if constexpr (KIND == 3)
-    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  else
-    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-
-// Epilogue of the first conv of a residual block (MODE 1) on the branch-group path, for a
-// warp whose part is 32 channels, 16-bit outputs: v_b = acc_b + bias_b, next_b =
-// relu(LN2_b(v_b)) for the G branches of the group.  The part's 32 columns of every branch
-// come out of TMEM with one wait and stay in registers through the moment exchange (no
-// write-back, no second read), and the arithmetic runs on two-lane FP32 instructions: a
-// quarter of the waits and half the FP32 instructions of the general epilogue, whose
-// per-group time otherwise exceeds the group's MMA time.
-template <int KIND, int G, int COUT, int EP, int SCR_STRIDE>
-__device__ __forceinline__ void conv1_group_part(const float* par, uint32_t tacc, int b0, int part, int quarter,
-                                                 int lane, float* scr_all, const StoreBox& sb) {
-  using PL = ParLayout<COUT>;
-  constexpr int PC = 32;
-  static_assert(COUT == EP * PC, "one 32-channel part per warp");
-  const int c0 = PC * part;
-  float v[G][PC];
-  {
-    uint32_t r[G][2][16];
-    __syncwarp();
-#pragma unroll
-    for (int bb = 0; bb < G; ++bb)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) tc::tmem_ld16_nowait(tacc + (uint32_t)(bb * COUT + c0 + 16 * h), r[bb][h]);
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int bb = 0; bb < G; ++bb)
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[bb][16 * h + i] = __uint_as_float(r[bb][h][i]);
-  }
-  // + bias; shifted moments of each branch over the part (shift: its first value), summed in
-  // two interleaved lanes
-  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
-  boxes_free(lane);   // the scratch shares the boxes of the last stores
-#pragma unroll
-  for (int bb = 0; bb < G; ++bb) {
-#pragma unroll
-    for (int k = 0; k < PC / CW; ++k) {
-      float x[CW];
-      lds8(par + PL::at(b0 + bb, PF_BIAS) + c0 + CW * k, x);
-#pragma unroll
-      for (int c = 0; c < CW; ++c) v[bb][CW * k + c] += x[c];
-    }
-    const float k0 = v[bb][0];
-    const unsigned long long kk = tc::f2pack(k0, k0);
-    unsigned long long s1 = 0ull, s2 = 0ull;
-#pragma unroll
-    for (int c = 0; c < PC; c += 2) {
-      const unsigned long long d = tc::f2sub(tc::f2pack(v[bb][c], v[bb][c + 1]), kk);
-      s1 = tc::f2add(s1, d);
-      s2 = tc::f2fma(d, d, s2);
-    }
-    float a1, b1, a2, b2;
-    tc::f2unpack(s1, a1, b1);
-    tc::f2unpack(s2, a2, b2);
-    const float t1 = a1 + b1, t2 = a2 + b2, m1 = t1 / (float)PC;
-    scr[(2 * bb) * 32 + lane] = k0 + m1;
-    scr[(2 * bb + 1) * 32 + lane] = fmaxf(t2 - t1 * m1, 0.f);
-  }
-  named_barrier(1 + quarter, 32 * EP);
-  float mean[G], rstd[G];
-#pragma unroll
-  for (int bb = 0; bb < G; ++bb) {
-    float n = 0.f, mu = 0.f, M2 = 0.f;
-#pragma unroll
-    for (int pp = 0; pp < EP; ++pp) {
-      const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE;
-      chan_fold(n, mu, M2, (float)PC, o[(2 * bb) * 32 + lane], o[(2 * bb + 1) * 32 + lane]);
-    }
-    mean[bb] = mu;
-    rstd[bb] = rsqrtf(M2 / (float)COUT + 1e-5f);
-  }
-  named_barrier(1 + quarter, 32 * EP);
-  // next_b = relu((v_b - mu) * rs * g + beta), one branch at a time through the warp's box
-#pragma unroll
-  for (int bb = 0; bb < G; ++bb) {
-    const int b = b0 + bb;
-    const unsigned long long mu2 = tc::f2pack(mean[bb], mean[bb]), rs2 = tc::f2pack(rstd[bb], rstd[bb]);
-    boxes_free(lane);
-#pragma unroll
-    for (int k = 0; k < PC / CW; ++k) {
-      float gm[CW], be[CW];
-      lds8(par + PL::at(b, PF_LN2G) + c0 + CW * k, gm);
-      lds8(par + PL::at(b, PF_LN2B) + c0 + CW * k, be);
-      uint32_t w[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int c = CW * k + 2 * e;
-        unsigned long long t = tc::f2mul(tc::f2sub(tc::f2pack(v[bb][c], v[bb][c + 1]), mu2), rs2);
-        t = tc::f2fma(t, tc::f2pack(gm[2 * e], gm[2 * e + 1]), tc::f2pack(be[2 * e], be[2 * e + 1]));
-        float lo, hi;
-        tc::f2unpack(t, lo, hi);
-        w[e] = relu_pack2<KIND>(lo, hi);
-      }
-      *reinterpret_cast<uint4*>(box_chunk(sb.nx, PC * 2, lane, k)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    boxes_store(sb, b, false, lane);
-  }
-}
-
-// Epilogue of the second conv of a fused residual block (MODE 2) on the branch-group path,
-// for a warp whose part is 32 channels, 16-bit next inputs.  Pass 1: v_b = acc_b + bias_b +
-// resid_b, written back to TMEM; the running Hadamard product of the v_b over the groups in
-// the TMEM stash; the LN1 moments of the support branches and, in the last group, those of
-// the product.  Pass 2, one output at a time through the warp's boxes: each support's
-// stream x_b = v_b and next input relu(LN1_b(v_b)); in the last group branch 0's stream
-// x_0 = LN_f(product) and next input relu(x_0).  Pass 1 goes in 8-column steps whose
-// residual rows (both branches) and TMEM loads are all issued before the step's one wait
-// (16-column steps spill at the 128-register budget of a 14-warp CTA and measured 6 %
-// slower); pass 2 reads 16 columns per wait; the arithmetic runs on two-lane FP32.
-template <int KIND, int G, int COUT, int EP, int SCR_STRIDE>
-__device__ __forceinline__ void conv2_group_part(const TcConvArgs& a, const float* par, uint32_t tacc,
-                                                 uint32_t tstash, int b0, bool first, bool last, bool valid,
-                                                 long long m, int part, int quarter, int lane, float* scr_all,
-                                                 const StoreBox& sb) {
-  using PL = ParLayout<COUT>;
-  constexpr int PC = 32;
-  static_assert(COUT == EP * PC, "one 32-channel part per warp");
-  const int c0 = PC * part;
-  // shifted moments: slot bb < G for support branch b0 + bb, slot G for the product
-  float ks[G + 1];
-  unsigned long long s1[G + 1], s2[G + 1];
-#pragma unroll
-  for (int i = 0; i <= G; ++i) {
-    ks[i] = 0.f;
-    s1[i] = s2[i] = 0ull;
-  }
-#pragma unroll
-  for (int j = 0; j < PC / CW; ++j) {
-    const int ch = c0 + CW * j;
-    float r[G][CW];
-#pragma unroll
-    for (int bb = 0; bb < G; ++bb) {
-      if (valid) {
-        ldg8(a.resid[b0 + bb] + m * COUT + ch, r[bb]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < CW; ++c) r[bb][c] = 0.f;
-      }
-    }
-    uint32_t acc[G][CW], qr[CW];
-    __syncwarp();
-#pragma unroll
-    for (int bb = 0; bb < G; ++bb) tc::tmem_ld8_nowait(tacc + (uint32_t)(bb * COUT + ch), acc[bb]);
-    if (!first) tc::tmem_ld8_nowait(tstash + (uint32_t)ch, qr);
-    tc::tmem_wait_ld();
-    unsigned long long q[CW / 2];
-#pragma unroll
-    for (int i = 0; i < CW / 2; ++i)
-      q[i] = first ? tc::f2pack(1.f, 1.f) : tc::f2pack(__uint_as_float(qr[2 * i]), __uint_as_float(qr[2 * i + 1]));
-    float bi[G][CW];
-#pragma unroll
-    for (int bb = 0; bb < G; ++bb) lds8(par + PL::at(b0 + bb, PF_BIAS) + ch, bi[bb]);
-#pragma unroll
-    for (int bb = 0; bb < G; ++bb) {
-      float v[CW];
-#pragma unroll
-      for (int e = 0; e < CW / 2; ++e) {
-        unsigned long long t = tc::f2add(tc::f2pack(__uint_as_float(acc[bb][2 * e]), __uint_as_float(acc[bb][2 * e + 1])),
-                                         tc::f2pack(bi[bb][2 * e], bi[bb][2 * e + 1]));
-        t = tc::f2add(t, tc::f2pack(r[bb][2 * e], r[bb][2 * e + 1]));
-        tc::f2unpack(t, v[2 * e], v[2 * e + 1]);
-      }
-      tc::tmem_st8_nowait(tacc + (uint32_t)(bb * COUT + ch), v);
-      if (b0 + bb != 0) {
-        if (j == 0) ks[bb] = v[0];
-        const unsigned long long kk = tc::f2pack(ks[bb], ks[bb]);
-#pragma unroll
-        for (int i = 0; i < CW / 2; ++i) {
-          const unsigned long long d = tc::f2sub(tc::f2pack(v[2 * i], v[2 * i + 1]), kk);
-          s1[bb] = tc::f2add(s1[bb], d);
-          s2[bb] = tc::f2fma(d, d, s2[bb]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < CW / 2; ++i) q[i] = tc::f2mul(q[i], tc::f2pack(v[2 * i], v[2 * i + 1]));
-    }
-    float qf[CW];
-#pragma unroll
-    for (int i = 0; i < CW / 2; ++i) tc::f2unpack(q[i], qf[2 * i], qf[2 * i + 1]);
-    if (last) {
-      if (j == 0) ks[G] = qf[0];
-      const unsigned long long kk = tc::f2pack(ks[G], ks[G]);
-#pragma unroll
-      for (int i = 0; i < CW / 2; ++i) {
-        const unsigned long long d = tc::f2sub(q[i], kk);
-        s1[G] = tc::f2add(s1[G], d);
-        s2[G] = tc::f2fma(d, d, s2[G]);
-      }
-    }
-    tc::tmem_st8_nowait(tstash + (uint32_t)ch, qf);
-  }
-  __syncwarp();
-  tc::tmem_wait_st();
-  // publish, then merge over the quarter's parts (Chan), the slots in use
-  float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
-  boxes_free(lane);   // the scratch shares the boxes of the last stores
-#pragma unroll
-  for (int i = 0; i <= G; ++i) {
-    if (i < G ? b0 + i == 0 : !last) continue;
-    float a1, c1, a2, c2;
-    tc::f2unpack(s1[i], a1, c1);
-    tc::f2unpack(s2[i], a2, c2);
-    const float t1 = a1 + c1, t2 = a2 + c2, m1 = t1 / (float)PC;
-    scr[(2 * i) * 32 + lane] = ks[i] + m1;
-    scr[(2 * i + 1) * 32 + lane] = fmaxf(t2 - t1 * m1, 0.f);
-  }
-  named_barrier(1 + quarter, 32 * EP);
-  float mean[G + 1], rstd[G + 1];
-#pragma unroll
-  for (int i = 0; i <= G; ++i) {
-    mean[i] = 0.f;
-    rstd[i] = 1.f;
-    if (i < G ? b0 + i == 0 : !last) continue;
-    float n = 0.f, mu = 0.f, M2 = 0.f;
-#pragma unroll
-    for (int pp = 0; pp < EP; ++pp) {
-      const float* o = scr_all + (size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE;
-      chan_fold(n, mu, M2, (float)PC, o[(2 * i) * 32 + lane], o[(2 * i + 1) * 32 + lane]);
-    }
-    mean[i] = mu;
-    rstd[i] = rsqrtf(M2 / (float)COUT + 1e-5f);
-  }
-  named_barrier(1 + quarter, 32 * EP);
-  // pass 2: the supports of the group, then (last group) branch 0
-#pragma unroll
-  for (int ob = 0; ob <= G; ++ob) {
-    const bool is_main = ob == G;
-    const int b = is_main ? 0 : b0 + ob;
-    if (is_main ? !last : b == 0) continue;
-    const unsigned long long mu2 = tc::f2pack(mean[ob], mean[ob]), rs2 = tc::f2pack(rstd[ob], rstd[ob]);
-    boxes_free(lane);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ch = c0 + 16 * h;
-      uint32_t xr[16];
-      __syncwarp();
-      tc::tmem_ld16_nowait(is_main ? tstash + (uint32_t)ch : tacc + (uint32_t)(ob * COUT + ch), xr);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int cc = ch + CW * k;
-        float gm[CW], be[CW], y[CW];
-        lds8(par + (is_main ? PL::LNFG : PL::at(b, PF_LN1G)) + cc, gm);
-        lds8(par + (is_main ? PL::LNFB : PL::at(b, PF_LN1B)) + cc, be);
-        uint32_t w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int c = CW * k + 2 * e;
-          const unsigned long long x2 = tc::f2pack(__uint_as_float(xr[c]), __uint_as_float(xr[c + 1]));
-          // LayerNorm: of the product for branch 0 (its stream), of v_b for a support (its
-          // next input); a support's stream is v_b itself
-          unsigned long long t = tc::f2mul(tc::f2sub(x2, mu2), rs2);
-          t = tc::f2fma(t, tc::f2pack(gm[2 * e], gm[2 * e + 1]), tc::f2pack(be[2 * e], be[2 * e + 1]));
-          float lo, hi;
-          tc::f2unpack(is_main ? t : x2, y[2 * e], y[2 * e + 1]);
-          tc::f2unpack(t, lo, hi);
-          w[e] = relu_pack2<KIND>(lo, hi);
-        }
-        stage_xs8<PC>(sb.xs, lane, 2 * h + k, y);
-        *reinterpret_cast<uint4*>(box_chunk(sb.nx, PC * 2, lane, 2 * h + k)) = make_uint4(w[0], w[1], w[2], w[3]);
-      }
-    }
-    boxes_store(sb, b, true, lane);
-  }
-}
-
 // Epilogue of branch group g (branches g*G .. g*G + G - 1) of a tile whose branches are
 // computed G at a time: the MMAs of one group overlap the epilogue of the previous one, and
 // TMEM columns [tstash, tstash + COUT) carry the running Hadamard product from group to
@@ -1145,13 +1176,13 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const flo
   constexpr int QMAX = HEAD_QMAX;
   using PL = ParLayout<COUT>;
   constexpr int NG = NB / G;
-  if constexpr (MODE == 1 && PW == 32 && KIND != 2) {
-    conv1_group_part<KIND, G, COUT, EP, SCR_STRIDE>(par, tacc, g * G, part, quarter, lane, scr_all, sb);
+  if constexpr (MODE == 1 && (PW == 16 || PW == 32)) {
+    conv1_part<KIND, G, COUT, EP, SCR_STRIDE, PW>(par, tacc, g * G, part, quarter, lane, scr_all, sb);
     return;
   }
-  if constexpr (MODE == 2 && PW == 32 && KIND != 2) {
-    conv2_group_part<KIND, G, COUT, EP, SCR_STRIDE>(a, par, tacc, tstash, g * G, g == 0, g == NB / G - 1, valid, m,
-                                                    part, quarter, lane, scr_all, sb);
+  if constexpr (MODE == 2 && (PW == 16 || PW == 32)) {
+    conv2_part<KIND, G, COUT, EP, SCR_STRIDE, PW>(a, par, tacc, tstash, g * G, g == 0, g == NB / G - 1, valid, m,
+                                                  part, quarter, lane, scr_all, sb);
     return;
   }
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
