@@ -283,7 +283,12 @@ def roofline_of(w, net, B, rx, steps, n_sm):
     conv_ms, conv_n = rx.profile_read(api.PROFILE_KINDS["conv"])
     avg_s = (conv_ms / max(conv_n, 1)) / 1e3
     per_step = conv_n / max(1, steps)
-    flops_per_launch = conv_flops(net, B) * n_body_convs(net) / max(1e-9, per_step)
+    # the whole-network kernel runs every layer and the head of the batch in one launch
+    whole = rx.whole_network("auto") and B >= api.WHOLE_NET_MIN_SLOTS
+    if whole:
+        flops_per_launch = net_flops_per_re(net) * B * net.n_sym * net.n_sc / max(1e-9, per_step)
+    else:
+        flops_per_launch = conv_flops(net, B) * n_body_convs(net) / max(1e-9, per_step)
     achieved = flops_per_launch / avg_s / 1e12 if conv_n else None
     if w.precision == "fp32":
         peak = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -303,8 +308,12 @@ def roofline_of(w, net, B, rx, steps, n_sm):
             else:
                 peak = peak * NOMINAL_FP8_OVER_BF16
                 src += " x 4.5/2.25 (nominal FP8/BF16 dense)"
-        kname = (f"conv_tc_kernel<{w.precision},{net.n_branches},{net.width},{net.width}> "
-                 f"(tcgen05 body 3x3 conv, {net.n_branches} branches per launch)")
+        if whole:
+            kname = (f"smallnet_kernel<{w.precision}> (tcgen05 whole network: every layer and the head, "
+                     f"one slot per CTA; FLOPs of all layers)")
+        else:
+            kname = (f"conv_tc_kernel<{w.precision},{net.n_branches},{net.width},{net.width}> "
+                     f"(tcgen05 body 3x3 conv, {net.n_branches} branches per launch)")
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic_per_launch(w, net, B, per_step),
             "kernel": kname, "peak_source": src, "launches": conv_n, "avg_launch_ms": avg_s * 1e3}

@@ -106,3 +106,14 @@ def test_checkpoint_hash_tracks_the_network_shape(lib):
     assert lib.conet_save_checkpoint(None, 0, None, 0) == -1
     assert lib.conet_load_checkpoint(None, None, 0, None) == -1
     assert lib.conet_selftest_timeout(None, 1e-3, None) == -1
+
+
+def test_whole_network_threshold_matches_header():
+    """The binding's automatic whole-network threshold is the header's constant, and the
+    mode argument is range-checked on the host."""
+    from paper_2510_12739_gb300 import api
+    src = open(os.path.join(ROOT, "include", "conet.h")).read()
+    m = re.search(r"#define\s+CONET_WHOLE_NET_MIN_SLOTS\s+(\d+)", src)
+    assert m and int(m.group(1)) == api.WHOLE_NET_MIN_SLOTS
+    lib = api.lib()
+    assert lib.conet_whole_network(None, 1, None) == -1
