@@ -241,17 +241,19 @@ int conet_graphs(conet_t h, int enable);
 /*
  * Whole-network kernel for small plain networks (2 branches x 32 channels, T (F + 1) <=
  * 1024, up to 8 layers, BF16 or calibrated E4M3 inference handles, product fusion): every
- * layer and the head of a slot run in one persistent kernel (one slot per CTA at a time)
- * whose activations stay in shared memory, instead of one launch per layer (the 14 x 72
- * networks of the paper's Example I are launch- and L2-bound layer by layer).  Results
- * equal the layer-by-layer path of the same precision up to FP32 accumulation order (and,
- * for E4M3, the rare activation code that order moves).  enable: 0 = never (layer by
- * layer), 1 = automatic (the default: forward calls of at least CONET_WHOLE_NET_MIN_SLOTS
- * slots, below which a slot per CTA leaves most SMs idle), 2 = every forward call.  An
- * E4M3 forward that calibrates runs layer by layer.  *available (may be NULL) <- 1 when the
- * handle's network qualifies.
+ * layer and the head of a slot run in one kernel whose activations stay in shared memory,
+ * instead of one launch per layer (the 14 x 72 networks of the paper's Example I, Sec. III,
+ * are launch- and L2-bound layer by layer).  Large calls run one slot per CTA; calls of few
+ * slots split each slot over a cluster of 8, 4 or 2 CTAs (one per SM) that exchange the
+ * rows at their tile boundaries through distributed shared memory (grids of F + 2 <= 128
+ * columns).  Results equal the layer-by-layer path of the same precision up to FP32
+ * accumulation order (and, for E4M3, the rare activation code that order moves).
+ * enable: 0 = never (layer by layer), 1 = automatic (the default: forward calls of at least
+ * CONET_WHOLE_NET_MIN_SLOTS slots), 2 = every forward call.  An E4M3 forward that
+ * calibrates runs layer by layer.  *available (may be NULL) <- 1 when the handle's network
+ * qualifies.  Errors: CONET_ERR_ARG for a NULL handle or enable outside 0..2.
  */
-#define CONET_WHOLE_NET_MIN_SLOTS 64
+#define CONET_WHOLE_NET_MIN_SLOTS 1
 int conet_whole_network(conet_t h, int enable, int* available);
 
 /*

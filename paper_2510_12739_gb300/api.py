@@ -309,4 +309,4 @@ def launch_count() -> int:
 PROFILE_KINDS = {"conv": 0, "conv_in": 1, "fuse": 2, "assemble": 3, "backward": 4, "adam": 5}
 # conet.h's CONET_WHOLE_NET_MIN_SLOTS: in automatic mode, forward calls of at least this many
 # slots run the whole-network kernel
-WHOLE_NET_MIN_SLOTS = 64
+WHOLE_NET_MIN_SLOTS = 1

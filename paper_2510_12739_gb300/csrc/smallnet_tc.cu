@@ -25,6 +25,13 @@
 //     input grid once the first layer has read it: the assembled input (BF16 x 16 or E4M3 x 32
 //     channels: 32-byte rows), repacked in global memory into the same padded row order (zero
 //     at the padding), comes in as 256-row boxes that land on 8 KB boundaries.
+// Calls of few slots split a slot over a cluster of S = 2, 4 or 8 CTAs (one per SM), CTA r
+// computing tiles [r 8/S, (r + 1) 8/S) of every layer.  A tile's taps reach W + 1 <= 128 rows
+// beyond it, so each CTA writes the first and last W + 1 rows of its outputs also into its
+// neighbours' grids (distributed shared memory).  Per layer, a CTA writes into a neighbour
+// only after the neighbour's MMAs of that layer are complete (`ndone`, signalled remotely),
+// and a CTA's next-layer MMAs start only after both neighbours' writes (`hfull`, release /
+// acquire at cluster scope, with an async-proxy fence on the writing side).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -91,9 +98,44 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <int KIND>
+// ---- cluster-split slots: distributed shared memory and cluster-scope barriers
+// generic-proxy writes to any CTA's shared memory become visible to the async proxy
+__device__ __forceinline__ void fence_proxy_async_cluster() {
+  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+// 16 bytes into shared::cluster address caddr (this CTA's or another of the cluster)
+__device__ __forceinline__ void st_cluster16(uint32_t caddr, uint4 v) {
+  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(caddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+// arrive on another CTA's mbarrier, releasing this thread's prior writes at cluster scope
+__device__ __forceinline__ void mbar_arrive_release_cluster(uint32_t caddr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+// bounded wait on this CTA's mbarrier with cluster-scope acquire (records `where` on timeout)
+__device__ __forceinline__ bool mbar_wait_acq_cluster(uint64_t* bar, uint32_t parity, int* err, int where) {
+  const uint64_t t0 = tc::globaltimer_ns();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tc::smem_u32(bar)), "r"(parity), "r"(tc::WAIT_HINT_NS)
+        : "memory");
+    if (ok) return true;
+    if (tc::globaltimer_ns() - t0 > tc::WAIT_NS) break;
+  }
+  atomicCAS(err, 0, where);
+  return false;
+}
+
+template <int KIND, int S>
 __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_constant__ SnMaps maps, SmallNetArgs a) {
   using K = SnK<KIND>;
+  constexpr int TPC = SN_TILES / S;          // output tiles per CTA
+  constexpr uint32_t TCOLS = TPC * SN_NB * SN_C;   // TMEM columns (a power of two >= 64)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const SnLayout L = sn_layout(a.T, a.F, K::ARow);
@@ -104,10 +146,15 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
   uint64_t* wempty = bars + 3;   // the layer's MMAs have read them
   uint64_t* dfull = bars + 4;    // the layer's accumulators are complete
   uint64_t* afull = bars + 5;    // the epilogue drained TMEM and wrote the next inputs (8 warps)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
+  uint64_t* ndone = bars + 6;    // (S > 1) the neighbours' MMAs of the layer are complete
+  uint64_t* hfull = bars + 7;    // (S > 1) the neighbours' halo rows of the layer's outputs are written
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = a.T, F = a.F, W = F + 1, D = a.depth;
   const int p0 = W;              // first output row: P(0, -1)
+  const int rank = S > 1 ? (int)tc::cluster_ctarank() : 0;
+  const int cid = (int)blockIdx.x / S, ncl = (int)gridDim.x / S;   // cluster (slot group) index
+  const int nn = (rank > 0 ? 1 : 0) + (rank < S - 1 ? 1 : 0);       // neighbours in the cluster
 
   // zero both grids and the input grid (their padding rows must read as zero), then init
   for (int i = threadIdx.x; i < (L.w_off) / 16; i += blockDim.x)
@@ -120,25 +167,30 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
       tc::mbar_init(wempty, 1);
       tc::mbar_init(dfull, 1);
       tc::mbar_init(afull, 8);
+      tc::mbar_init(ndone, nn > 0 ? nn : 1);
+      tc::mbar_init(hfull, nn > 0 ? 8 * nn : 1);
       tc::fence_mbar_init();
       tc::prefetch_tmap(&maps.x0);
     }
     __syncwarp();
-    tc::tmem_alloc(tmem_slot, 512);
+    tc::tmem_alloc(tmem_slot, TCOLS);
   }
   fence_proxy_async_smem();      // the zeroes are visible to TMA and the tensor cores
   tc::fence_before_sync();
-  __syncthreads();
+  if constexpr (S > 1)
+    tc::cluster_sync();          // every CTA's grids are zero and its barriers initialised
+  else
+    __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tmem_slot;
   int* err = a.err;
-  const int n_iter = a.B > (int)blockIdx.x ? (a.B - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int n_iter = a.B > cid ? (a.B - 1 - cid) / ncl + 1 : 0;
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------------- TMA producer
     bool ok = true;
     for (int it = 0; ok && it < n_iter; ++it) {
-      const int slot = (int)blockIdx.x + it * (int)gridDim.x;
+      const int slot = cid + it * ncl;
       // the input grid of this slot, once the previous slot's first layer has read the last one
       if (!tc::mbar_wait(xempty, (uint32_t)(it & 1) ^ 1u, err, 31)) break;
       const int nbox = ((T + 2) * W + SN_XBOX - 1) / SN_XBOX;
@@ -175,7 +227,13 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
           ok = false;
           break;
         }
+        // the neighbours' halo rows of this layer's inputs (phases count layers 0 .. D - 2)
+        if (S > 1 && l > 0 && !mbar_wait_acq_cluster(hfull, (uint32_t)((it * (D - 1) + l - 1) & 1), err, 37)) {
+          ok = false;
+          break;
+        }
         tc::fence_after_sync();
+        fence_proxy_async_smem();
         const int row_b = l == 0 ? SN_XROW : K::ARow;   // operand row bytes (input grid / branch grids)
         const int ksteps = K::ksteps(l);
         const int guard = l == 0 ? SN_GX : SN_G;
@@ -183,8 +241,9 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
         for (int b = 0; b < SN_NB; ++b) {
           const uint32_t asm_b = tc::smem_u32(smem + (l == 0 ? L.x_off : L.a_off[b]));
           const uint32_t wb = wsm + (uint32_t)(b * 9 * SN_C * row_b);
-          for (int mt = 0; mt < SN_TILES; ++mt) {
-            const uint32_t d = tbase + (uint32_t)(mt * SN_NB * SN_C + b * SN_C);
+          for (int ml = 0; ml < TPC; ++ml) {
+            const int mt = rank * TPC + ml;
+            const uint32_t d = tbase + (uint32_t)(ml * SN_NB * SN_C + b * SN_C);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
               const int shift = (tap / 3 - 1) * W + (tap % 3 - 1);
@@ -205,10 +264,25 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
   } else if (warp >= 2) {
     // ---------------------------------------------------------------- epilogue (8 warps)
     const int q = warp & 3;                         // TMEM lane quarter
-    const int half = (warp - 2) >> 2;               // tiles half, 2 * k + half
+    const int half = (warp - 2) >> 2;               // local tiles half, 2 * k + half
+    // (S > 1) this CTA's output rows, the rows its neighbours read, and their grids' addresses
+    const int row0 = p0 + rank * TPC * 128, row1 = row0 + TPC * 128;
+    uint32_t nbr_grid[2][SN_NB] = {};
+    uint32_t nbr_ndone[2] = {}, nbr_hfull[2] = {};
+    if constexpr (S > 1) {
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int nr = side == 0 ? rank - 1 : rank + 1;
+        if (nr < 0 || nr >= S) continue;
+#pragma unroll
+        for (int b = 0; b < SN_NB; ++b) nbr_grid[side][b] = tc::mapa(tc::smem_u32(smem + L.a_off[b]), (uint32_t)nr);
+        nbr_ndone[side] = tc::mapa(tc::smem_u32(ndone), (uint32_t)nr);
+        nbr_hfull[side] = tc::mapa(tc::smem_u32(hfull), (uint32_t)nr);
+      }
+    }
     bool ok = true;
     for (int it = 0; ok && it < n_iter; ++it) {
-      const int slot = (int)blockIdx.x + it * (int)gridDim.x;
+      const int slot = cid + it * ncl;
       for (int l = 0; l < D; ++l) {
         const int g = it * D + l;
         const bool got = tc::mbar_wait(dfull, (uint32_t)(g & 1), err, 36);
@@ -218,14 +292,29 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
         }
         tc::fence_after_sync();
         const bool last = l == D - 1;
-        for (int mt = half; mt < SN_TILES; mt += 2) {
+        const bool halo = S > 1 && !last;
+        if (halo) {
+          // this CTA's MMAs of the layer are complete: its neighbours may write into its grids;
+          // then wait until theirs are, before writing into theirs
+          if (warp == 2 && lane == 0) {
+            if (nbr_ndone[0]) mbar_arrive_release_cluster(nbr_ndone[0]);
+            if (nbr_ndone[1]) mbar_arrive_release_cluster(nbr_ndone[1]);
+          }
+          const bool nd = mbar_wait_acq_cluster(ndone, (uint32_t)((it * (D - 1) + l) & 1), err, 38);
+          if (!__all_sync(0xffffffffu, nd)) {
+            ok = false;
+            break;
+          }
+        }
+        for (int ml = half; ml < TPC; ml += 2) {
+          const int mt = rank * TPC + ml;
           const int P = p0 + mt * 128 + 32 * q + lane;
           const int t = P / W - 1, f = P % W - 1;
           const bool valid = t >= 0 && t < T && f >= 0 && f < F;
           float x[SN_NB][SN_C];
 #pragma unroll
           for (int b = 0; b < SN_NB; ++b) {
-            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * SN_NB * SN_C + b * SN_C);
+            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(ml * SN_NB * SN_C + b * SN_C);
             float v[16];
             tc::tmem_ld16(ta, v);
 #pragma unroll
@@ -281,7 +370,11 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
                       w4[e] = (lo & 0xFFFFu) | (hi << 16);
                     }
                   }
-                  *reinterpret_cast<uint4*>(row + 16 * (k ^ ((r >> 2) & 1))) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                  const int off = r * K::ARow + 16 * (k ^ ((r >> 2) & 1));
+                  const uint4 v4 = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                  *reinterpret_cast<uint4*>(row + 16 * (k ^ ((r >> 2) & 1))) = v4;
+                  if (halo && P - row0 <= W && nbr_grid[0][b]) st_cluster16(nbr_grid[0][b] + (uint32_t)off, v4);
+                  if (halo && row1 - 1 - P <= W && nbr_grid[1][b]) st_cluster16(nbr_grid[1][b] + (uint32_t)off, v4);
                 }
               } else {
 #pragma unroll
@@ -293,7 +386,11 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
                                                     : __floats2bfloat162_rn(0.f, 0.f);
                     w4[e] = *reinterpret_cast<const uint32_t*>(&h2);
                   }
-                  *reinterpret_cast<uint4*>(row + 16 * (k ^ ((r >> 1) & 3))) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                  const int off = r * K::ARow + 16 * (k ^ ((r >> 1) & 3));
+                  const uint4 v4 = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                  *reinterpret_cast<uint4*>(row + 16 * (k ^ ((r >> 1) & 3))) = v4;
+                  if (halo && P - row0 <= W && nbr_grid[0][b]) st_cluster16(nbr_grid[0][b] + (uint32_t)off, v4);
+                  if (halo && row1 - 1 - P <= W && nbr_grid[1][b]) st_cluster16(nbr_grid[1][b] + (uint32_t)off, v4);
                 }
               }
             }
@@ -310,18 +407,28 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
           }
         }
         fence_proxy_async_smem();   // the grids written here are read by the next layer's MMAs
+        if (halo) fence_proxy_async_cluster();   // ... and the neighbours' grids, by theirs
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(afull);
+        if (lane == 0) {
+          tc::mbar_arrive(afull);
+          if (halo) {
+            if (nbr_hfull[0]) mbar_arrive_release_cluster(nbr_hfull[0]);
+            if (nbr_hfull[1]) mbar_arrive_release_cluster(nbr_hfull[1]);
+          }
+        }
       }
     }
   }
   tc::fence_before_sync();
-  __syncthreads();
+  if constexpr (S > 1)
+    tc::cluster_sync();   // no CTA leaves while a neighbour may still write its grids or barriers
+  else
+    __syncthreads();
   if (warp == 0) {
     __syncwarp();
     tc::fence_after_sync();
-    tc::tmem_dealloc(tbase, 512);
+    tc::tmem_dealloc(tbase, TCOLS);
   }
 }
 
@@ -394,20 +501,80 @@ int launch_smallnet_pad(const void* x, void* xp, int slots, int T, int F, cudaSt
   return check_launch("smallnet_pad_kernel");
 }
 
+// Cluster size S for a call of B slots: the largest of 8, 4, 2 whose clusters of the kernel
+// can all be resident at once (one slot each), else 1 (one slot per CTA, persistent).  A
+// split needs a tile's halo, W + 1 rows, within the neighbouring CTA's tiles.
+template <int KIND, int S>
+int cluster_capacity(size_t smem) {
+  static int cap = -1;
+  static size_t cap_smem = 0;
+  if (cap < 0 || cap_smem != smem) {
+    auto* kern = smallnet_kernel<KIND, S>;
+    CONET_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, n_sm = 0, n_cl = 0;
+    CONET_CUDA(cudaGetDevice(&dev));
+    CONET_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    if (S == 1) {
+      n_cl = n_sm;
+    } else {
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = S;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(n_sm / S * S));
+      cfg.blockDim = dim3(SN_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      CONET_CUDA(cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg));
+    }
+    cap = n_cl;
+    cap_smem = smem;
+  }
+  return cap;
+}
+
+template <int KIND, int S>
+int launch_smallnet_s(const SnMaps& maps, const SmallNetArgs& a, size_t smem, int n_cl, cudaStream_t s) {
+  auto* kern = smallnet_kernel<KIND, S>;
+  const int ncl = a.B < n_cl ? a.B : n_cl;
+  if (S == 1) {
+    kern<<<ncl, SN_THREADS, smem, s>>>(maps, a);
+    return check_launch("smallnet_kernel");
+  }
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(S * ncl));
+  cfg.blockDim = dim3(SN_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CONET_CUDA(cudaLaunchKernelEx(&cfg, kern, maps, a));
+  return check_launch("smallnet_kernel (cluster)");
+}
+
 template <int KIND>
 int launch_smallnet_t(const SnMaps& maps, const SmallNetArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)sn_layout(a.T, a.F, SnK<KIND>::ARow).bytes + 1024;
-  static size_t attr = 0;
-  if (attr < smem) {
-    CONET_CUDA(cudaFuncSetAttribute(smallnet_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
+  const bool split_ok = a.F + 2 <= 128;   // W + 1 halo rows within one neighbouring tile
+  int cap = 0;
+  if (split_ok) {
+    if ((cap = cluster_capacity<KIND, 8>(smem)) < 0) return CONET_ERR_CUDA;
+    if (a.B <= cap) return launch_smallnet_s<KIND, 8>(maps, a, smem, cap, s);
+    if ((cap = cluster_capacity<KIND, 4>(smem)) < 0) return CONET_ERR_CUDA;
+    if (a.B <= cap) return launch_smallnet_s<KIND, 4>(maps, a, smem, cap, s);
+    if ((cap = cluster_capacity<KIND, 2>(smem)) < 0) return CONET_ERR_CUDA;
+    if (a.B <= cap) return launch_smallnet_s<KIND, 2>(maps, a, smem, cap, s);
   }
-  int dev = 0, n_sm = 0;
-  CONET_CUDA(cudaGetDevice(&dev));
-  CONET_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = a.B < n_sm ? a.B : n_sm;
-  smallnet_kernel<KIND><<<grid, SN_THREADS, smem, s>>>(maps, a);
-  return check_launch("smallnet_kernel");
+  if ((cap = cluster_capacity<KIND, 1>(smem)) < 0) return CONET_ERR_CUDA;
+  return launch_smallnet_s<KIND, 1>(maps, a, smem, cap, s);
 }
 
 int launch_smallnet(int kind, const CUtensorMap& x0_map, const CUtensorMap (*w_maps)[2], const SmallNetArgs& a,

@@ -1,6 +1,8 @@
 """CUDA-graph replay of the inference forward (conet_graphs): repeated identical calls replay
 a captured graph and must give exactly the eager forward's LLRs, follow weight reloads (the
-graph reads the weight buffers), and still count their kernel launches."""
+graph reads the weight buffers), and still count their kernel launches.  An E4M3 handle's
+first forward after new weights calibrates on the layer-by-layer path; later ones may run the
+whole-network kernel, so each call is compared with the eager call of the same position."""
 import numpy as np
 import pytest
 
@@ -31,12 +33,14 @@ def _setup(key, precision, B, **net_kw):
 
 
 def _eager(api, net, precision, params, Y, mask, B):
+    """The eager LLRs of a handle's first forward (E4M3: the calibrating one) and of a later one."""
     rx = api.Receiver(net, precision=precision, max_batch=B)
     rx.graphs(False)
     rx.load_weights(params)
-    out = rx.forward(Y, mask).clone()
+    first = rx.forward(Y, mask).clone()
+    later = rx.forward(Y, mask).clone()
     rx.sync()
-    return out.cpu().numpy()
+    return first.cpu().numpy(), later.cpu().numpy()
 
 
 CASES = [("plain_14x72_b16_fp32", "fp32", 16, {}),
@@ -61,7 +65,7 @@ def test_replay_matches_eager_and_follows_weights(key, precision, B, net_kw):
         rx.forward(Y, mask, llr=llr)
         rx.sync()
         counts.append(lib().conet_launch_count() - n0)
-        np.testing.assert_array_equal(llr.cpu().numpy(), want1, err_msg=f"call {call}")
+        np.testing.assert_array_equal(llr.cpu().numpy(), want1[min(call, 1)], err_msg=f"call {call}")
     # every call issues (or replays) the same kernels, the calibrating E4M3 call more
     assert counts[-1] > 0 and counts[-1] == counts[-2], counts
     rx.load_weights(p2)
@@ -69,12 +73,12 @@ def test_replay_matches_eager_and_follows_weights(key, precision, B, net_kw):
         llr.fill_(float("nan"))
         rx.forward(Y, mask, llr=llr)
         rx.sync()
-        np.testing.assert_array_equal(llr.cpu().numpy(), want2, err_msg=f"reload call {call}")
+        np.testing.assert_array_equal(llr.cpu().numpy(), want2[min(call, 1)], err_msg=f"reload call {call}")
 
 
 def test_new_output_buffer_runs_eagerly_then_replays():
     api, net, p1, _, Y, mask, llr = _setup("plain_14x72_b16_fp32", "bf16", 8)
-    want = _eager(api, net, "bf16", p1, Y, mask, 8)
+    want = _eager(api, net, "bf16", p1, Y, mask, 8)[1]
     rx = api.Receiver(net, precision="bf16", max_batch=8)
     rx.load_weights(p1)
     other = torch.empty_like(llr)

@@ -9,7 +9,9 @@ plain networks.  Against the layer-by-layer path of the same handle (the same BF
 another FP32 summation order) it must agree to 1e-5 (measured 4e-8 to 2e-7).
 Cases cover the full 14 x 72 grid at the benchmark batches, more slots than SMs, narrower
 grids (fewer than eight 128-row tiles of real rows), 1..8 layers, partial fusion and a
-LayerNorm after the fusion.
+LayerNorm after the fusion.  Calls of few slots split each slot over a cluster of 8, 4 or 2
+CTAs that exchange halo rows through distributed shared memory (1-24 slots: 8 or 4; 60: 4
+or 2, depending on how many clusters fit), larger calls run one slot per CTA (200, 300).
 
 E4M3: the first forward calibrates the activation scales on the layer-by-layer path; later
 forwards run the whole-network kernel with those scales.  Against the oracle's E4M3 emulation
@@ -31,7 +33,7 @@ def _gpu():
     need_gpu()
 
 
-CASES = [(dict(), 16), (dict(), 1), (dict(), 200), (dict(n_sc=40), 3), (dict(n_sc=17), 2), (dict(n_sym=7, pilot_syms=(1, 5), n_sc=40), 2),
+CASES = [(dict(), 16), (dict(), 1), (dict(), 200), (dict(), 24), (dict(), 60), (dict(n_sc=40), 3), (dict(n_sc=17), 2), (dict(n_sym=7, pilot_syms=(1, 5), n_sc=40), 2),
          (dict(depth=2), 4), (dict(depth=8), 2), (dict(fuse_mask=0b0101), 3), (dict(norm=1, depth=3), 2)]
 
 
