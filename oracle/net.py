@@ -3,7 +3,12 @@
 Architecture (Sec. III, Fig. "Example I", Fig. RB, Fig. MRB; readings O7-O13):
 
 * Branch 0 is the main net, branches 1..M the support nets; every branch sees the
-  whole input grid (Sec. III: the TTI is processed concurrently by all subnets).
+  whole input grid (Sec. III: the TTI is processed concurrently by all subnets), unless
+  ``support_inputs`` = 1: then the support nets are fed only the pilot information (Sec.
+  III's generalisation: subsets of the inputs, such as the pilot symbols, fed selectively
+  to supporting nets).  Their input layers read the pilot mask and the LS estimate at the
+  pilots but not the received signal: the weights on the Re / Im Y channels of every
+  antenna are held at zero (reading O15).
 * Input layer of every branch: 3x3 conv + bias + ReLU.
 * Plain networks: ``depth`` 3x3 conv + ReLU layers per branch (the input layer
   included).  Residual networks: input layer then ``depth`` blocks; support branches
@@ -314,7 +319,17 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
             return head1x1(tp, dwconv3x3(tp, x, ids[name + ".dw"]), ids[name + ".w"], ids[name + ".b"])
         return conv(x, ids[name + ".w"], ids[name + ".b"])
 
-    acts = [relu(tp, conv(x_in, ids[f"b{b}.in.w"], ids[f"b{b}.in.b"])) for b in range(nb)]
+    def input_w(b):
+        # selective support inputs: the support net's weights on the received-signal
+        # channels (the first 2 n_rx) are zero, and so is their gradient
+        w = ids[f"b{b}.in.w"]
+        if b == 0 or not getattr(cfg, "support_inputs", 0):
+            return w
+        M = np.ones(P[f"b{b}.in.w"].shape)
+        M[..., :2 * cfg.n_rx] = 0.0
+        return tp.op(tp[w] * M, (w,), lambda g: (g * M,))
+
+    acts = [relu(tp, conv(x_in, input_w(b), ids[f"b{b}.in.b"])) for b in range(nb)]
     x = fuse(0, acts)
     if not cfg.residual:
         for l in range(1, cfg.depth):

@@ -190,6 +190,8 @@ FD_CASES = [
     dict(feedback=1, n_branches=3),
     dict(feedback=1, fuse_op=1, residual=1, norm=1),
     dict(depthwise=1, residual=1, norm=1, width=4),
+    dict(support_inputs=1, n_branches=3),
+    dict(support_inputs=1, residual=1, norm=1),
 ]
 
 
@@ -291,3 +293,49 @@ def test_depthwise_block_is_the_separable_composition():
     assert onet.param_count(std) - onet.param_count(cfg) == n_convs * (per_conv_std - per_conv_dw)
     names = [n for n, _ in onet.param_layout(cfg)]
     assert "b0.k0.c1.dw" in names and "b1.k1.c2.w" in names
+
+
+def _support_in_w(cfg, flat, b):
+    """View of branch b's input-layer weights [C, 3, 3, c_in] in a flat parameter vector."""
+    o = 0
+    for name, shape in onet.param_layout(cfg):
+        n = int(np.prod(shape))
+        if name == f"b{b}.in.w":
+            return flat[o:o + n].reshape(shape)
+        o += n
+    raise KeyError(b)
+
+
+@pytest.mark.parametrize("kw", [dict(n_branches=3), dict(residual=1, norm=1, n_branches=3), dict(n_rx=2)])
+def test_selective_support_inputs_are_zeroed_signal_weights(kw):
+    """Support nets fed only the pilot information (Sec. III): the network equals the
+    full-input network whose support input layers have zero weights on the Re / Im Y
+    channels of every antenna; the main net keeps them; and the received signal then
+    reaches the LLRs only through the main net."""
+    cfg = tiny_net(support_inputs=1, **kw)
+    full = replace(cfg, support_inputs=0)
+    flat = onet.init_params(cfg, 21) + 0.1 * np.random.default_rng(22).standard_normal(onet.param_count(cfg))
+    X0, _, _ = _inputs(cfg, 23)
+    zeroed = flat.copy()
+    for b in range(1, cfg.n_branches):
+        _support_in_w(cfg, zeroed, b)[..., :2 * cfg.n_rx] = 0.0
+    np.testing.assert_array_equal(onet.forward(cfg, flat, X0), onet.forward(full, zeroed, X0))
+    assert not np.array_equal(onet.forward(cfg, flat, X0), onet.forward(full, flat, X0))
+    # the main net's signal weights matter: zeroing them too changes the output
+    main0 = zeroed.copy()
+    _support_in_w(cfg, main0, 0)[..., :2 * cfg.n_rx] = 0.0
+    assert not np.allclose(onet.forward(full, main0, X0), onet.forward(full, zeroed, X0))
+
+
+def test_selective_support_inputs_gradient_is_zero_on_withheld_channels():
+    cfg = tiny_net(support_inputs=1, n_branches=3)
+    flat = onet.init_params(cfg, 31) + 0.1 * np.random.default_rng(32).standard_normal(onet.param_count(cfg))
+    X0, bits, mask = _inputs(cfg, 33)
+    _, g, _ = onet.loss_and_grad(cfg, flat, X0, bits, mask)
+    for b in range(cfg.n_branches):
+        gw = _support_in_w(cfg, g, b)
+        if b == 0:
+            assert np.abs(gw[..., :2 * cfg.n_rx]).max() > 0
+        else:
+            assert np.all(gw[..., :2 * cfg.n_rx] == 0.0)
+            assert np.abs(gw[..., 2 * cfg.n_rx:]).max() > 0

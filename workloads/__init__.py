@@ -39,6 +39,8 @@ class NetConfig:
         net continues with its own activation plus the main net's (before the fusion).
     depthwise: 1 = the convs inside RB / MRB blocks are depthwise-separable: a per-channel
         3x3 conv followed by a 1x1 conv with bias (Sec. II-A, Sec. III).
+    support_inputs: 1 = the support nets are fed only the pilot information (pilot mask and
+        LS estimate at the pilots), not the received signal (Sec. III, selective inputs).
     """
     n_rx: int
     n_sc: int
@@ -53,6 +55,7 @@ class NetConfig:
     fuse_op: int = 0
     feedback: int = 0
     depthwise: int = 0
+    support_inputs: int = 0
     n_sym: int = 14
     pilot_syms: tuple = (2, 11)
     pilot_comb: int = 2
