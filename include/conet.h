@@ -98,6 +98,12 @@ typedef enum {
  *                      bias, then a 1x1 conv with bias.  Flat layout of such a conv: depthwise
  *                      W [C][3][3], then 1x1 W [C][C], bias [C] (in place of W, bias below).
  *                      FP32 inference handles only (else CONET_ERR_UNSUPPORTED).
+ *   support_inputs   : 1 = selective inputs (Sec. III): the support nets (branches 1..) are
+ *                      fed only the pilot information -- the pilot mask and the LS estimate
+ *                      at the pilots -- and not the received signal: their input layers'
+ *                      weights on the Re / Im Y channels (the first 2 n_rx of the flat
+ *                      layout's c_in) act as zero whatever the parameters hold, and their
+ *                      gradients are zero.  Needs n_branches >= 2 (else CONET_ERR_ARG).
  */
 typedef struct {
   int n_rx, n_sym, n_sc, qam_bits;
@@ -113,6 +119,7 @@ typedef struct {
   int fuse_op;                 /* 0 = product, 1 = sum at every fusion point */
   int feedback;                /* 1 = Example II: supports add the main net's activation */
   int depthwise;               /* 1 = depthwise-separable convs inside RB / MRB blocks */
+  int support_inputs;          /* 1 = support nets see only the pilot information */
 } conet_config;
 
 /*

@@ -31,6 +31,7 @@ def make_config(net, max_batch: int = 1, train: bool = False, recompute: bool = 
     c.fuse_op = int(getattr(net, "fuse_op", 0))
     c.feedback = int(getattr(net, "feedback", 0))
     c.depthwise = int(getattr(net, "depthwise", 0))
+    c.support_inputs = int(getattr(net, "support_inputs", 0))
     return c
 
 

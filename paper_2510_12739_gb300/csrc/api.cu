@@ -139,6 +139,9 @@ static int validate_config(const conet_config* c) {
   if (c->fuse_op < 0 || c->fuse_op > 1) return fail(CONET_ERR_ARG, "fuse_op %d not in {0, 1}", c->fuse_op);
   if (c->feedback < 0 || c->feedback > 1) return fail(CONET_ERR_ARG, "feedback %d not in {0, 1}", c->feedback);
   if (c->depthwise < 0 || c->depthwise > 1) return fail(CONET_ERR_ARG, "depthwise %d not in {0, 1}", c->depthwise);
+  if (c->support_inputs < 0 || c->support_inputs > 1)
+    return fail(CONET_ERR_ARG, "support_inputs %d not in {0, 1}", c->support_inputs);
+  if (c->support_inputs && c->n_branches < 2) return fail(CONET_ERR_ARG, "support_inputs needs a support net");
   return CONET_OK;
 }
 
@@ -489,6 +492,7 @@ uint64_t config_hash(const conet_config& c) {
                    c.residual, c.norm, c.fuse_mask, c.resnet_baseline, c.n_pilot_syms, c.pilot_comb,
                    c.fuse_op, c.feedback, c.depthwise};
   for (int v : f) mix(v);
+  if (c.support_inputs) mix(0x5e1ec7 + c.support_inputs);   // (absent from hashes of full-input networks)
   for (int i = 0; i < c.n_pilot_syms && i < 4; ++i) mix(c.pilot_syms[i]);
   mix((int64_t)c.pilot_seed);
   return h;

@@ -105,6 +105,7 @@ int net_setup(conet_s* h) {
     return fail(CONET_ERR_UNSUPPORTED, "depthwise-separable convs: FP32 inference of residual networks only");
   const size_t n = h->L.total;
   CONET_TRY(dev_alloc_t(h, &h->params, n));
+  if (h->cfg.support_inputs) CONET_TRY(dev_alloc_t(h, &h->params_eff, n));
   CONET_TRY(dev_alloc_t(h, &h->grads, n));
   CONET_TRY(dev_alloc_t(h, &h->adam_m, n));
   CONET_TRY(dev_alloc_t(h, &h->adam_v, n));
@@ -196,10 +197,27 @@ int net_setup(conet_s* h) {
   return CONET_OK;
 }
 
+// Selective support inputs (Sec. III): the support nets' input-layer weights on the
+// received-signal channels (the first 2 N of the input) held at zero in `w` (the master
+// parameters' effective copy, or their gradient).
+static int zero_withheld_inputs(const conet_s* h, float* w, cudaStream_t s) {
+  if (!h->cfg.support_inputs) return CONET_OK;
+  for (int b = 1; b < h->nb; ++b) CONET_TRY(launch_zero_input_channels(w + h->L.in_w[b], h->C, h->cin, 2 * h->N, s));
+  return CONET_OK;
+}
+
+// The parameters the kernels' weight layouts are made from.
+static const float* eff_params(const conet_s* h) { return h->cfg.support_inputs ? h->params_eff : h->params; }
+
 int net_weights_changed(conet_s* h, cudaStream_t s) {
+  if (h->cfg.support_inputs) {
+    CONET_CUDA(cudaMemcpyAsync(h->params_eff, h->params, h->L.total * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CONET_TRY(zero_withheld_inputs(h, h->params_eff, s));
+  }
+  const float* pe = eff_params(h);
   for (const auto& c : h->L.convs) {
     const int cin_dst = c.cin == h->cin ? h->c_pad : c.cin;
-    CONET_TRY(launch_weights_to_tap_major(h->params + c.off, c.cout, c.cin, cin_dst, h->wt + h->wt_off.at(c.off), s,
+    CONET_TRY(launch_weights_to_tap_major(pe + c.off, c.cout, c.cin, cin_dst, h->wt + h->wt_off.at(c.off), s,
                                           c.taps));
     if (h->cfg.train && c.cin != h->cin && c.taps == 9) {
       if (h->tc_dgrad)
@@ -611,17 +629,18 @@ int tc_setup(conet_s* h) {
 int tc_weights_changed(conet_s* h, cudaStream_t s) {
   const int kind = tc_kind(h);
   if (kind < 0) return CONET_OK;
+  const float* pe = eff_params(h);
   for (const auto& c : h->L.convs) {
     const int cin_dst = c.cin == h->cin ? tc_cin0(kind) : c.cin;
     const size_t wo = h->wb_off.at(c.off);
     if (kind == 1)
-      CONET_TRY(launch_weights_split(h->params + c.off, c.cout, c.cin, cin_dst, static_cast<float*>(h->wb) + wo,
+      CONET_TRY(launch_weights_split(pe + c.off, c.cout, c.cin, cin_dst, static_cast<float*>(h->wb) + wo,
                                      h->wb_lo + wo, s));
     else if (kind == 2)
-      CONET_TRY(launch_weights_fp8(h->params + c.off, c.cout, c.cin, cin_dst, static_cast<uint8_t*>(h->wb) + wo,
+      CONET_TRY(launch_weights_fp8(pe + c.off, c.cout, c.cin, cin_dst, static_cast<uint8_t*>(h->wb) + wo,
                                    h->fp8_wscale + h->fp8_ws_off.at(c.off), s));
     else
-      CONET_TRY(launch_weights_16(kind, h->params + c.off, c.cout, c.cin, cin_dst, static_cast<uint16_t*>(h->wb) + wo,
+      CONET_TRY(launch_weights_16(kind, pe + c.off, c.cout, c.cin, cin_dst, static_cast<uint16_t*>(h->wb) + wo,
                                   s));
   }
   h->fp8_calibrated = false;   // activation ranges change with the weights
@@ -1061,7 +1080,7 @@ int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
     }
     CONET_TRY(bw.wgrad(x, G1, true, w_off, b_off));
   }
-  return CONET_OK;
+  return zero_withheld_inputs(h, h->grads, s);   // their gradient is zero
 }
 
 int net_adam(conet_s* h, float lr, int step, cudaStream_t s) {

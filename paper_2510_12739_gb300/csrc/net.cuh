@@ -51,6 +51,7 @@ struct conet_s {
   conet::Layout L;
   int T = 0, F = 0, N = 0, Q = 0, C = 0, nb = 0, cin = 0, c_pad = 0;
   float* params = nullptr;
+  float* params_eff = nullptr;               // support_inputs: params with the withheld weights zero
   float* grads = nullptr;
   float* adam_m = nullptr;
   float* adam_v = nullptr;
