@@ -10,7 +10,7 @@ int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, cons
   // fused branch 0 no LayerNorm of its own
   if (a.fuse && (a.pre == 2 || (tc_groups(kind, nb, cout) > 1 && a.post[0] == 2)))
     return fail(CONET_ERR_UNSUPPORTED, "fused layer with a LayerNorm pre-activation or a normalised fused branch");
-  const int mode = tc_mode(kind, nb, a);
+  const int mode = tc_mode(kind, nb, cin, cout, a);
   switch (kind) {
     case 0: return launch_conv_tc_bf16(nb, cin, cout, mode, maps, a, s);
     case 1: return launch_conv_tc_tf32(nb, cin, cout, mode, maps, a, s);

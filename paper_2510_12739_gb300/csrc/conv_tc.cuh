@@ -212,7 +212,9 @@ struct Cfg {
   // which is dead while the boxes are in use.
   static constexpr bool STAGED = MODE != 0 && staged_ok(KIND, NB, CIN, COUT);
   static constexpr int PW = part_width(KIND, NB, COUT);
-  static constexpr size_t XS_B = MODE == 1 ? 0 : stg_xs_bytes(KIND, NB, COUT), NX_B = stg_nx_bytes(KIND, NB, COUT);
+  // (MODE 4 stores through no box: the region is its scratch only)
+  static constexpr size_t XS_B = (MODE == 1 || MODE == 4) ? 0 : stg_xs_bytes(KIND, NB, COUT),
+                          NX_B = MODE == 4 ? 0 : stg_nx_bytes(KIND, NB, COUT);
   static constexpr size_t REG_B =
       kb_ceil(XS_B + NX_B > SCR_WARP_FLOATS * sizeof(float) ? XS_B + NX_B : SCR_WARP_FLOATS * sizeof(float));
   static constexpr size_t SCR = STAGED ? 0 : scr_bytes(EP);
@@ -339,10 +341,12 @@ __device__ void stage_params(const TcConvArgs& a, float* par, int i0, int stride
 // supports and ReLU of the main branch, next input) and MODE 3 (input layer of a fused
 // residual network: MODE 2 with a ReLU pre-activation and no residual) fix them at compile
 // time, so their epilogues test no absent output and take no run-time branch on the layer
-// type.
+// type.  MODE 4 (the last conv2 of a fused residual network at inference: residual add,
+// fusion + LN and the 1x1 head; no stream or next input) runs only where the fast
+// epilogue (conv2_part) serves the shape (tc_mode).
 template <int MODE>
 struct Lay {
-  static constexpr bool FUSED = MODE == 2 || MODE == 3;
+  static constexpr bool FUSED = MODE == 2 || MODE == 3 || MODE == 4;
   __device__ static bool pre_relu(const TcConvArgs& a) { return MODE == 0 ? a.pre == 1 : MODE == 3; }
   __device__ static bool pre_ln(const TcConvArgs& a) { return MODE == 0 ? a.pre == 2 : MODE == 1; }
   __device__ static bool fuse(const TcConvArgs& a) { return MODE == 0 ? a.fuse != 0 : FUSED; }
@@ -350,12 +354,16 @@ struct Lay {
     return MODE == 0 ? (a.fuse != 0 && a.lnf_g != nullptr) : FUSED;
   }
   __device__ static int post(const TcConvArgs& a, int b) { return MODE == 0 ? a.post[b] : FUSED ? (b == 0 ? 1 : 2) : 0; }
-  __device__ static bool resid(const TcConvArgs& a, int b) { return MODE == 0 ? a.resid[b] != nullptr : MODE == 2; }
+  __device__ static bool resid(const TcConvArgs& a, int b) {
+    return MODE == 0 ? a.resid[b] != nullptr : (MODE == 2 || MODE == 4);
+  }
   __device__ static bool t_out(const TcConvArgs& a, int b) { return MODE == 0 && a.t_out[b] != nullptr; }
   __device__ static bool a_out(const TcConvArgs& a, int b) { return MODE == 0 && a.a_out[b] != nullptr; }
-  __device__ static bool xs_out(const TcConvArgs& a, int b) { return MODE == 0 ? a.xs_out[b] != nullptr : FUSED; }
-  __device__ static bool nx_out(const TcConvArgs& a, int b) { return MODE == 0 ? a.nx_out[b] != nullptr : true; }
-  __device__ static bool head(const TcConvArgs& a) { return MODE == 0 && a.head_w != nullptr; }
+  __device__ static bool xs_out(const TcConvArgs& a, int b) {
+    return MODE == 0 ? a.xs_out[b] != nullptr : (FUSED && MODE != 4);
+  }
+  __device__ static bool nx_out(const TcConvArgs& a, int b) { return MODE == 0 ? a.nx_out[b] != nullptr : MODE != 4; }
+  __device__ static bool head(const TcConvArgs& a) { return MODE == 0 ? a.head_w != nullptr : MODE == 4; }
   __device__ static bool measure(const TcConvArgs& a) { return MODE == 0 && a.measure != 0; }
   __device__ static bool amax(const TcConvArgs& a, int b) { return MODE == 0 && a.amax[b] != nullptr; }
 };
@@ -674,23 +682,29 @@ __device__ __forceinline__ void conv1_part(const float* par, uint32_t tacc, int 
   }
 }
 
-// Epilogue of the second conv of a fused residual block (MODE 2), for a warp whose part is
-// PC = 16 or 32 channels of G branches b0 .. b0 + G - 1 (a branch group: first / last say
-// which; or all branches: both).  Pass 1: v_b = acc_b (x dq_b, E4M3) + bias_b + resid_b,
-// written back to TMEM; the running Hadamard product of the v_b in the TMEM stash; the LN1
-// moments of the support branches and, in the last group, those of the product.  Pass 2,
-// one output at a time through the warp's boxes: each support's stream x_b = v_b and next
-// input relu(LN1_b(v_b)); in the last group branch 0's stream x_0 = LN_f(product) and next
-// input relu(x_0).  Pass 1 goes in 8-column steps whose residual rows and TMEM loads are
+// Epilogue of the fused fixed shapes (MODE 2: second conv of a residual block; MODE 3: the
+// input layer, a_b = relu(v_b) and no residual; MODE 4: the last block's second conv, with
+// the head instead of stream and next input), for a warp whose part is PC = 16 or 32
+// channels of G branches b0 .. b0 + G - 1 (a branch group: first / last say which; or all
+// branches: both).  Pass 1: v_b = acc_b (x dq_b, E4M3) + bias_b (+ resid_b), a_b = v_b
+// (MODE 3: relu(v_b)), written back to TMEM; the running Hadamard product of the a_b in the
+// TMEM stash; the LN1 moments of the support branches and, in the last group, those of the
+// product.  Pass 2, one output at a time through the warp's boxes: each support's stream
+// x_b = a_b and next input relu(LN1_b(a_b)); in the last group branch 0's stream x_0 =
+// LN_f(product) and next input relu(x_0).  MODE 4 writes nothing back and takes no support
+// moments; its pass 2 forms the head's partial sums of LN_f(product) over the part, and the
+// quarter's part 0 adds them up through the scratch into the LLRs.  Pass 1 goes in 8-column steps whose residual rows and TMEM loads are
 // all issued before the step's one wait (16-column steps spill at the 128-register budget
 // of a 14-warp CTA and measured 6 % slower); pass 2 reads 16 columns per wait; the
 // arithmetic runs on two-lane FP32 instructions.
-template <int KIND, int G, int COUT, int EP, int SCR_STRIDE, int PC>
+template <int KIND, int G, int COUT, int EP, int SCR_STRIDE, int PC, int MODE>
 __device__ __forceinline__ void conv2_part(const TcConvArgs& a, const float* par, uint32_t tacc, uint32_t tstash,
                                            int b0, bool first, bool last, bool valid, long long m, int part,
                                            int quarter, int lane, float* scr_all, const StoreBox& sb) {
   using PL = ParLayout<COUT>;
   static_assert(COUT == EP * PC && (PC == 16 || PC == 32), "equal parts of 16 or 32 channels");
+  static_assert(MODE == 2 || MODE == 3 || MODE == 4, "fused fixed shapes");
+  constexpr bool RESID = MODE != 3, PRE_RELU = MODE == 3, HEAD = MODE == 4;
   const int c0 = PC * part;
   // shifted moments: slot bb < G for support branch b0 + bb, slot G for the product
   float ks[G + 1];
@@ -706,7 +720,7 @@ __device__ __forceinline__ void conv2_part(const TcConvArgs& a, const float* par
     float r[G][CW];
 #pragma unroll
     for (int bb = 0; bb < G; ++bb) {
-      if (valid) {
+      if (RESID && valid) {
         ldg8(a.resid[b0 + bb] + m * COUT + ch, r[bb]);
       } else {
 #pragma unroll
@@ -736,11 +750,15 @@ __device__ __forceinline__ void conv2_part(const TcConvArgs& a, const float* par
         unsigned long long t = tc::f2pack(__uint_as_float(acc[bb][2 * e]), __uint_as_float(acc[bb][2 * e + 1]));
         if constexpr (KIND == 2) t = tc::f2mul(t, tc::f2pack(dq[2 * e], dq[2 * e + 1]));
         t = tc::f2add(t, tc::f2pack(bi[bb][2 * e], bi[bb][2 * e + 1]));
-        t = tc::f2add(t, tc::f2pack(r[bb][2 * e], r[bb][2 * e + 1]));
+        if constexpr (RESID) t = tc::f2add(t, tc::f2pack(r[bb][2 * e], r[bb][2 * e + 1]));
         tc::f2unpack(t, v[2 * e], v[2 * e + 1]);
+        if constexpr (PRE_RELU) {
+          v[2 * e] = fmaxf(v[2 * e], 0.f);
+          v[2 * e + 1] = fmaxf(v[2 * e + 1], 0.f);
+        }
       }
-      tc::tmem_st8_nowait(tacc + (uint32_t)(bb * COUT + ch), v);
-      if (b0 + bb != 0) {
+      if constexpr (!HEAD) tc::tmem_st8_nowait(tacc + (uint32_t)(bb * COUT + ch), v);
+      if (!HEAD && b0 + bb != 0) {
         if (j == 0) ks[bb] = v[0];
         const unsigned long long kk = tc::f2pack(ks[bb], ks[bb]);
 #pragma unroll
@@ -800,6 +818,61 @@ __device__ __forceinline__ void conv2_part(const TcConvArgs& a, const float* par
     rstd[i] = rsqrtf(M2 / (float)COUT + 1e-5f);
   }
   named_barrier(1 + quarter, 32 * EP);
+  if constexpr (HEAD) {
+    // the head on x_0 = LN_f(product): partial sums over the part, then part 0 adds the parts
+    if (!last) return;
+    float hq[HEAD_QMAX];
+#pragma unroll
+    for (int qq = 0; qq < HEAD_QMAX; ++qq) hq[qq] = 0.f;
+    const unsigned long long mu2 = tc::f2pack(mean[G], mean[G]), rs2 = tc::f2pack(rstd[G], rstd[G]);
+#pragma unroll
+    for (int h = 0; h < PC / 16; ++h) {
+      const int ch = c0 + 16 * h;
+      uint32_t xr[16];
+      __syncwarp();
+      tc::tmem_ld16_nowait(tstash + (uint32_t)ch, xr);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int cc = ch + CW * k;
+        float gm[CW], be[CW], x0[CW];
+        lds8(par + PL::LNFG + cc, gm);
+        lds8(par + PL::LNFB + cc, be);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c = CW * k + 2 * e;
+          unsigned long long t = tc::f2mul(
+              tc::f2sub(tc::f2pack(__uint_as_float(xr[c]), __uint_as_float(xr[c + 1])), mu2), rs2);
+          t = tc::f2fma(t, tc::f2pack(gm[2 * e], gm[2 * e + 1]), tc::f2pack(be[2 * e], be[2 * e + 1]));
+          tc::f2unpack(t, x0[2 * e], x0[2 * e + 1]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < HEAD_QMAX; ++qq) {
+          if (qq >= a.Q) break;
+          float hw[CW];
+          lds8(par + PL::HEADW + qq * COUT + cc, hw);
+          float sacc = 0.f;
+#pragma unroll
+          for (int c = 0; c < CW; ++c) sacc = fmaf(hw[c], x0[c], sacc);
+          hq[qq] += sacc;
+        }
+      }
+    }
+    __syncwarp();
+    for (int qq = 0; qq < a.Q && qq < HEAD_QMAX; ++qq) scr[qq * 32 + lane] = hq[qq];
+    named_barrier(5 + quarter, 32 * EP);
+    if (part == 0 && valid) {
+      for (int qq = 0; qq < a.Q && qq < HEAD_QMAX; ++qq) {
+        float sum = 0.f;
+#pragma unroll
+        for (int pp = 0; pp < EP; ++pp) sum += scr_all[(size_t)(4 * pp + ((quarter + 2) & 3)) * SCR_STRIDE + qq * 32 + lane];
+        const float v = sum + lds1(par + PL::HEADB + qq);
+        a.llr[m * a.Q + qq] = v;
+        if (!(fabsf(v) <= FLT_MAX)) *a.nonfinite = 1;
+      }
+    }
+    return;
+  }
   // pass 2: the supports of the group, then (last group) branch 0
 #pragma unroll
   for (int ob = 0; ob <= G; ++ob) {
@@ -862,9 +935,10 @@ __device__ __forceinline__ void tc_epilogue(const TcConvArgs& a, const float* pa
     conv1_part<KIND, NB, COUT, EP, SCR_STRIDE, PW>(par, tacc, 0, part, quarter, lane, scr_all, sb);
     return;
   }
-  if constexpr (MODE == 2 && (PW == 16 || PW == 32) && pow2_ceil(NB * COUT) >= NB * COUT + COUT) {
-    conv2_part<KIND, NB, COUT, EP, SCR_STRIDE, PW>(a, par, tacc, tacc + (uint32_t)(NB * COUT), 0, true, true, valid,
-                                                   m, part, quarter, lane, scr_all, sb);
+  if constexpr ((MODE == 2 || MODE == 3 || MODE == 4) && (PW == 16 || PW == 32) &&
+                pow2_ceil(NB * COUT) >= NB * COUT + COUT) {
+    conv2_part<KIND, NB, COUT, EP, SCR_STRIDE, PW, MODE>(a, par, tacc, tacc + (uint32_t)(NB * COUT), 0, true, true,
+                                                         valid, m, part, quarter, lane, scr_all, sb);
     return;
   }
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
@@ -1180,9 +1254,9 @@ __device__ __forceinline__ void tc_epilogue_group(const TcConvArgs& a, const flo
     conv1_part<KIND, G, COUT, EP, SCR_STRIDE, PW>(par, tacc, g * G, part, quarter, lane, scr_all, sb);
     return;
   }
-  if constexpr (MODE == 2 && (PW == 16 || PW == 32)) {
-    conv2_part<KIND, G, COUT, EP, SCR_STRIDE, PW>(a, par, tacc, tstash, g * G, g == 0, g == NB / G - 1, valid, m,
-                                                  part, quarter, lane, scr_all, sb);
+  if constexpr ((MODE == 2 || MODE == 3 || MODE == 4) && (PW == 16 || PW == 32)) {
+    conv2_part<KIND, G, COUT, EP, SCR_STRIDE, PW, MODE>(a, par, tacc, tstash, g * G, g == 0, g == NB / G - 1, valid,
+                                                        m, part, quarter, lane, scr_all, sb);
     return;
   }
   float* scr = scr_all + (size_t)(4 * part + ((quarter + 2) & 3)) * SCR_STRIDE;
@@ -1773,9 +1847,24 @@ int launch_tc_t(const TcMaps& maps, const TcConvArgs& a, cudaStream_t s) {
   return check_launch("conv_tc_kernel");
 }
 
+// Whether the fast fused epilogue (conv2_part) serves a shape: equal 16- or 32-channel parts,
+// staged stores, and room for the product (a branch-group stash, or spare accumulator columns).
+__host__ __device__ constexpr bool fast_fused(int kind, int nb, int cin, int cout) {
+  return staged_ok(kind, nb, cin, cout) &&
+         (part_width(kind, nb, cout) == 16 || part_width(kind, nb, cout) == 32) &&
+         (tc_groups(kind, nb, cout) > 1 || pow2_ceil(nb * cout) >= nb * cout + cout);
+}
+
 // The compile-time layer shape (Lay) that a launch's arguments match, 0 if none.
-int tc_mode(int kind, int nb, const TcConvArgs& a) {
-  if (a.measure || a.head_w || nb < 2 || a.op || a.feedback) return 0;
+int tc_mode(int kind, int nb, int cin, int cout, const TcConvArgs& a) {
+  if (a.measure || nb < 2 || a.op || a.feedback) return 0;
+  if (a.head_w) {
+    // the last conv2 of a fused residual network, at inference, where the fast epilogue runs
+    bool m4 = a.pre == 0 && a.fuse && a.lnf_g && a.llr && cin == cout && fast_fused(kind, nb, cin, cout);
+    for (int b = 0; b < nb; ++b)
+      m4 = m4 && a.resid[b] && !a.nx_out[b] && !a.t_out[b] && !a.a_out[b] && !a.amax[b];
+    return m4 ? 4 : 0;
+  }
   bool m1 = a.pre == 2 && !a.fuse, m2 = a.pre == 0 && a.fuse && a.lnf_g, m3 = a.pre == 1 && a.fuse && a.lnf_g;
   for (int b = 0; b < nb; ++b) {
     if (a.t_out[b] || a.a_out[b] || !a.nx_out[b] || a.amax[b]) return 0;
@@ -1802,6 +1891,7 @@ int tc_mode(int kind, int nb, const TcConvArgs& a) {
     constexpr bool BODY_ = CI == CO && NBV >= 2, INPUT_ = CI != CO && NBV >= 3;                                    \
     if (BODY_ && mode == 1) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, BODY_ ? 1 : 0>(maps, a, s);            \
     if (BODY_ && mode == 2) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, BODY_ ? 2 : 0>(maps, a, s);            \
+    if (BODY_ && mode == 4) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, BODY_ ? 4 : 0>(maps, a, s);            \
     if (INPUT_ && mode == 3) return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, INPUT_ ? 3 : 0>(maps, a, s);          \
     return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, 0>(maps, a, s);                                                \
   }

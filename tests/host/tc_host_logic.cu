@@ -68,9 +68,9 @@ int main() {
     a.ln2_g[b] = buf;
     a.ln2_b[b] = buf;
   }
-  CHECK(tc_mode(0, 3, a) == 1);
+  CHECK(tc_mode(0, 3, 64, 64, a) == 1);
   a.a_out[1] = buf;                          // an extra output: run-time epilogue
-  CHECK(tc_mode(0, 3, a) == 0);
+  CHECK(tc_mode(0, 3, 64, 64, a) == 0);
 
   // conv2 of a fused residual block
   TcConvArgs c = base_args(3);
@@ -87,34 +87,46 @@ int main() {
       c.ln1_b[b] = buf;
     }
   }
-  CHECK(tc_mode(0, 3, c) == 2);
+  CHECK(tc_mode(0, 3, 64, 64, c) == 2);
   TcConvArgs d = c;
-  d.head_w = buf;                            // the last block feeds the head
-  CHECK(tc_mode(0, 3, d) == 0);
+  d.head_w = buf;                            // the last block feeds the head, and still has outputs
+  CHECK(tc_mode(0, 3, 64, 64, d) == 0);
+  for (int b = 0; b < 3; ++b) d.nx_out[b] = nullptr;
+  d.llr = buf;                               // only the head: the fast head shape where it serves
+  CHECK(tc_mode(0, 3, 64, 64, d) == 4);
+  TcConvArgs d4 = d;
+  d4.resid[3] = buf;
+  d4.xs_out[3] = buf;
+  CHECK(tc_mode(0, 4, 96, 96, d4) == 4);     // branch groups: the stash holds the product
+  CHECK(tc_mode(0, 4, 64, 64, d4) == 0);     // no spare accumulator columns for the product
+  CHECK(tc_mode(2, 3, 64, 64, d) == 0);      // uneven E4M3 parts: run-time epilogue
+  CHECK(tc_mode(1, 3, 64, 64, d) == 0);      // split TF32: no staged epilogue
+  d.a_out[0] = buf;                          // training outputs: run-time epilogue
+  CHECK(tc_mode(0, 3, 64, 64, d) == 0);
   d = c;
   d.post[0] = 2;                             // a normalised main branch is not the fixed shape
-  CHECK(tc_mode(0, 3, d) == 0);
+  CHECK(tc_mode(0, 3, 64, 64, d) == 0);
   d = c;
   d.measure = 1;                             // E4M3 calibration passes stay run-time
-  CHECK(tc_mode(2, 3, d) == 0);
-  CHECK(tc_mode(2, 3, c) == 0);              // E4M3 needs its output scales
+  CHECK(tc_mode(2, 3, 64, 64, d) == 0);
+  CHECK(tc_mode(2, 3, 64, 64, c) == 0);              // E4M3 needs its output scales
   for (int b = 0; b < 3; ++b) d.qinv[b] = buf;
   d.measure = 0;
-  CHECK(tc_mode(2, 3, d) == 2);
-  CHECK(tc_mode(1, 3, c) == 0);              // split TF32 needs the low parts
+  CHECK(tc_mode(2, 3, 64, 64, d) == 2);
+  CHECK(tc_mode(1, 3, 64, 64, c) == 0);              // split TF32 needs the low parts
   for (int b = 0; b < 3; ++b) d.nx_lo[b] = buf;
-  CHECK(tc_mode(1, 3, d) == 2);
+  CHECK(tc_mode(1, 3, 64, 64, d) == 2);
 
   // input layer of a fused residual network: ReLU pre-activation, no residual
   TcConvArgs e = c;
   e.pre = 1;
   for (int b = 0; b < 3; ++b) e.resid[b] = nullptr;
-  CHECK(tc_mode(0, 3, e) == 3);
+  CHECK(tc_mode(0, 3, 16, 64, e) == 3);
   e.resid[2] = buf;                          // partly residual: neither shape
-  CHECK(tc_mode(0, 3, e) == 0);
+  CHECK(tc_mode(0, 3, 16, 64, e) == 0);
 
   // one branch never takes a fixed shape (no fusion)
-  CHECK(tc_mode(0, 1, a) == 0);
+  CHECK(tc_mode(0, 1, 64, 64, a) == 0);
 
   if (failures) return 1;
   std::printf("host logic ok\n");
