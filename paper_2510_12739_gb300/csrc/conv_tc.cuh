@@ -109,13 +109,17 @@ __host__ __device__ constexpr int tc_groups(int kind, int nb, int cout) {
 }
 
 // Epilogue warps per TMEM lane quarter (channel parts): 4 (18 warps, up to 96 registers
-// each), or 3 (14 warps, up to 128 registers) for the single-group E4M3 epilogues of three
-// or more branches, whose dequantisation state needs the larger budget, and for the
-// branch-group epilogues (measured: 4 parts 5 % faster than 3 with 16-bit operands on the
-// 14x624 network, 6 % slower with E4M3; on the 14x3276 branch-group network 3 parts are
-// 3.5 % faster now that its epilogues have fixed layer shapes).
+// each), or 3 (14 warps, up to 128 registers) for the branch-group epilogues and for the
+// single-group E4M3 epilogues of three or more branches whose Cout splits evenly in three
+// (measured: 4 parts 5 % faster than 3 with 16-bit operands on the 14x624 network; on the
+// 14x3276 branch-group network 3 parts are 3.5 % faster; on the 14x624 E4M3 network four
+// even parts of 16 channels, which the fast fixed-shape epilogues need, beat three uneven
+// ones by 26 %).
 __host__ __device__ constexpr int epi_parts(int kind, int nb, int cout) {
-  return (tc_groups(kind, nb, cout) == 1 && kind == 2 && nb >= 3) || tc_groups(kind, nb, cout) > 1 ? 3 : 4;
+  return (tc_groups(kind, nb, cout) == 1 && kind == 2 && nb >= 3 && (cout / 8) % 3 == 0) ||
+                 tc_groups(kind, nb, cout) > 1
+             ? 3
+             : 4;
 }
 
 // Staged output stores of the fixed layer shapes (MODE 1..3, below): each epilogue warp

@@ -99,7 +99,7 @@ int main() {
   d4.xs_out[3] = buf;
   CHECK(tc_mode(0, 4, 96, 96, d4) == 4);     // branch groups: the stash holds the product
   CHECK(tc_mode(0, 4, 64, 64, d4) == 0);     // no spare accumulator columns for the product
-  CHECK(tc_mode(2, 3, 64, 64, d) == 0);      // uneven E4M3 parts: run-time epilogue
+  CHECK(tc_mode(2, 3, 64, 64, d) == 4);      // E4M3: four even parts of 16 channels
   CHECK(tc_mode(1, 3, 64, 64, d) == 0);      // split TF32: no staged epilogue
   d.a_out[0] = buf;                          // training outputs: run-time epilogue
   CHECK(tc_mode(0, 3, 64, 64, d) == 0);
