@@ -89,7 +89,7 @@ __host__ __device__ inline SnLayout sn_layout(int T, int F, int a_row) {
   L.w_off = o;
   o += SN_NB * 9 * SN_C * a_row;
   L.bar_off = o;
-  o += 128;
+  o += 256;
   L.bytes = o;
   return L;
 }
@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
   uint64_t* ndone = bars + 6;    // (S > 1) the neighbours' MMAs of the layer are complete
   uint64_t* hfull = bars + 7;    // (S > 1) the neighbours' halo rows of the layer's outputs are written
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+  uint64_t* dfull_t = bars + 16; // (S = 1) tiles 0 .. t of the layer are complete (one per tile)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = a.T, F = a.F, W = F + 1, D = a.depth;
   const int p0 = W;              // first output row: P(0, -1)
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
       tc::mbar_init(wempty, 1);
       tc::mbar_init(dfull, 1);
       tc::mbar_init(afull, 8);
+      for (int i = 0; i < TPC; ++i) tc::mbar_init(&dfull_t[i], 1);
       tc::mbar_init(ndone, nn > 0 ? nn : 1);
       tc::mbar_init(hfull, nn > 0 ? 8 * nn : 1);
       tc::fence_mbar_init();
@@ -238,11 +240,13 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
         const int ksteps = K::ksteps(l);
         const int guard = l == 0 ? SN_GX : SN_G;
         const uint32_t wsm = tc::smem_u32(smem + L.w_off);
-        for (int b = 0; b < SN_NB; ++b) {
-          const uint32_t asm_b = tc::smem_u32(smem + (l == 0 ? L.x_off : L.a_off[b]));
-          const uint32_t wb = wsm + (uint32_t)(b * 9 * SN_C * row_b);
-          for (int ml = 0; ml < TPC; ++ml) {
-            const int mt = rank * TPC + ml;
+        // tile by tile (one slot per CTA: each tile's completion is signalled, so the epilogue
+        // of a tile overlaps the next tiles' MMAs)
+        for (int ml = 0; ml < TPC; ++ml) {
+          const int mt = rank * TPC + ml;
+          for (int b = 0; b < SN_NB; ++b) {
+            const uint32_t asm_b = tc::smem_u32(smem + (l == 0 ? L.x_off : L.a_off[b]));
+            const uint32_t wb = wsm + (uint32_t)(b * 9 * SN_C * row_b);
             const uint32_t d = tbase + (uint32_t)(ml * SN_NB * SN_C + b * SN_C);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
               }
             }
           }
+          if (S == 1) tc::mma_commit(&dfull_t[ml]);
         }
         tc::mma_commit(dfull);
         tc::mma_commit(wempty);
@@ -285,12 +290,14 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
       const int slot = cid + it * ncl;
       for (int l = 0; l < D; ++l) {
         const int g = it * D + l;
-        const bool got = tc::mbar_wait(dfull, (uint32_t)(g & 1), err, 36);
-        if (!__all_sync(0xffffffffu, got)) {
-          ok = false;
-          break;
+        if (S > 1) {   // (one slot per CTA: per-tile waits below)
+          const bool got = tc::mbar_wait(dfull, (uint32_t)(g & 1), err, 36);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
         }
-        tc::fence_after_sync();
         const bool last = l == D - 1;
         const bool halo = S > 1 && !last;
         if (halo) {
@@ -311,25 +318,52 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
           const int P = p0 + mt * 128 + 32 * q + lane;
           const int t = P / W - 1, f = P % W - 1;
           const bool valid = t >= 0 && t < T && f >= 0 && f < F;
+          if (S == 1) {   // this tile's accumulators are complete
+            const bool got = tc::mbar_wait(&dfull_t[ml], (uint32_t)(g & 1), err, 36);
+            if (!__all_sync(0xffffffffu, got)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+          }
           float x[SN_NB][SN_C];
+          {
+            uint32_t r[SN_NB][2][16];
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < SN_NB; ++b)
+#pragma unroll
+              for (int h = 0; h < 2; ++h)
+                tc::tmem_ld16_nowait(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(ml * SN_NB * SN_C + b * SN_C + 16 * h),
+                                     r[b][h]);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int b = 0; b < SN_NB; ++b)
+#pragma unroll
+              for (int c = 0; c < SN_C; ++c) x[b][c] = __uint_as_float(r[b][c >> 4][c & 15]);
+          }
 #pragma unroll
           for (int b = 0; b < SN_NB; ++b) {
-            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(ml * SN_NB * SN_C + b * SN_C);
-            float v[16];
-            tc::tmem_ld16(ta, v);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) x[b][c] = v[c];
-            tc::tmem_ld16(ta + 16, v);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) x[b][16 + c] = v[c];
-            const float* bias = a.bias[l][b];
+            const float4* bias4 = reinterpret_cast<const float4*>(a.bias[l][b]);
             if constexpr (KIND == 2) {
-              const float* dq = a.dq[l][b];
+              const float4* dq4 = reinterpret_cast<const float4*>(a.dq[l][b]);
 #pragma unroll
-              for (int c = 0; c < SN_C; ++c) x[b][c] *= __ldg(dq + c);                      // dequantise
+              for (int c = 0; c < SN_C; c += 4) {                                             // dequantise
+                const float4 d = __ldg(dq4 + c / 4);
+                x[b][c] *= d.x;
+                x[b][c + 1] *= d.y;
+                x[b][c + 2] *= d.z;
+                x[b][c + 3] *= d.w;
+              }
             }
 #pragma unroll
-            for (int c = 0; c < SN_C; ++c) x[b][c] = fmaxf(x[b][c] + __ldg(bias + c), 0.f);   // a_b = ReLU(conv + bias)
+            for (int c = 0; c < SN_C; c += 4) {                                               // a_b = ReLU(conv + bias)
+              const float4 bv = __ldg(bias4 + c / 4);
+              x[b][c] = fmaxf(x[b][c] + bv.x, 0.f);
+              x[b][c + 1] = fmaxf(x[b][c + 1] + bv.y, 0.f);
+              x[b][c + 2] = fmaxf(x[b][c + 2] + bv.z, 0.f);
+              x[b][c + 3] = fmaxf(x[b][c + 3] + bv.w, 0.f);
+            }
           }
           if (a.fuse[l]) {
 #pragma unroll
@@ -346,6 +380,15 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
 #pragma unroll
               for (int c = 0; c < SN_C; ++c)
                 x[0][c] = (x[0][c] - mean) * rs * __ldg(a.lnf_g[l] + c) + __ldg(a.lnf_b[l] + c);
+            }
+          }
+          if (S == 1 && !last && ml + 1 < TPC) {
+            // the next tile's MMAs read this tile's last W + 1 rows: they finish before the
+            // rows are overwritten (the previous tile's finished before this tile's)
+            const bool got = tc::mbar_wait(&dfull_t[ml + 1], (uint32_t)(g & 1), err, 39);
+            if (!__all_sync(0xffffffffu, got)) {
+              ok = false;
+              break;
             }
           }
           if (!last) {
@@ -406,6 +449,7 @@ __global__ void __launch_bounds__(SN_THREADS, 1) smallnet_kernel(const __grid_co
             }
           }
         }
+        if (!ok) break;
         fence_proxy_async_smem();   // the grids written here are read by the next layer's MMAs
         if (halo) fence_proxy_async_cluster();   // ... and the neighbours' grids, by theirs
         tc::fence_before_sync();
