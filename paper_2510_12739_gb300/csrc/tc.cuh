@@ -295,13 +295,15 @@ __device__ __forceinline__ void mma_pair(uint32_t d, uint64_t a, uint64_t b, uin
 }
 
 // Once every MMA this thread issued so far has completed, arrive once on the mbarrier at
-// bar's shared::cta offset in each CTA of the pair (an mbarrier signal: no data moves).
+// bar's shared::cta offset in each CTA of the pair (an mbarrier signal: no data moves): two
+// single-target commits, one to this CTA's barrier and one, through its shared::cluster
+// address, to the peer's.
 __device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"((uint16_t)3)
-      : "memory");
+  uint32_t peer;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, 1;" : "=r"(peer) : "r"(smem_u32(bar)));
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(peer) : "memory");
 }
 
 // Arrive on `bar` once every previously issued MMA of this thread has completed.
