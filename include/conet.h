@@ -386,6 +386,17 @@ int conet_loss_ber(const float* llr, const uint8_t* bits, const uint8_t* pilot_m
                    int F, int Q, float grad_scale, float* dllr, double* loss_sum,
                    unsigned long long* err_bits, unsigned long long* n_bits, void* stream);
 
+/*
+ * Bit-error counting alone (the BER of Sec. IV's figures): over the data REs of llr (dev
+ * float [B][T][F][Q], pilot REs where pilot_mask [T][F] is 1 are skipped) the hard
+ * decisions [LLR > 0] are compared with bits (dev u8 [B][T][F][Q]); err_bits += the
+ * errors, n_bits += the bits compared (caller-owned device u64 counters, zero them first;
+ * either may be NULL).  The same kernel and counts as conet_loss_ber with no loss or
+ * gradient.  CONET_ERR_ARG / CONET_ERR_SHAPE on the host for NULL inputs or bad sizes.
+ */
+int conet_ber_count(const float* llr, const uint8_t* bits, const uint8_t* pilot_mask, int B, int T, int F,
+                    int Q, unsigned long long* err_bits, unsigned long long* n_bits, void* stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /*

@@ -67,6 +67,7 @@ SIGNATURES = {
     "conet_assemble_input": (I, [CFG, P, P, P, I, P, P]),
     "conet_ls_lmmse": (I, [CFG, P, P, P, P, P, P, I, I, P, P]),
     "conet_loss_ber": (I, [P, P, P, I, I, I, I, F32, P, P, P, P, P]),
+    "conet_ber_count": (I, [P, P, P, I, I, I, I, P, P, P]),
     "conet_profile_enable": (I, [P, I]),
     "conet_profile_read": (I, [P, I, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "conet_launch_count": (C.c_ulonglong, []),

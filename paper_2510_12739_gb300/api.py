@@ -286,6 +286,15 @@ def loss_ber(llr, bits, pilot_mask, grad_scale: float = 0.0, want_grad=False, st
     return loss, cnt, dllr
 
 
+def ber_count(llr, bits, pilot_mask, stream=None) -> torch.Tensor:
+    """Hard-decision bit errors and bits counted over the data REs: int64 [2] on the device."""
+    B, T, F, Q = llr.shape
+    cnt = torch.zeros(2, dtype=torch.int64, device=llr.device)
+    check(lib().conet_ber_count(_ptr(llr), _ptr(bits), _ptr(pilot_mask), B, T, F, Q, C.c_void_p(cnt.data_ptr()),
+                                C.c_void_p(cnt.data_ptr() + 8), _stream(stream)))
+    return cnt
+
+
 def conv3x3_wgrad(x, dz, want_bias=True, stream=None):
     """(dW [Cout][3][3][Cin], db [Cout]) of one 3x3 'same' conv: x [B,T,F,Cin], dz [B,T,F,Cout]."""
     B, T, F, cin = x.shape

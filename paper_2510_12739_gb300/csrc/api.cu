@@ -457,6 +457,11 @@ int conet_loss_ber(const float* llr, const uint8_t* bits, const uint8_t* pilot_m
                          (cudaStream_t)stream);
 }
 
+int conet_ber_count(const float* llr, const uint8_t* bits, const uint8_t* pilot_mask, int B, int T, int F, int Q,
+                    unsigned long long* err_bits, unsigned long long* n_bits, void* stream) {
+  return conet_loss_ber(llr, bits, pilot_mask, B, T, F, Q, 0.f, nullptr, nullptr, err_bits, n_bits, stream);
+}
+
 // ------------------------------------------------------------------ checkpoints
 // Version-1 layout: a 64-byte header, then the FP32 master parameters, Adam's first and
 // second moments (n floats each, the flat parameter layout).

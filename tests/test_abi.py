@@ -82,6 +82,7 @@ def test_host_side_argument_errors(lib):
     assert lib.conet_forward(None, None, None, None, 1, None, None) == -1
     assert lib.conet_backward(None, None, 1, None) == -1
     assert lib.conet_loss_ber(None, None, None, 1, 14, 72, 4, 0.0, None, None, None, None, None) == -1
+    assert lib.conet_ber_count(None, None, None, 1, 14, 72, 4, None, None, None) == -1
     cfg = api.make_config(base)
     assert lib.conet_sim_generate(C.byref(cfg), None, 0, 0, 1, 0.0, None, None, None, None, None, None) == -1
 

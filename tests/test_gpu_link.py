@@ -136,3 +136,6 @@ def test_loss_and_bit_errors_match_oracle():
     l_ref, d_ref = onet.bce_loss(llr.astype(np.float64), bits, mask)
     assert abs(loss.item() / n_ref - l_ref) < 1e-6 * l_ref
     assert normwise(dllr.cpu().numpy(), d_ref * n_ref * 0.25) < 1e-6
+    # the counting-only entry point: the same counts, bit-exact
+    cnt2 = api.ber_count(dev(llr), dev(bits), dev(mask))
+    assert int(cnt2[0]) == e_ref and int(cnt2[1]) == n_ref
