@@ -16,7 +16,7 @@ tests therefore compare against the oracle's emulation of the same 16-bit receiv
 (oracle.half: the same operands rounded, FP64 elsewhere), element-wise maximum, with bars
 from the worst measured He-init case with a margin (BF16 6.2e-2 -> 0.1, FP16 1.7e-2 ->
 3e-2, both on single slots of the full 256-slot 14 x 624 batch); the FP64 bars of the
-the benchmark spec (2e-2) are asserted on trained weights, where the fused products are well
+precision target (2e-2) are asserted on trained weights, where the fused products are well
 conditioned, in test_gpu_trained_parity.py (measured there: BF16 1.1e-2, FP16 1.8e-3 against
 FP64; BF16 4.5e-3, FP16 8.9e-4 against the emulation)."""
 import numpy as np

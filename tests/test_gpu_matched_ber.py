@@ -51,7 +51,7 @@ def _ber(row, k):
 def test_16bit_ber_within_2_percent_of_fp32(tables, grid, prec):
     for snr, row in tables[grid].items():
         if row["fp32"][0] < MIN_ERRORS:
-            continue                              # insufficient errors: reported, not judged
+            continue                              # insufficient errors: reported, not asserted
         gap = abs(_ber(row, prec) - _ber(row, "fp32")) / _ber(row, "fp32")
         assert gap <= 0.02, (grid, snr, prec, gap)
 

@@ -1,5 +1,5 @@
 """Statistical pins of the oracle's LMMSE equaliser and exact demapper (the LS-LMMSE
-receiver of Sec. I and Sec. IV, the BER judge of every trained-network test).
+receiver of Sec. I and Sec. IV, the BER reference of every trained-network test).
 
 With the channel known, y = h x + n per antenna, n ~ CN(0, s2 I), the SIMO LMMSE output is
 x_hat = h^H y / (|h|^2 + s2) = mu x + e with mu = |h|^2 / (|h|^2 + s2) and e a circular
