@@ -90,9 +90,9 @@ typedef enum {
  *   feedback         : 1 = Example II (Sec. III, Fig. "conet2"): at every fusion point each
  *                      support net continues with its own activation plus the main net's
  *                      (taken before the fusion).
- *   fuse_op = 1 and feedback = 1 are inference-only (train = 1 returns
- *   CONET_ERR_UNSUPPORTED), and on the tensor-core paths need a network whose accumulators
- *   fit TMEM twice (not the 4 x 96 network).
+ *   fuse_op = 1 and feedback = 1 train only on FP32 handles of plain networks (train = 1
+ *   otherwise returns CONET_ERR_UNSUPPORTED), and on the tensor-core paths (inference) need
+ *   a network whose accumulators fit TMEM twice (not the 4 x 96 network).
  *   depthwise        : residual networks: 1 = every conv inside an RB / MRB is depthwise-
  *                      separable (Sec. II-A, Sec. III): a per-channel 3x3 'same' conv without
  *                      bias, then a 1x1 conv with bias.  Flat layout of such a conv: depthwise

@@ -122,11 +122,37 @@ __global__ void __launch_bounds__(EW_THREADS) fuse_bwd_kernel(FuseBwdArgs a) {
         for (int j = 0; j < CPL; ++j) gu[b][j] = 0.f;
     }
     if (a.fuse) {
+      // Example II's feedback: a support's stored activation is its next input a_b + a_0,
+      // which fed the next layer; the fusion and the ReLU masks read a_b, and a_0 also
+      // receives every support's input gradient
+      float gfb[CPL];
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) gfb[j] = 0.f;
+      if (a.feedback) {
+#pragma unroll
+        for (int b = 1; b < MAX_BR; ++b) {
+          if (b >= a.n_br) continue;
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            u[b][j] -= u[0][j];
+            gfb[j] += gu[b][j];
+          }
+        }
+      }
       float gp[CPL];
       if (a.ln_g) {
         float p[CPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) p[j] = u[0][j] * u[1][j] * u[2][j] * u[3][j];
+        for (int j = 0; j < CPL; ++j) {
+          if (a.op == 1) {
+            p[j] = 0.f;
+#pragma unroll
+            for (int b = 0; b < MAX_BR; ++b)
+              if (b < a.n_br) p[j] += u[b][j];
+          } else {
+            p[j] = u[0][j] * u[1][j] * u[2][j] * u[3][j];
+          }
+        }
         ln_backward(p, gx0, a.ln_g, C, lane, gp, pv[0], pv[1]);
       } else {
 #pragma unroll
@@ -138,10 +164,12 @@ __global__ void __launch_bounds__(EW_THREADS) fuse_bwd_kernel(FuseBwdArgs a) {
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
           float o = gp[j];
+          if (a.op != 1) {
 #pragma unroll
-          for (int i = 0; i < MAX_BR; ++i)
-            if (i != b) o *= u[i][j];
-          gu[b][j] = (b == 0 ? 0.f : gu[b][j]) + o;
+            for (int i = 0; i < MAX_BR; ++i)
+              if (i != b) o *= u[i][j];
+          }
+          gu[b][j] = (b == 0 ? gfb[j] : gu[b][j]) + o;
         }
       }
     } else {

@@ -134,6 +134,8 @@ struct FuseBwdArgs {
   const float* ln_g;          // post-fusion LN gain or NULL
   float* part;                // [grid][2][C] dgamma / dbeta partials (when ln_g)
   int n_br, fuse, relu_mask, C;
+  int op;                     // interaction: 0 = product, 1 = sum
+  int feedback;               // Example II: the supports' u hold a_b + a_0 (their next input)
   long long M;
 };
 int launch_fuse_bwd(const FuseBwdArgs& a, cudaStream_t s);

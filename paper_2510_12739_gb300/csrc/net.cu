@@ -99,8 +99,8 @@ int tc_weights_changed(conet_s* h, cudaStream_t s);
 int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
 
 int net_setup(conet_s* h) {
-  if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train)
-    return fail(CONET_ERR_UNSUPPORTED, "sum interaction and Example II feedback are inference-only");
+  if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train && (h->prec != CONET_FP32 || h->cfg.residual))
+    return fail(CONET_ERR_UNSUPPORTED, "sum interaction and Example II feedback train on FP32 plain networks only");
   if (h->cfg.depthwise && (h->cfg.train || h->prec != CONET_FP32 || !h->cfg.residual))
     return fail(CONET_ERR_UNSUPPORTED, "depthwise-separable convs: FP32 inference of residual networks only");
   const size_t n = h->L.total;
@@ -967,6 +967,8 @@ struct Bwd {
     f.n_br = h->nb;
     f.fuse = fused_at(h->cfg, point);
     f.relu_mask = relu_mask;
+    f.op = h->cfg.fuse_op;
+    f.feedback = h->cfg.feedback;
     f.C = h->C;
     f.M = M;
     CONET_TRY(launch_fuse_bwd(f, s));

@@ -1,7 +1,7 @@
 """GPU parity of the other interaction operations of Sec. III (f2): the element-wise sum at
 the fusion points (fuse_op = 1) and Example II's feedback (Fig. "conet2": every support net
 continues with its own activation plus the main net's), on the FP32 fusion stage and the
-tensor-core run-time epilogue, against the oracle (FP64, and its 16-bit / E4M3 emulations
+tensor-core run-time epilogue, and their backward on FP32 plain networks, against the oracle (FP64, and its 16-bit / E4M3 emulations
 for the reduced-precision paths).  Bars as in the product-fusion tests: FP32 1e-4 normwise
 against FP64; 16-bit 1e-3 against the emulation on plain networks and the He-init
 LayerNorm bars on residual ones; E4M3 1e-2 against its emulation on plain networks."""
@@ -72,9 +72,48 @@ def test_unsupported_combinations_are_refused():
     with pytest.raises(ConetError) as e:                  # branch-group network on the tensor cores
         api.Receiver(replace(w.net, n_sc=29, feedback=1), "bf16", max_batch=1)
     assert e.value.code == -8
-    with pytest.raises(ConetError) as e:                  # training with the sum interaction
-        api.Receiver(replace(WORKLOADS["plain_14x72_b16_fp32"].net, fuse_op=1), "fp32", max_batch=1, train=True)
+    with pytest.raises(ConetError) as e:                  # training with the sum interaction: FP32 only
+        api.Receiver(replace(WORKLOADS["plain_14x72_b16_fp32"].net, fuse_op=1), "bf16", max_batch=1, train=True)
     assert e.value.code == -8
+    with pytest.raises(ConetError) as e:                  # ... and plain networks only
+        api.Receiver(replace(WORKLOADS["resid_14x624_b256_fp32"].net, n_sc=37, feedback=1), "fp32", max_batch=1,
+                     train=True)
+    assert e.value.code == -8
+
+
+@pytest.mark.parametrize("kw", VARIANTS + [dict(fuse_op=1, norm=1), dict(feedback=1, norm=1, fuse_mask=0b0101)])
+def test_training_gradients_fp32(kw):
+    """Backward of the sum interaction and of Example II's feedback (FP32 plain networks): the
+    GPU gradient against the FP64 oracle's, per parameter tensor, within the product-fusion
+    bar (2e-4 normwise)."""
+    from oracle import net as onet, rx as orx
+    from paper_2510_12739_gb300 import api
+    from workloads import random_grid
+    w = WORKLOADS["train_14x72_b128_bf16"]
+    net = replace(w.net, n_sc=24, n_branches=3, depth=3, width=16, **kw)
+    B = 3
+    ref = oracle_inputs(net, w.sim, 3, 0, B)
+    params = onet.init_params(net, 4)
+    params = (params + 0.05 * np.random.default_rng(4).standard_normal(params.size)).astype(np.float32)
+    rx = api.Receiver(net, precision="fp32", max_batch=B, train=True)
+    rx.load_weights(params)
+    llr = rx.forward(dev(ref["Y32"]), dev(ref["pilot_mask"]))
+    dllr = random_grid(13, llr.shape, scale=1e-3)
+    rx.backward(dev(dllr))
+    g = rx.grads_device().cpu().numpy()
+    Yd = ref["Y32"][..., 0].astype(np.float64) + 1j * ref["Y32"][..., 1]
+    X0 = orx.assemble_input(Yd, ref["pilot_sym"], ref["pilot_mask"])
+    L_ref, tape = onet.forward(net, params.astype(np.float64), X0, keep_tape=True)
+    g_ref, _ = onet.backward(net, tape, dllr.astype(np.float64))
+    assert normwise(llr.cpu().numpy(), L_ref) < 1e-4
+    o, worst = 0, (0.0, None)
+    for name, shape in onet.param_layout(net):
+        n = int(np.prod(shape))
+        e = normwise(g[o:o + n], g_ref[o:o + n])
+        worst = max(worst, (e, name))
+        o += n
+    print(f"training {kw}: worst gradient tensor {worst}")
+    assert worst[0] < 2e-4, worst
 
 
 @pytest.mark.parametrize("key,kw", [("resid_14x624_b256_fp32", dict(n_sc=37, depth=2)),
