@@ -97,7 +97,8 @@ struct DwArgs {
 int launch_dwconv3x3(const DwArgs& a, int n_br, cudaStream_t s);
 
 // ---------------------------------------------------------------- fusion / LN / head
-// Per RE (one warp): x0 = fuse ? LN?(prod_b u_b) : u_0 (written to x0_out);
+// Per RE (fuse_quad / fuse_row in csrc/fuse.cu):
+// x0 = fuse ? LN?(prod_b u_b or sum_b u_b) : u_0 (written to x0_out);
 // h_b = relu(LN1_b(x_b)) or relu(x_b) (written to h_out[b] when set);
 // llr = head_w x0 + head_b when head_w is set.
 struct FuseArgs {

@@ -74,6 +74,40 @@ def test_resnet_112():
     check_fp32(L, L_ref)
 
 
+@pytest.mark.parametrize("width,nb,kw", [(16, 3, dict()), (32, 2, dict()), (88, 2, dict()),
+                                         (88, 1, dict(resnet_baseline=1))])
+def test_residual_every_conv_width(width, nb, kw):
+    """Residual LayerNorm networks at the other widths the FP32 conv is built for, so that
+    every instantiation's LayerNorm rows and its stage between layers run: at 88 channels a
+    CTA has 176 threads, five full warps and a half one (the width of the matched ResNet of
+    the interference study)."""
+    w = WORKLOADS["resid_14x624_b256_fp32"]
+    net = replace(w.net, n_sc=37, depth=2, width=width, n_branches=nb, **kw)
+    L, L_ref, _ = run_pair(net, w.sim, 2, perturb=0.02)
+    check_fp32(L, L_ref)
+
+
+def test_repeated_and_smaller_batches_agree_bitwise():
+    """Repeated calls agree bitwise, and a smaller batch afterwards gives the first slot's
+    LLRs of the larger one bitwise: every RE's arithmetic is independent of the tiling and of
+    the launch's other slots."""
+    from oracle import net as onet
+    from paper_2510_12739_gb300 import api
+    w = WORKLOADS["resid_14x624_b256_fp32"]
+    net = replace(w.net, n_sc=37, depth=2)
+    ref = oracle_inputs(net, w.sim, 5, 0, 3)
+    rx = api.Receiver(net, precision="fp32", max_batch=3)
+    rx.load_weights(onet.init_params(net, 3).astype(np.float32))
+    Y, M = dev(ref["Y32"]), dev(ref["pilot_mask"])
+    L1 = rx.forward(Y, M).cpu().numpy()
+    L2 = rx.forward(Y, M).cpu().numpy()
+    np.testing.assert_array_equal(L1, L2)
+    L3 = rx.forward(Y[:1].contiguous(), M).cpu().numpy()
+    np.testing.assert_array_equal(L3, L1[:1])
+    L4 = rx.forward(Y, M).cpu().numpy()
+    np.testing.assert_array_equal(L4, L1)
+
+
 def test_residual_96_four_antennas():
     w = WORKLOADS["resid_14x3276_b1024_bf16"]
     net = replace(w.net, n_sc=29, depth=2)
