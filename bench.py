@@ -61,8 +61,11 @@ def parse():
 
 
 def conv_flops(net, B):
-    """Algorithmic FLOPs (2 x MACs) of one body 3x3 conv layer over B slots (all branches)."""
-    return 2.0 * B * net.n_sym * net.n_sc * 9 * net.width * net.width * net.n_branches
+    """Algorithmic FLOPs (2 x MACs) of one body conv layer over B slots (all branches): the 3x3
+    conv, or the depthwise-separable conv's per-channel 3x3 plus 1x1."""
+    C = net.width
+    per_re = 9 * C + C * C if getattr(net, "depthwise", 0) else 9 * C * C
+    return 2.0 * B * net.n_sym * net.n_sc * per_re * net.n_branches
 
 
 def n_body_convs(net):
@@ -72,7 +75,8 @@ def n_body_convs(net):
 
 def net_flops_per_re(net):
     C, nb = net.width, net.n_branches
-    return 2 * 9 * net.c_in * C * nb + n_body_convs(net) * 2 * 9 * C * C * nb + 2 * C * net.qam_bits
+    body = 9 * C + C * C if getattr(net, "depthwise", 0) else 9 * C * C
+    return 2 * 9 * net.c_in * C * nb + n_body_convs(net) * 2 * body * nb + 2 * C * net.qam_bits
 
 
 def tensor_peak():
@@ -311,6 +315,9 @@ def roofline_of(w, net, B, rx, steps, n_sm):
         if whole:
             kname = (f"smallnet_kernel<{w.precision}> (tcgen05 whole network: every layer and the head, "
                      f"one slot per CTA; FLOPs of all layers)")
+        elif getattr(net, "depthwise", 0):
+            kname = (f"dwconv3x3_16_kernel + conv_tc_kernel<{w.precision},{net.n_branches},{net.width},"
+                     f"{net.width}> 1x1 (depthwise-separable body conv: two launches, FLOPs of both)")
         else:
             kname = (f"conv_tc_kernel<{w.precision},{net.n_branches},{net.width},{net.width}> "
                      f"(tcgen05 body 3x3 conv, {net.n_branches} branches per launch)")
@@ -498,7 +505,8 @@ def main():
                                   ("resid_14x3276_b1024_bf16", "fp8", 3),
                                   ("interf_14x72_b512_fp8", "fp8", 20), ("interf_14x72_b512_fp8", "bf16", 20),
                                   ("interf_14x72_b512_fp8", "fp32", 20),
-                                  ("plain_14x72_b16_fp32", "fp32", 20), ("plain_14x72_b16_fp32", "bf16", 20)]:
+                                  ("plain_14x72_b16_fp32", "fp32", 20), ("plain_14x72_b16_fp32", "bf16", 20),
+                                  ("resid_dw_14x624_b256_bf16", "bf16", 10), ("resid_dw_14x624_b256_bf16", "fp32", 5)]:
             vw = dataclasses.replace(WORKLOADS[name], precision=prec)
             r = measure_inference(ctx, vw, vw.batch, steps, 2)
             variants[f"{name}:{prec}"] = {"value": r["value"], "unit": "slots/s", "ms_per_step": r["ms_per_step"],

@@ -316,6 +316,15 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
         # a residual block's conv: standard 3x3, or depthwise-separable (per-channel 3x3, then
         # 1x1 with bias: "depthwise convolutions" of Sec. II-A / III)
         if getattr(cfg, "depthwise", 0):
+            if quant is not None and not hasattr(quant, "grad"):
+                # reduced-precision operands (reading R8): the per-channel 3x3 reads the
+                # activation in the operand format with its weights in full precision, its
+                # output is stored in the operand format, and the 1x1 takes operand-format
+                # weights
+                xq = tp.leaf(quant.act(tp[x]))
+                d = tp.leaf(quant.act(tp[dwconv3x3(tp, xq, ids[name + ".dw"])]))
+                wq = tp.leaf(quant.weight(tp[ids[name + ".w"]]))
+                return head1x1(tp, d, wq, ids[name + ".b"])
             return head1x1(tp, dwconv3x3(tp, x, ids[name + ".dw"]), ids[name + ".w"], ids[name + ".b"])
         return conv(x, ids[name + ".w"], ids[name + ".b"])
 

@@ -11,6 +11,11 @@ int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, cons
   if (a.fuse && (a.pre == 2 || (tc_groups(kind, nb, cout) > 1 && a.post[0] == 2)))
     return fail(CONET_ERR_UNSUPPORTED, "fused layer with a LayerNorm pre-activation or a normalised fused branch");
   const int mode = tc_mode(kind, nb, cin, cout, a);
+  if (a.taps == 1) {
+    if (kind == 0) return launch_conv_tc_pw_bf16(nb, cin, cout, mode, maps, a, s);
+    if (kind == 3) return launch_conv_tc_pw_fp16(nb, cin, cout, mode, maps, a, s);
+    return fail(CONET_ERR_UNSUPPORTED, "tensor-core 1x1 conv kind %d", kind);
+  }
   switch (kind) {
     case 0: return launch_conv_tc_bf16(nb, cin, cout, mode, maps, a, s);
     case 1: return launch_conv_tc_tf32(nb, cin, cout, mode, maps, a, s);
@@ -63,11 +68,13 @@ int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int
   return CONET_OK;
 }
 
-int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps) {
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps,
+                    int n_taps) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CONET_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  if (taps > n_taps) return fail(CONET_ERR_ARG, "weight box of %d taps over a tensor of %d", taps, n_taps);
   const int e = (kind == 0 || kind == 3) ? 2 : kind == 1 ? 4 : 1;
-  const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)cout, 9};
+  const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)cout, (cuuint64_t)n_taps};
   const cuuint64_t strides[2] = {(cuuint64_t)cin * e, (cuuint64_t)cout * cin * e};
   const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)rows, (cuuint32_t)taps};
   const cuuint32_t es[3] = {1, 1, 1};
@@ -82,6 +89,7 @@ int tc_branch_groups(int kind, int nb, int cout) { return tc_groups(kind, nb, co
 
 // Channels per K chunk and taps per stage of the instantiation for (kind, nb, cin, cout).
 int tc_chunk(int kind, int nb, int cin, int cout) { return tc_kc(kind, nb, cin, cout); }
+int tc_chunk_pw(int kind, int nb, int c) { return tc_plan(kind, nb, c, c, false); }
 int tc_taps(int kind, int nb, int cin, int cout) { return tc_halo(kind, nb, cin, cout) ? 3 : 1; }
 int tc_wbox_rows(int kind, int nb, int cin, int cout) { return cout / 2; }   // one CTA's half of a pair's B
 int tc_wbox_taps(int kind, int nb, int cin, int cout) { return tc_taps(kind, nb, cin, cout); }
@@ -125,12 +133,12 @@ int launch_weights_split(const float* w, int cout, int cin_src, int cin_dst, flo
 }
 
 // [Cout][3][3][cin_src] FP32 master -> [9][Cout][cin_dst] BF16, zero padded input channels
-__global__ void weights_bf16_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+__global__ void weights_bf16_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst, int taps,
                                     __nv_bfloat16* __restrict__ out) {
-  const int n = 9 * cout * cin_dst;
+  const int n = taps * cout * cin_dst;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int ci = i % cin_dst, rem = i / cin_dst, co = rem % cout, tap = rem / cout;
-    out[i] = __float2bfloat16_rn(ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f);
+    out[i] = __float2bfloat16_rn(ci < cin_src ? w[((size_t)co * taps + tap) * cin_src + ci] : 0.f);
   }
 }
 
@@ -166,12 +174,12 @@ __global__ void grads_bf16_kernel(GradsBf16Args a, int nb, long long n8) {
   }
 }
 
-__global__ void weights_f16_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst,
+__global__ void weights_f16_kernel(const float* __restrict__ w, int cout, int cin_src, int cin_dst, int taps,
                                    __half* __restrict__ out) {
-  const int n = 9 * cout * cin_dst;
+  const int n = taps * cout * cin_dst;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int ci = i % cin_dst, rem = i / cin_dst, co = rem % cout, tap = rem / cout;
-    out[i] = __float2half_rn(ci < cin_src ? w[((size_t)co * 9 + tap) * cin_src + ci] : 0.f);
+    out[i] = __float2half_rn(ci < cin_src ? w[((size_t)co * taps + tap) * cin_src + ci] : 0.f);
   }
 }
 
@@ -192,13 +200,14 @@ int launch_grads_bf16(const float* const* in, void* const* out, int nb, long lon
   return check_launch("grads_bf16_kernel");
 }
 
-int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s) {
+int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s,
+                      int taps) {
   if (kind == 3)
-    weights_f16_kernel<<<grid_for(9LL * cout * cin_dst, 256, 512), 256, 0, s>>>(w, cout, cin_src, cin_dst,
-                                                                                reinterpret_cast<__half*>(out));
+    weights_f16_kernel<<<grid_for((long long)taps * cout * cin_dst, 256, 512), 256, 0, s>>>(
+        w, cout, cin_src, cin_dst, taps, reinterpret_cast<__half*>(out));
   else
-    weights_bf16_kernel<<<grid_for(9LL * cout * cin_dst, 256, 512), 256, 0, s>>>(
-        w, cout, cin_src, cin_dst, reinterpret_cast<__nv_bfloat16*>(out));
+    weights_bf16_kernel<<<grid_for((long long)taps * cout * cin_dst, 256, 512), 256, 0, s>>>(
+        w, cout, cin_src, cin_dst, taps, reinterpret_cast<__nv_bfloat16*>(out));
   return check_launch("weights_16_kernel");
 }
 

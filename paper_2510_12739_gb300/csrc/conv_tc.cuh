@@ -182,6 +182,9 @@ __host__ __device__ constexpr int tc_kc(int kind, int nb, int cin, int cout) {
   return tc_halo(kind, nb, cin, cout) ? tc_plan(kind, nb, cin, cout, true) : tc_plan(kind, nb, cin, cout, false);
 }
 
+// HALO: 1 = the halo stage of a 3x3 conv (three subcarrier taps per stage), 0 = one 3x3 tap
+// per stage, 2 = a 1x1 conv (the pointwise half of a depthwise-separable conv: only the
+// centre tap, weights [1][Cout][Cin], CIN / KC K steps per tile).
 template <int KIND, int NB, int CIN, int COUT, int KC, int HALO, int MODE = 0>
 struct Cfg {
   static constexpr int ELT = elt_of(KIND);
@@ -189,9 +192,9 @@ struct Cfg {
   static_assert(ROW == 32 || ROW == 64 || ROW == 128, "row bytes");
   static constexpr int SLICES = ROW / 32;               // MMAs (32 bytes of K each) per chunk
   static constexpr int NSPLIT = nsplit_of(KIND);        // split TF32: hi and lo copies of A and B
-  static constexpr int TAPS = HALO ? 3 : 1;             // weight taps (subcarrier shifts) per stage
-  static constexpr int A_BOX = HALO ? TILE_M + 2 : TILE_M;
-  static constexpr int A_PART = (HALO ? HALO_ROWS : TILE_M) * ROW;
+  static constexpr int TAPS = HALO == 1 ? 3 : 1;        // weight taps (subcarrier shifts) per stage
+  static constexpr int A_BOX = HALO == 1 ? TILE_M + 2 : TILE_M;
+  static constexpr int A_PART = (HALO == 1 ? HALO_ROWS : TILE_M) * ROW;
   static constexpr int B_ROWS = COUT / 2;               // weight rows (output channels) per CTA
   static constexpr int B_PART = TAPS * B_ROWS * ROW;
   static constexpr int A_BYTES = NSPLIT * A_PART;
@@ -199,8 +202,8 @@ struct Cfg {
   static constexpr int NG = tc_groups(KIND, NB, COUT); // branch groups per tile
   static constexpr int G = NB / NG;                     // branches per MMA unit (one stage holds G)
   static constexpr int STAGE_TX = G * NSPLIT * (A_BOX * ROW + B_PART);   // bytes one CTA loads per stage
-  static constexpr int STAGE = (int)stage_bytes(KIND, G, COUT, ROW, HALO ? HALO_ROWS : TILE_M, TAPS);
-  static constexpr int K_ITERS = (9 / TAPS) * (CIN / KC);
+  static constexpr int STAGE = (int)stage_bytes(KIND, G, COUT, ROW, HALO == 1 ? HALO_ROWS : TILE_M, TAPS);
+  static constexpr int K_ITERS = (HALO == 2 ? 1 : 9 / TAPS) * (CIN / KC);
   static constexpr int COLS = NG == 1 ? pow2_ceil(NB * COUT) : G * COUT;   // stride of accumulator sets
   static constexpr int N_ACC = NG == 1 ? (2 * COLS <= 512 ? 2 : 1) : 2;
   static constexpr int STASH = NG == 1 ? 0 : 2 * G * COUT;                 // running-product columns
@@ -1669,11 +1672,12 @@ __global__ void __launch_bounds__((Cfg<KIND, NB, CIN, COUT, KC, HALO>::THREADS),
         if (rank == 0) tc::mbar_arrive_expect_tx(&full[s], 2 * K::STAGE_TX);
         const uint32_t fb_s = full0 + (uint32_t)(s * sizeof(uint64_t));
         // halo stage: symbol row t + dt, subcarriers from one before the tile, taps
-        // (dt, -1..1); else one tap (dt, df) with the tile's rows shifted by df
+        // (dt, -1..1); else one tap (dt, df) with the tile's rows shifted by df; a 1x1 conv
+        // reads the tile's own rows and its single weight tap
         const int grp = k / (CIN / KC), ch = (k % (CIN / KC)) * KC;
-        const int dt = HALO ? grp - 1 : grp / 3 - 1;
-        const int f0 = HALO ? fb * TILE_M - 1 : fb * TILE_M + grp % 3 - 1;
-        const int tap0 = HALO ? 3 * grp : grp;
+        const int dt = HALO == 1 ? grp - 1 : HALO == 2 ? 0 : grp / 3 - 1;
+        const int f0 = HALO == 1 ? fb * TILE_M - 1 : HALO == 2 ? fb * TILE_M : fb * TILE_M + grp % 3 - 1;
+        const int tap0 = HALO == 1 ? 3 * grp : HALO == 2 ? 0 : grp;
         const int r0 = (int)rank * K::B_ROWS;   // this CTA's half of the output channels
         uint8_t* st = smem + (size_t)s * K::STAGE;
 #pragma unroll
@@ -1900,11 +1904,27 @@ int tc_mode(int kind, int nb, int cin, int cout, const TcConvArgs& a) {
     return launch_tc_t<KI, NBV, CI, CO, KC_, HALO_, 0>(maps, a, s);                                                \
   }
 
+// The 1x1 conv (C -> C) of a depthwise-separable residual block of NBV branches: the body
+// conv's layer shapes with the pointwise stage (HALO = 2).
+#define TC_PW_CASE(KI, NBV, C)                                                                                    \
+  if (kind == KI && nb == NBV && cin == C && cout == C) {                                                          \
+    constexpr int KC_ = tc_plan(KI, NBV, C, C, false);                                                             \
+    if (mode == 1) return launch_tc_t<KI, NBV, C, C, KC_, 2, 1>(maps, a, s);                                        \
+    if (mode == 2) return launch_tc_t<KI, NBV, C, C, KC_, 2, 2>(maps, a, s);                                        \
+    if (mode == 4) return launch_tc_t<KI, NBV, C, C, KC_, 2, 4>(maps, a, s);                                        \
+    return launch_tc_t<KI, NBV, C, C, KC_, 2, 0>(maps, a, s);                                                      \
+  }
+
 // Dispatchers of the instantiated shapes of one operand type (conv_tc_<type>.cu); mode is
 // tc_mode's classification.  CONET_ERR_UNSUPPORTED for a shape that is not instantiated.
 int launch_conv_tc_bf16(int nb, int cin, int cout, int mode, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
 int launch_conv_tc_fp16(int nb, int cin, int cout, int mode, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
 int launch_conv_tc_tf32(int nb, int cin, int cout, int mode, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
 int launch_conv_tc_e4m3(int nb, int cin, int cout, int mode, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
+// the 1x1 convs of depthwise-separable blocks (conv_tc_pw_<type>.cu)
+int launch_conv_tc_pw_bf16(int nb, int cin, int cout, int mode, const TcMaps& maps, const TcConvArgs& a,
+                           cudaStream_t s);
+int launch_conv_tc_pw_fp16(int nb, int cin, int cout, int mode, const TcMaps& maps, const TcConvArgs& a,
+                           cudaStream_t s);
 
 }  // namespace conet

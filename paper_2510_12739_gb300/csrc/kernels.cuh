@@ -95,6 +95,16 @@ struct DwArgs {
   long long M;
 };
 int launch_dwconv3x3(const DwArgs& a, int n_br, cudaStream_t s);
+// The same conv on 16-bit activations (kind 0 BF16, 3 FP16) with FP32 weights [C][3][3]:
+// products accumulated in FP32 over the taps in order, the sum rounded once to the format.
+struct DwArgs16 {
+  const void* in[MAX_BR];
+  const float* w[MAX_BR];
+  void* out[MAX_BR];
+  int C, T, F;
+  long long M;
+};
+int launch_dwconv3x3_16(int kind, const DwArgs16& a, int n_br, cudaStream_t s);
 
 // ---------------------------------------------------------------- fusion / LN / head
 // Per RE (fuse_quad / fuse_row in csrc/fuse.cu):
@@ -258,14 +268,19 @@ struct TcConvArgs {
   int measure;
   int op;                      // fused layers: 0 = product, 1 = sum of the branches
   int feedback;                // fused layers, Example II: supports continue with a_b + a_0
+  int taps;                    // 0: the 3x3 conv; 1: a 1x1 conv (maps built with tc_chunk_pw,
+                               // one-tap boxes and [1][Cout][Cin] weights; BF16 / FP16)
 };
 int launch_conv_tc(int kind, int nb, int cin, int cout, const TcMaps& maps, const TcConvArgs& a, cudaStream_t s);
 // TMA maps of one conv operand: activations [slots][T][F][C] read in boxes of kc channels x
-// (TILE_M, or TILE_M + 2 when taps == 3) subcarriers; weights [9][cout][cin] in boxes of
-// kc x rows x taps (rows = tc_wbox_rows, taps = tc_wbox_taps of the conv's shape).
+// (TILE_M, or TILE_M + 2 when taps == 3) subcarriers; weights [n_taps][cout][cin] (9, or 1
+// for a 1x1 conv) in boxes of kc x rows x taps (rows = tc_wbox_rows, taps = tc_wbox_taps of
+// the conv's shape; 1 for a 1x1 conv).
 int make_act_map(CUtensorMap* map, int kind, const void* base, int C, int F, int T, int slots, int kc, int taps);
-int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps);
+int make_weight_map(CUtensorMap* map, int kind, const void* base, int cin, int cout, int kc, int rows, int taps,
+                    int n_taps = 9);
 int tc_chunk(int kind, int nb, int cin, int cout);
+int tc_chunk_pw(int kind, int nb, int c);   // channels per K chunk of the 1x1 conv (C -> C)
 int tc_branch_groups(int kind, int nb, int cout);   // branch groups per tile (1: all branches at once)
 // BF16 tensor-core dgrad operands: Wd[tap'][o][i] = W[i][8 - tap'][o] (the kernel rotated by
 // 180 degrees, input and output channels exchanged; input channel fastest) from the FP32
@@ -281,7 +296,9 @@ int tc_store_cols(int kind, int nb, int cin, int cout);
 // output map of a staged store: [slots x T][F][C] elements of `out_kind` (-1: FP32; else an
 // operand kind), box {cols, 32, 1}, swizzled for rows of cols elements
 int make_out_map(CUtensorMap* map, int out_kind, void* base, int C, int F, int symbols, int cols);
-int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s);
+// [Cout][taps][cin_src] FP32 master -> [taps][Cout][cin_dst] BF16 (kind 0) / FP16 (kind 3)
+int launch_weights_16(int kind, const float* w, int cout, int cin_src, int cin_dst, void* out, cudaStream_t s,
+                      int taps = 9);
 int launch_weights_split(const float* w, int cout, int cin_src, int cin_dst, float* hi, float* lo, cudaStream_t s);
 int launch_assemble_split(const float* Y, const uint8_t* mask, const float* psym, int B, int N, int T, int F,
                           int c_pad, float* hi, float* lo, cudaStream_t s);

@@ -101,8 +101,9 @@ int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float
 int net_setup(conet_s* h) {
   if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train && (h->prec != CONET_FP32 || h->cfg.residual))
     return fail(CONET_ERR_UNSUPPORTED, "sum interaction and Example II feedback train on FP32 plain networks only");
-  if (h->cfg.depthwise && (h->cfg.train || h->prec != CONET_FP32 || !h->cfg.residual))
-    return fail(CONET_ERR_UNSUPPORTED, "depthwise-separable convs: FP32 inference of residual networks only");
+  if (h->cfg.depthwise &&
+      (h->cfg.train || !h->cfg.residual || (h->prec != CONET_FP32 && h->prec != CONET_BF16 && h->prec != CONET_FP16)))
+    return fail(CONET_ERR_UNSUPPORTED, "depthwise-separable convs: FP32, BF16 and FP16 inference of residual networks only");
   const size_t n = h->L.total;
   CONET_TRY(dev_alloc_t(h, &h->params, n));
   if (h->cfg.support_inputs) CONET_TRY(dev_alloc_t(h, &h->params_eff, n));
@@ -126,7 +127,8 @@ int net_setup(conet_s* h) {
   if (h->prec != CONET_FP32 && !h->cfg.train) {
     // bytes per conv-input value (hi + lo for split TF32)
     const double opnd = h->prec == CONET_TF32X3 ? 8.0 : h->prec == CONET_FP8E4M3 ? 1.0 : 2.0;
-    const double per_slot = (double)h->T * h->F * ((double)na * h->C * 4 + 2.0 * h->nb * h->C * opnd + 32 * opnd);
+    const double n_in = h->cfg.depthwise ? 3.0 : 2.0;   // 16-bit conv inputs per branch (+ depthwise output)
+    const double per_slot = (double)h->T * h->F * ((double)na * h->C * 4 + n_in * h->nb * h->C * opnd + 32 * opnd);
     const double fit = 48e9 / per_slot;
     h->chunk = fit < 1 ? 1 : (fit < h->cfg.max_batch ? (int)fit : h->cfg.max_batch);
   }
@@ -135,7 +137,7 @@ int net_setup(conet_s* h) {
   CONET_TRY(dev_alloc_t(h, &h->X0, need_x0 ? re * h->c_pad : 4));
   h->act.resize(na);
   for (size_t i = 0; i < na; ++i) CONET_TRY(dev_alloc_t(h, &h->act[i], re * h->C));
-  if (h->cfg.depthwise)
+  if (h->cfg.depthwise && h->prec == CONET_FP32)
     for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->dw_out[b], re * h->C));
   CONET_TRY(dev_alloc_t(h, &h->d_loss, 1));
   CONET_TRY(dev_alloc_t(h, &h->d_cnt, 2));
@@ -556,11 +558,13 @@ int tc_setup(conet_s* h) {
       CONET_TRY(dev_alloc(h, &h->nxb[i][b], re * h->C * e));
       if (split) CONET_TRY(dev_alloc_t(h, &h->nxb_lo[i][b], re * h->C));
     }
+  if (h->cfg.depthwise)
+    for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc(h, &h->dwb[b], re * h->C * e));
   size_t wb = 0, ws = 0;
   for (const auto& c : h->L.convs) {
     const int cin_dst = c.cin == h->cin ? cin0 : c.cin;
     h->wb_off[c.off] = wb;
-    wb += (size_t)9 * cin_dst * c.cout;
+    wb += (size_t)c.taps * cin_dst * c.cout;
     h->fp8_ws_off[c.off] = ws;
     ws += (size_t)c.cout;
   }
@@ -596,15 +600,18 @@ int tc_setup(conet_s* h) {
   h->tcmaps.resize(n);
   for (int idx = 0; idx < n; ++idx) {
     const int cin = idx == 0 ? cin0 : h->C;
-    const int kc = tc_chunk(kind, h->nb, cin, h->C);
-    const int taps = tc_taps(kind, h->nb, cin, h->C);
-    const int wrows = tc_wbox_rows(kind, h->nb, cin, h->C), wtaps = tc_wbox_taps(kind, h->nb, cin, h->C);
+    // a depthwise-separable block conv: the 1x1 reads the depthwise output with one-tap boxes
+    const bool pw = h->cfg.depthwise && idx > 0;
+    const int kc = pw ? tc_chunk_pw(kind, h->nb, h->C) : tc_chunk(kind, h->nb, cin, h->C);
+    const int taps = pw ? 1 : tc_taps(kind, h->nb, cin, h->C);
+    const int wrows = tc_wbox_rows(kind, h->nb, cin, h->C), wtaps = pw ? 1 : tc_wbox_taps(kind, h->nb, cin, h->C);
     if (kc <= 0) return fail(CONET_ERR_UNSUPPORTED, "no tensor-core stage fits (kind %d, Cin %d, C %d)", kind, cin, h->C);
     for (int b = 0; b < h->nb; ++b) {
       const size_t woff = h->wb_off.at((size_t)tc_conv_w(h, idx, b));
-      CONET_TRY(make_act_map(&h->tcmaps[idx].a[b], kind, tc_conv_in(h, idx, b), cin, h->F, h->T, h->chunk, kc, taps));
+      CONET_TRY(make_act_map(&h->tcmaps[idx].a[b], kind, pw ? h->dwb[b] : tc_conv_in(h, idx, b), cin, h->F, h->T,
+                             h->chunk, kc, taps));
       CONET_TRY(make_weight_map(&h->tcmaps[idx].w[b], kind, static_cast<const uint8_t*>(h->wb) + woff * e, cin,
-                                h->C, kc, wrows, wtaps));
+                                h->C, kc, wrows, wtaps, pw ? 1 : 9));
       if (split) {
         CONET_TRY(make_act_map(&h->tcmaps[idx].a_lo[b], kind, tc_conv_in_lo(h, idx, b), cin, h->F, h->T, h->chunk,
                                kc, taps));
@@ -640,8 +647,8 @@ int tc_weights_changed(conet_s* h, cudaStream_t s) {
       CONET_TRY(launch_weights_fp8(pe + c.off, c.cout, c.cin, cin_dst, static_cast<uint8_t*>(h->wb) + wo,
                                    h->fp8_wscale + h->fp8_ws_off.at(c.off), s));
     else
-      CONET_TRY(launch_weights_16(kind, pe + c.off, c.cout, c.cin, cin_dst, static_cast<uint16_t*>(h->wb) + wo,
-                                  s));
+      CONET_TRY(launch_weights_16(kind, pe + c.off, c.cout, c.cin, cin_dst, static_cast<uint16_t*>(h->wb) + wo, s,
+                                  c.taps));
   }
   h->fp8_calibrated = false;   // activation ranges change with the weights
   return CONET_OK;
@@ -824,6 +831,25 @@ static int net_forward_tc_chunk(conet_s* h, const float* Y, const uint8_t* mask,
       CONET_TRY(fp8_set_scales(h, idx + 1, h->fp8_margin, s));
     }
     if (idx + 1 == n && !llr) break;     // calibration only: the head's output is not needed
+    if (h->cfg.depthwise && idx > 0) {
+      // depthwise-separable block conv: the per-channel 3x3 into dwb, then the 1x1 below
+      const int k = (idx - 1) / 2;
+      DwArgs16 d = {};
+      for (int b = 0; b < h->nb; ++b) {
+        d.in[b] = tc_conv_in(h, idx, b);
+        d.w[b] = P(h, (idx - 1) % 2 == 0 ? h->L.blk[b][k].c1d : h->L.blk[b][k].c2d);
+        d.out[b] = h->dwb[b];
+      }
+      d.C = h->C;
+      d.T = h->T;
+      d.F = h->F;
+      d.M = (long long)B * h->T * h->F;
+      prof_begin(h, PK_CONV, s);
+      const int rc = launch_dwconv3x3_16(kind, d, h->nb, s);
+      prof_end(h, s);
+      CONET_TRY(rc);
+      a.taps = 1;
+    }
     CONET_TRY(tc_conv(h, idx, a, B, s));
   }
   h->fwd_B = B;

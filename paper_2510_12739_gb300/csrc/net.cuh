@@ -73,6 +73,7 @@ struct conet_s {
   // tensor-core (BF16) path
   void* X0b = nullptr;                       // assembled input, BF16 [B][T][F][16]
   void* nxb[2][conet::MAX_BR] = {};          // BF16 conv inputs (ping-pong / H1, H2)
+  void* dwb[conet::MAX_BR] = {};             // 16-bit depthwise outputs (depthwise-separable blocks)
   void* X0b_lo = nullptr;                    // split-TF32 path: low parts of X0b / nxb / wb
   float* nxb_lo[2][conet::MAX_BR] = {};
   float* wb_lo = nullptr;

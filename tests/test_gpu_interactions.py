@@ -134,11 +134,31 @@ def test_depthwise_separable_blocks_fp32(key, kw):
         assert np.all(np.isfinite(L)) and err < 1e-4, err
 
 
-def test_depthwise_refused_outside_fp32_inference():
+@pytest.mark.parametrize("key,kw", [("resid_14x624_b256_fp32", dict(n_sc=37, depth=2)),
+                                    ("resid_14x624_b256_fp32", dict(n_sc=130, depth=1, n_branches=2, width=32)),
+                                    ("resid_14x3276_b1024_bf16", dict(n_sc=29, depth=2))])
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_depthwise_separable_blocks_16bit(key, kw, precision):
+    """Depthwise-separable blocks on the 16-bit tensor-core path (f3, reading R8): the
+    per-channel 3x3 on 16-bit activations (FP32 weights and accumulation, output rounded to
+    the format), then the 1x1 as a one-tap tcgen05 conv with the body convs' fused epilogues,
+    against the oracle's emulation at the He-init LayerNorm bars; also with the sum
+    interaction and Example II feedback where the network runs as one branch group."""
+    w = WORKLOADS[key]
+    extras = [dict()] if w.net.n_branches * w.net.width > 256 else [dict(), dict(fuse_op=1, feedback=1)]
+    for extra in extras:
+        net = replace(w.net, depthwise=1, **kw, **extra)
+        L, R = _run(net, w.sim, 2, precision)
+        err = normwise(L, R)
+        print(f"depthwise {key} {kw} {extra} {precision}: {err:.2e}")
+        assert np.all(np.isfinite(L)) and err < EMU_MAX_LN[precision], err
+
+
+def test_depthwise_refused_outside_its_paths():
     from paper_2510_12739_gb300 import api
     from paper_2510_12739_gb300._lib import ConetError
     net = replace(WORKLOADS["resid_14x624_b256_fp32"].net, depthwise=1, n_sc=37, depth=1)
-    for prec, train in (("bf16", False), ("fp32", True)):
+    for prec, train in (("fp8", False), ("tf32x3", False), ("fp32", True), ("bf16", True)):
         with pytest.raises(ConetError) as e:
             api.Receiver(net, prec, max_batch=1, train=train)
         assert e.value.code == -8

@@ -124,3 +124,66 @@ def test_training_gradient_with_identity_rounding_is_the_exact_gradient():
         assert np.allclose(g_id, g_ref, rtol=1e-12, atol=1e-14), kw
         g16 = half.grad_16(cfg, flat, X0, dllr)
         assert not np.allclose(g16, g_ref, rtol=1e-4)       # BF16 rounding does move it
+
+
+class _Recorder:
+    """Identity quantisation hooks that record what they are handed."""
+
+    def __init__(self):
+        self.acts, self.weights = [], []
+
+    def act(self, x):
+        self.acts.append(np.array(x, dtype=np.float64))
+        return np.asarray(x, dtype=np.float64)
+
+    def weight(self, w):
+        self.weights.append(np.array(w, dtype=np.float64))
+        return np.asarray(w, dtype=np.float64)
+
+
+def _dw_brute(X, W):
+    B, T, F, C = X.shape
+    out = np.zeros_like(X)
+    Xp = np.zeros((B, T + 2, F + 2, C))
+    Xp[:, 1:-1, 1:-1] = X
+    for kh in range(3):
+        for kw in range(3):
+            out += Xp[:, kh:kh + T, kw:kw + F] * W[:, kh, kw]
+    return out
+
+
+def test_depthwise_blocks_round_the_separable_operands():
+    """Reading R8, pinned through recording hooks: the reduced-precision forward of a
+    depthwise-separable network passes to the rounding hooks exactly the input layer's
+    operands and, per block conv, the conv's input, the per-channel 3x3's output (which is the
+    3x3 of the rounded input, by brute force) and the 1x1 weight, never the per-channel
+    weights; with identity hooks it is the exact forward, and with 16-bit rounding it stays
+    within a few roundings of it."""
+    from workloads import tiny_net
+    cfg = replace(tiny_net(residual=1, norm=1, depthwise=1, width=8), n_sc=10)
+    rng = np.random.default_rng(7)
+    flat = onet.init_params(cfg, 4) + 0.05 * rng.standard_normal(onet.param_count(cfg))
+    X0 = rng.standard_normal((2, cfg.n_sym, cfg.n_sc, cfg.c_in))
+    rec = _Recorder()
+    L = onet.forward(cfg, flat, X0, quant=rec)
+    assert np.array_equal(L, onet.forward(cfg, flat, X0))
+    nb, C, D = cfg.n_branches, cfg.width, cfg.depth
+    params, o = {}, 0
+    for name, shape in onet.param_layout(cfg):
+        n = int(np.prod(shape))
+        params[name] = flat[o:o + n].reshape(shape)
+        o += n
+    assert [w.shape for w in rec.weights] == [(C, 3, 3, cfg.c_in)] * nb + [(C, C)] * (2 * D * nb)
+    assert len(rec.acts) == nb + 2 * 2 * D * nb
+    blocks = rec.acts[nb:]
+    i = 0
+    for k in range(D):
+        for b in range(nb):
+            for conv in ("c1", "c2"):
+                x_in, dw_out = blocks[i], blocks[i + 1]
+                assert np.allclose(dw_out, _dw_brute(x_in, params[f"b{b}.k{k}.{conv}.dw"]), rtol=0, atol=1e-12)
+                i += 2
+    for fmt, unit in (("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11)):
+        L16 = half.forward_16(cfg, flat, X0, fmt)
+        assert not np.array_equal(L16, L)
+        assert np.max(np.abs(L16 - L)) <= 200 * unit * np.max(np.abs(L))

@@ -147,6 +147,9 @@ WORKLOADS = {
     "resnet_d24_14x624_bf16": Workload(
         "resnet_d24_14x624_bf16", _NET_D24, _SIM2, 256, "bf16",
         description="24-layer pre-activation ResNet, 1 branch x (input + 11 RB) x 96, 1.83 M parameters"),
+    "resid_dw_14x624_b256_bf16": Workload(
+        "resid_dw_14x624_b256_bf16", replace(_NET2, depthwise=1), _SIM2, 256, "bf16",
+        description="the 14x624 residual CoNet with depthwise-separable block convs (per-channel 3x3 + 1x1)"),
 }
 
 
