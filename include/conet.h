@@ -97,8 +97,8 @@ typedef enum {
  *                      separable (Sec. II-A, Sec. III): a per-channel 3x3 'same' conv without
  *                      bias, then a 1x1 conv with bias.  Flat layout of such a conv: depthwise
  *                      W [C][3][3], then 1x1 W [C][C], bias [C] (in place of W, bias below).
- *                      Inference handles of precision FP32, BF16 or FP16 (else
- *                      CONET_ERR_UNSUPPORTED); BF16 / FP16 run the per-channel 3x3 on the
+ *                      Inference handles of precision FP32, BF16 or FP16 and FP32 training
+ *                      handles (else CONET_ERR_UNSUPPORTED); BF16 / FP16 run the per-channel 3x3 on the
  *                      16-bit activations (FP32 weights and accumulation, output rounded to
  *                      the format) and the 1x1 on the tensor cores, for the 2 x 32, 3 x 64
  *                      and 4 x 96 networks (other widths: CONET_ERR_UNSUPPORTED at the

@@ -270,10 +270,11 @@ __global__ void dwconv3x3_kernel(DwArgs a, int n_br) {
       if (tt < 0 || tt >= a.T || ff < 0 || ff >= a.F) continue;
       const long long mm = m + (long long)(tap / 3 - 1) * a.F + (tap % 3 - 1);
       const float4 x = __ldg(reinterpret_cast<const float4*>(a.in[b] + mm * a.C + c));
-      acc.x = fmaf(__ldg(w + (c + 0) * 9 + tap), x.x, acc.x);
-      acc.y = fmaf(__ldg(w + (c + 1) * 9 + tap), x.y, acc.y);
-      acc.z = fmaf(__ldg(w + (c + 2) * 9 + tap), x.z, acc.z);
-      acc.w = fmaf(__ldg(w + (c + 3) * 9 + tap), x.w, acc.w);
+      const int wt = a.flip ? 8 - tap : tap;
+      acc.x = fmaf(__ldg(w + (c + 0) * 9 + wt), x.x, acc.x);
+      acc.y = fmaf(__ldg(w + (c + 1) * 9 + wt), x.y, acc.y);
+      acc.z = fmaf(__ldg(w + (c + 2) * 9 + wt), x.z, acc.z);
+      acc.w = fmaf(__ldg(w + (c + 3) * 9 + wt), x.w, acc.w);
     }
     *reinterpret_cast<float4*>(a.out[b] + m * a.C + c) = acc;
   }

@@ -86,13 +86,16 @@ struct ConvArgs {
 };
 int launch_conv3x3_fp32(const ConvArgs& a, int n_br, int cin, int cout, cudaStream_t s);
 
-// Depthwise 3x3 'same' conv per branch: out[m][c] = sum_tap w[c][tap] in[m + shift][c].
+// Depthwise 3x3 'same' conv per branch: out[m][c] = sum_tap w[c][tap'] in[m + shift(tap)][c]
+// with tap' = tap, or 8 - tap when flip is set (the kernel rotated by 180 degrees: the data
+// gradient of the conv).
 struct DwArgs {
   const float* in[MAX_BR];
   const float* w[MAX_BR];      // [C][3][3]
   float* out[MAX_BR];
   int C, T, F;
   long long M;
+  int flip;
 };
 int launch_dwconv3x3(const DwArgs& a, int n_br, cudaStream_t s);
 // The same conv on 16-bit activations (kind 0 BF16, 3 FP16) with FP32 weights [C][3][3]:
@@ -195,6 +198,30 @@ int launch_wgrad(const WgradArgs& a, cudaStream_t s);
 // {8/16, 16/16, 8/32, 32/32, 8/64, 64/64}), else launch_wgrad; partials need
 // wgrad_tiled_splits(M, n_br) * n_br * 9 * cin * cout floats.
 int launch_wgrad_tiled(const WgradArgs& a, cudaStream_t s);
+// Weight gradients of a depthwise-separable block conv (FP32 path, csrc/dwbwd.cu): the 1x1's
+// dW[co][ci] = sum_m g[m][co] z[m][ci] (z = the per-channel 3x3's output) and the per-channel
+// 3x3's dWd[c][tap] = sum_m dz[m][c] x[m + shift(tap)][c]; both overwrite dW / dWd (master
+// layouts [C][C] and [C][3][3]) through per-CTA partials in `part` (dw_bwd_splits(n_br) x
+// n_br x C x C floats at most).
+struct Wgrad1x1Args {
+  const float* g[MAX_BR];
+  const float* z[MAX_BR];
+  float* dW[MAX_BR];
+  float* part;
+  int C, n_br;
+  long long M;
+};
+struct DwWgradArgs {
+  const float* x[MAX_BR];
+  const float* dz[MAX_BR];
+  float* dWd[MAX_BR];
+  float* part;
+  int C, n_br, T, F;
+  long long M;
+};
+int dw_bwd_splits(int n_br);
+int launch_wgrad1x1(const Wgrad1x1Args& a, cudaStream_t s);
+int launch_dw_wgrad(const DwWgradArgs& a, cudaStream_t s);
 int wgrad_tiled_splits(long long M, int n_br);
 // Fixed-order sum over S split partials [S][n_br][9][cin][cout] of branch br into the master
 // layout dW [cout][3][3][cin_src].

@@ -101,9 +101,10 @@ int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float
 int net_setup(conet_s* h) {
   if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train && (h->prec != CONET_FP32 || h->cfg.residual))
     return fail(CONET_ERR_UNSUPPORTED, "sum interaction and Example II feedback train on FP32 plain networks only");
-  if (h->cfg.depthwise &&
-      (h->cfg.train || !h->cfg.residual || (h->prec != CONET_FP32 && h->prec != CONET_BF16 && h->prec != CONET_FP16)))
-    return fail(CONET_ERR_UNSUPPORTED, "depthwise-separable convs: FP32, BF16 and FP16 inference of residual networks only");
+  if (h->cfg.depthwise && (!h->cfg.residual || (h->cfg.train && h->prec != CONET_FP32) ||
+                            (h->prec != CONET_FP32 && h->prec != CONET_BF16 && h->prec != CONET_FP16)))
+    return fail(CONET_ERR_UNSUPPORTED,
+                "depthwise-separable convs: residual networks, FP32 training, FP32 / BF16 / FP16 inference");
   const size_t n = h->L.total;
   CONET_TRY(dev_alloc_t(h, &h->params, n));
   if (h->cfg.support_inputs) CONET_TRY(dev_alloc_t(h, &h->params_eff, n));
@@ -980,6 +981,61 @@ struct Bwd {
     prof_end(h, s);
     return rc;
   }
+  // gradients of a depthwise-separable block conv of every branch (x: its input, g: the
+  // gradient of its output, out: the gradient of x), with dw_out as the scratch of the
+  // per-channel 3x3's output z and then of its gradient dz
+  int sep(const float* const* x, float* const* g, const long* d_off, const long* w_off, const long* b_off,
+          float* const* out) {
+    const int nb = h->nb, C = h->C;
+    DwArgs z = {};
+    for (int b = 0; b < nb; ++b) {
+      z.in[b] = x[b];
+      z.w[b] = P(h, d_off[b]);
+      z.out[b] = h->dw_out[b];
+    }
+    z.C = C;
+    z.T = h->T;
+    z.F = h->F;
+    z.M = M;
+    Wgrad1x1Args w = {};
+    DwWgradArgs v = {};
+    ConvArgs c = {};
+    DwArgs d = z;
+    for (int b = 0; b < nb; ++b) {
+      w.g[b] = g[b];
+      w.z[b] = h->dw_out[b];
+      w.dW[b] = h->grads + w_off[b];
+      c.in[b] = g[b];
+      c.w[b] = P(h, w_off[b]);   // master [Cout][Cin]: the one-tap conv's [1][K = Cout][N = Cin]
+      c.out0[b] = h->dw_out[b];
+      v.x[b] = x[b];
+      v.dz[b] = h->dw_out[b];
+      v.dWd[b] = h->grads + d_off[b];
+      d.in[b] = h->dw_out[b];
+      d.out[b] = out[b];
+    }
+    w.part = v.part = h->wg_part;
+    w.C = v.C = C;
+    w.n_br = v.n_br = nb;
+    w.M = v.M = M;
+    v.T = h->T;
+    v.F = h->F;
+    c.M = (int)M;
+    c.T = h->T;
+    c.F = h->F;
+    c.taps = 1;
+    d.flip = 1;
+    prof_begin(h, PK_BACKWARD, s);
+    int rc = launch_dwconv3x3(z, nb, s);                                  // z
+    if (rc == CONET_OK) rc = launch_wgrad1x1(w, s);                        // d W1
+    if (rc == CONET_OK) rc = launch_conv3x3_fp32(c, nb, C, C, s);          // dz = g W1
+    if (rc == CONET_OK) rc = launch_dw_wgrad(v, s);                        // d Wd
+    if (rc == CONET_OK) rc = launch_dwconv3x3(d, nb, s);                   // dx
+    prof_end(h, s);
+    CONET_TRY(rc);
+    for (int b = 0; b < nb; ++b) CONET_TRY(bias(g[b], b_off[b]));
+    return CONET_OK;
+  }
   int fuse(const float* const* u, const float* gx0, float* const* gxs, float* const* gu, int point, int relu_mask) {
     FuseBwdArgs f = {};
     for (int b = 0; b < h->nb; ++b) {
@@ -1076,23 +1132,35 @@ int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
       for (int b = 0; b < nb; ++b) u[b] = A.U(blk, b);
       CONET_TRY(bw.fuse(u, G0[0], gxs, G1, k, 0));                       // G1 = d u
       const float* x[MAX_BR];
+      long d_off[MAX_BR];
+      const bool sep = h->cfg.depthwise != 0;
       // conv2: input h2, output gradient d u
       for (int b = 0; b < nb; ++b) {
         x[b] = A.H2(blk, b);
         w_off[b] = L.blk[b][blk].c2w;
         b_off[b] = L.blk[b][blk].c2b;
+        d_off[b] = L.blk[b][blk].c2d;
       }
-      CONET_TRY(bw.wgrad(x, G1, false, w_off, b_off));
-      CONET_TRY(bw.dgrad(G1, w_off, G2));                               // G2 = d h2
+      if (sep) {
+        CONET_TRY(bw.sep(x, G1, d_off, w_off, b_off, G2));               // G2 = d h2
+      } else {
+        CONET_TRY(bw.wgrad(x, G1, false, w_off, b_off));
+        CONET_TRY(bw.dgrad(G1, w_off, G2));                             // G2 = d h2
+      }
       for (int b = 0; b < nb; ++b)                                      // G0 = d t1
         CONET_TRY(bw.ln_relu(G2[b], A.T1(blk, b), L.blk[b][blk].ln2g, L.blk[b][blk].ln2b, nullptr, G0[b]));
       for (int b = 0; b < nb; ++b) {
         x[b] = A.H1(blk, b);
         w_off[b] = L.blk[b][blk].c1w;
         b_off[b] = L.blk[b][blk].c1b;
+        d_off[b] = L.blk[b][blk].c1d;
       }
-      CONET_TRY(bw.wgrad(x, G0, false, w_off, b_off));
-      CONET_TRY(bw.dgrad(G0, w_off, G2));                               // G2 = d h1
+      if (sep) {
+        CONET_TRY(bw.sep(x, G0, d_off, w_off, b_off, G2));               // G2 = d h1
+      } else {
+        CONET_TRY(bw.wgrad(x, G0, false, w_off, b_off));
+        CONET_TRY(bw.dgrad(G0, w_off, G2));                             // G2 = d h1
+      }
       for (int b = 0; b < nb; ++b)                                      // G0 = d x (skip + pre-act)
         CONET_TRY(bw.ln_relu(G2[b], A.XS(blk, b), L.blk[b][blk].ln1g, L.blk[b][blk].ln1b, G1[b], G0[b]));
       gxs = G0;
