@@ -99,8 +99,12 @@ int tc_weights_changed(conet_s* h, cudaStream_t s);
 int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float* llr, cudaStream_t s);
 
 int net_setup(conet_s* h) {
-  if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train && (h->prec != CONET_FP32 || h->cfg.residual))
-    return fail(CONET_ERR_UNSUPPORTED, "sum interaction and Example II feedback train on FP32 plain networks only");
+  // (Example II's feedback adds the main activation into the supports' rows in place, so a
+  // per-block recompute would add it twice)
+  if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train &&
+      (h->prec != CONET_FP32 || (h->cfg.residual && h->cfg.recompute && h->cfg.feedback)))
+    return fail(CONET_ERR_UNSUPPORTED,
+                "sum interaction and Example II feedback train on FP32 handles only (feedback: without recompute)");
   if (h->cfg.depthwise && (!h->cfg.residual || (h->cfg.train && h->prec != CONET_FP32) ||
                             (h->prec != CONET_FP32 && h->prec != CONET_BF16 && h->prec != CONET_FP16)))
     return fail(CONET_ERR_UNSUPPORTED,

@@ -75,17 +75,19 @@ def test_unsupported_combinations_are_refused():
     with pytest.raises(ConetError) as e:                  # training with the sum interaction: FP32 only
         api.Receiver(replace(WORKLOADS["plain_14x72_b16_fp32"].net, fuse_op=1), "bf16", max_batch=1, train=True)
     assert e.value.code == -8
-    with pytest.raises(ConetError) as e:                  # ... and plain networks only
+    with pytest.raises(ConetError) as e:                  # feedback adds in place: no per-block recompute
         api.Receiver(replace(WORKLOADS["resid_14x624_b256_fp32"].net, n_sc=37, feedback=1), "fp32", max_batch=1,
-                     train=True)
+                     train=True, recompute=True)
     assert e.value.code == -8
 
 
-@pytest.mark.parametrize("kw", VARIANTS + [dict(fuse_op=1, norm=1), dict(feedback=1, norm=1, fuse_mask=0b0101)])
+@pytest.mark.parametrize("kw", VARIANTS + [dict(fuse_op=1, norm=1), dict(feedback=1, norm=1, fuse_mask=0b0101),
+                                dict(fuse_op=1, residual=1, norm=1), dict(feedback=1, residual=1, norm=1),
+                                dict(fuse_op=1, feedback=1, residual=1, norm=1, fuse_mask=0b101)])
 def test_training_gradients_fp32(kw):
-    """Backward of the sum interaction and of Example II's feedback (FP32 plain networks): the
-    GPU gradient against the FP64 oracle's, per parameter tensor, within the product-fusion
-    bar (2e-4 normwise)."""
+    """Backward of the sum interaction and of Example II's feedback (FP32 plain and residual
+    networks): the GPU gradient against the FP64 oracle's, per parameter tensor, within the
+    product-fusion bar (2e-4 normwise)."""
     from oracle import net as onet, rx as orx
     from paper_2510_12739_gb300 import api
     from workloads import random_grid
