@@ -16,7 +16,9 @@ Architecture (Sec. III, Fig. "Example I", Fig. RB, Fig. MRB; readings O7-O13):
   plus the skip), the main branch the modified block MRB (the RB without its first
   normalisation, because its input was normalised right after the fusion).
 * Fusion after layer / block i (bit i of ``fuse_mask``): the main activation becomes
-  the element-wise (Hadamard) product of the main and all support activations,
+  the element-wise (Hadamard) product of the main and all support activations (or,
+  ``fuse_op``, their sum or, in plain networks, their concatenation over channels, reading
+  R9, which the main's next layer then reads with n_branches x width input channels),
   followed by LayerNorm over channels when ``norm`` is set; the support branches
   continue with their own unfused activations.
 * Head: 1x1 conv of the main activation to Q LLRs per resource element.
@@ -37,6 +39,12 @@ ADAM_EPS = 1e-8
 
 
 # ----------------------------------------------------------------------------- parameters
+def fused_width(cfg, i):
+    """Channels of the main activation after fusion point i: n_branches x width where the
+    point concatenates (fuse_op 2), else width."""
+    return cfg.n_branches * cfg.width if getattr(cfg, "fuse_op", 0) == 2 and cfg.fused(i) else cfg.width
+
+
 def param_layout(cfg):
     """Ordered list of (name, shape) of the flat float parameter vector."""
     C, Q = cfg.width, cfg.qam_bits
@@ -45,7 +53,8 @@ def param_layout(cfg):
         out += [(f"b{b}.in.w", (C, 3, 3, cfg.c_in)), (f"b{b}.in.b", (C,))]
         if not cfg.residual:
             for l in range(1, cfg.depth):
-                out += [(f"b{b}.l{l}.w", (C, 3, 3, C)), (f"b{b}.l{l}.b", (C,))]
+                cin = fused_width(cfg, l - 1) if b == 0 else C
+                out += [(f"b{b}.l{l}.w", (C, 3, 3, cin)), (f"b{b}.l{l}.b", (C,))]
         else:
             for k in range(cfg.depth):
                 if b >= 1 or cfg.resnet_baseline:
@@ -63,8 +72,9 @@ def param_layout(cfg):
         n_points = cfg.depth + 1 if cfg.residual else cfg.depth
         for i in range(n_points):
             if cfg.fused(i):
-                out += [(f"f{i}.g", (C,)), (f"f{i}.b", (C,))]
-    out += [("head.w", (Q, C)), ("head.b", (Q,))]
+                out += [(f"f{i}.g", (fused_width(cfg, i),)), (f"f{i}.b", (fused_width(cfg, i),))]
+    head_c = C if cfg.residual else fused_width(cfg, cfg.depth - 1)
+    out += [("head.w", (Q, head_c)), ("head.b", (Q,))]
     return out
 
 
@@ -257,6 +267,13 @@ def add(tp, x, y):
     return tp.op(tp[x] + tp[y], (x, y), lambda g: (g, g))
 
 
+def concat(tp, xs):
+    """Concatenation over the channel axis, branch 0 first."""
+    vals = [tp[x] for x in xs]
+    sizes = np.cumsum([v.shape[-1] for v in vals])[:-1]
+    return tp.op(np.concatenate(vals, axis=-1), tuple(xs), lambda g: tuple(np.split(g, sizes, axis=-1)))
+
+
 def add_all(tp, xs):
     out = xs[0]
     for x in xs[1:]:
@@ -283,6 +300,8 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
     conv3x3_rounded; otherwise the quantised operands are tape leaves (inference only).
     ``taps`` (optional dict): receives, per fusion point i followed by a LayerNorm, the
     variance over channels of the fused product at every RE, taps[i] = [B, T, F]."""
+    if getattr(cfg, "fuse_op", 0) == 2 and cfg.residual:
+        raise ValueError("concatenation fuses plain networks only (a residual stream keeps its width)")
     tp = Tape()
     P = unflatten(cfg, np.asarray(flat, dtype=np.float64))
     ids = {k: tp.leaf(v) for k, v in P.items()}
@@ -303,7 +322,8 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
         # supports keep their own activation, plus the main's with Example II's feedback
         if not cfg.fused(i):
             return list(acts)
-        m = add_all(tp, acts) if getattr(cfg, "fuse_op", 0) == 1 else hadamard(tp, acts)
+        op = getattr(cfg, "fuse_op", 0)
+        m = add_all(tp, acts) if op == 1 else concat(tp, acts) if op == 2 else hadamard(tp, acts)
         if cfg.norm:
             if taps is not None:
                 taps[i] = tp[m].var(axis=-1)

@@ -192,6 +192,9 @@ FD_CASES = [
     dict(depthwise=1, residual=1, norm=1, width=4),
     dict(support_inputs=1, n_branches=3),
     dict(support_inputs=1, residual=1, norm=1),
+    dict(fuse_op=2, norm=1, n_branches=3),
+    dict(fuse_op=2, fuse_mask=0b01),
+    dict(fuse_op=2, feedback=1, norm=1),
 ]
 
 
@@ -339,3 +342,29 @@ def test_selective_support_inputs_gradient_is_zero_on_withheld_channels():
         else:
             assert np.all(gw[..., :2 * cfg.n_rx] == 0.0)
             assert np.abs(gw[..., 2 * cfg.n_rx:]).max() > 0
+
+
+def test_concatenation_with_zero_support_weights_is_the_unfused_main():
+    """Concatenation (fuse_op 2, reading R9) without LayerNorm: when the main's wide layers and
+    the head give zero weight to the support channels (input channels C.. of the concatenated
+    activation), the LLRs are those of the same network without fusion whose main weights are
+    the first C input channels; the parameter count grows by the support channels' weights."""
+    cfg = tiny_net(fuse_op=2, n_sc=7)
+    plain = replace(cfg, fuse_mask=0)
+    C, nb = cfg.width, cfg.n_branches
+    rng = np.random.default_rng(21)
+    flat = onet.init_params(cfg, 5) + 0.1 * rng.standard_normal(onet.param_count(cfg))
+    P = onet.unflatten(cfg, flat)
+    for l in range(1, cfg.depth):
+        P[f"b0.l{l}.w"][..., C:] = 0.0
+    P["head.w"][:, C:] = 0.0
+    Q = {name: (P[name][..., :C] if name.startswith("b0.l") and name.endswith(".w") else
+                P[name][:, :C] if name == "head.w" else P[name]) for name, _ in onet.param_layout(cfg)}
+    flat_c = np.concatenate([P[name].ravel() for name, _ in onet.param_layout(cfg)])
+    flat_p = np.concatenate([Q[name].ravel() for name, _ in onet.param_layout(plain)])
+    X0, _, _ = _inputs(cfg, 3)
+    assert np.allclose(onet.forward(cfg, flat_c, X0), onet.forward(plain, flat_p, X0), rtol=0, atol=1e-12)
+    extra = (cfg.depth - 1) * C * 9 * (nb - 1) * C + cfg.qam_bits * (nb - 1) * C
+    assert onet.param_count(cfg) - onet.param_count(plain) == extra
+    with pytest.raises(ValueError):
+        onet.forward(replace(cfg, residual=1, norm=1), onet.init_params(replace(cfg, residual=1, norm=1), 1), X0)

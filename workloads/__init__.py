@@ -34,7 +34,9 @@ class NetConfig:
     resnet_baseline: 1 = a single pre-activation ResNet branch, no fusion (the
         DeepRx-style comparison network).
     fuse_op: the interaction operation at a fusion point (Sec. III lists multiplication,
-        addition and concatenation): 0 = element-wise product, 1 = element-wise sum.
+        addition and concatenation): 0 = element-wise product, 1 = element-wise sum, 2 =
+        concatenation over channels (plain networks; the main's next layer and the head then
+        read n_branches x width channels).
     feedback: 1 = Example II (Sec. III, Fig. "conet2"): at every fusion point each support
         net continues with its own activation plus the main net's (before the fusion).
     depthwise: 1 = the convs inside RB / MRB blocks are depthwise-separable: a per-channel
