@@ -86,7 +86,12 @@ typedef enum {
  *                      recompute = 0.  Ignored by inference handles and plain networks.
  *   fuse_op          : the interaction at a fusion point (Sec. III: multiplication,
  *                      addition or concatenation of the subnets' activations): 0 = the
- *                      element-wise product (default), 1 = the element-wise sum.
+ *                      element-wise product (default), 1 = the element-wise sum, 2 = the
+ *                      concatenation over channels (plain networks, n_branches x width <=
+ *                      128, FP32 inference handles only): the main's next conv and the
+ *                      head then read n_branches x width channels, so in the flat layout
+ *                      the main's layer weights after a fused layer are [C][3][3][nb C],
+ *                      the fusion LayerNorm's gamma / beta [nb C] and the head [Q][nb C].
  *   feedback         : 1 = Example II (Sec. III, Fig. "conet2"): at every fusion point each
  *                      support net continues with its own activation plus the main net's
  *                      (taken before the fusion).

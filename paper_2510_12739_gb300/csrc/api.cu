@@ -58,6 +58,12 @@ bool fused_at(const conet_config& c, int i) {
   return (c.fuse_mask >> i) & 1;
 }
 
+// Channels of the main activation after fusion point i: n_branches x width where the point
+// concatenates (fuse_op 2, plain networks), else width.
+int fused_width(const conet_config& c, int i) {
+  return c.fuse_op == 2 && fused_at(c, i) ? c.n_branches * c.width : c.width;
+}
+
 Layout build_layout(const conet_config& c) {
   Layout L;
   const int C = c.width, Q = c.qam_bits, cin = 2 * c.n_rx + 3;
@@ -89,7 +95,7 @@ Layout build_layout(const conet_config& c) {
     if (!c.residual) {
       for (int l = 1; l < c.depth; ++l) {
         long w, bb;
-        conv(C, C, &w, &bb);
+        conv(b == 0 ? fused_width(c, l - 1) : C, C, &w, &bb);
         L.lw[b].push_back(w);
         L.lb[b].push_back(bb);
       }
@@ -109,11 +115,15 @@ Layout build_layout(const conet_config& c) {
   const int n_points = c.residual ? c.depth + 1 : c.depth;
   for (int i = 0; i < n_points; ++i) {
     long g = -1, bb = -1;
-    if (c.norm && fused_at(c, i)) ln(&g, &bb);
+    if (c.norm && fused_at(c, i)) {
+      g = take((size_t)fused_width(c, i), 1, 0.f);
+      bb = take((size_t)fused_width(c, i), 2, 0.f);
+    }
     L.fg.push_back(g);
     L.fb.push_back(bb);
   }
-  L.hw = take((size_t)Q * C, 0, sqrtf(2.0f / C));
+  const int head_c = c.residual ? C : fused_width(c, c.depth - 1);
+  L.hw = take((size_t)Q * head_c, 0, sqrtf(2.0f / head_c));
   L.hb = take((size_t)Q, 2, 0.f);
   L.total = o;
   return L;
@@ -136,7 +146,11 @@ static int validate_config(const conet_config* c) {
     if (i && c->pilot_syms[i] <= c->pilot_syms[i - 1]) return fail(CONET_ERR_ARG, "pilot symbols must increase");
   }
   if (c->pilot_comb < 1) return fail(CONET_ERR_ARG, "pilot_comb %d < 1", c->pilot_comb);
-  if (c->fuse_op < 0 || c->fuse_op > 1) return fail(CONET_ERR_ARG, "fuse_op %d not in {0, 1}", c->fuse_op);
+  if (c->fuse_op < 0 || c->fuse_op > 2) return fail(CONET_ERR_ARG, "fuse_op %d not in {0, 1, 2}", c->fuse_op);
+  if (c->fuse_op == 2 && c->residual)
+    return fail(CONET_ERR_ARG, "concatenation (fuse_op 2) fuses plain networks only");
+  if (c->fuse_op == 2 && c->n_branches * c->width > 128)
+    return fail(CONET_ERR_ARG, "concatenated width %d > 128", c->n_branches * c->width);
   if (c->feedback < 0 || c->feedback > 1) return fail(CONET_ERR_ARG, "feedback %d not in {0, 1}", c->feedback);
   if (c->depthwise < 0 || c->depthwise > 1) return fail(CONET_ERR_ARG, "depthwise %d not in {0, 1}", c->depthwise);
   if (c->support_inputs < 0 || c->support_inputs > 1)

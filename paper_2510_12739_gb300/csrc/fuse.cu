@@ -2,7 +2,7 @@
 // interaction, its LayerNorm, the pre-activations of the next block and the LLR head
 // (fuse_quad, four REs per warp step, for widths that are multiples of 32; else
 // fuse_row, one RE per warp step).  The forward and the backward's recompute of a
-// block's input both launch it.
+// block's input both launch it; the concatenation interaction runs concat_fuse_kernel.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -321,9 +321,86 @@ __global__ void fuse_kernel(FuseArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ concatenation
+// The concatenation interaction (op 2) of a plain network: the main's next input is the
+// branches' rows side by side, W = n_br x C <= 128 channels, normalised over all W when
+// fuse_g is set, written to x0_out [M][W]; the head (at the last layer) reads all W.  One
+// warp per RE, lane l holding channels l + 32 v.  With feedback the supports' rows get the
+// main's added in place.
+__global__ void concat_fuse_kernel(FuseArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int C = a.C, W = a.n_br * a.C;
+  for (long long m = warp0; m < a.M; m += nwarps) {
+    float x[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = lane + 32 * v;
+      x[v] = c < W ? __ldcg(a.u[c / C] + m * C + c % C) : 0.f;
+    }
+    if (a.feedback) {
+      // Example II: each support continues with its activation plus the main's (the
+      // concatenation above keeps the values before this)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int c = lane + 32 * v;
+        if (c >= C && c < W)
+          const_cast<float*>(a.u[c / C])[m * C + c % C] = x[v] + __ldcg(a.u[0] + m * C + c % C);
+      }
+    }
+    if (a.fuse_g) {
+      float s = 0.f;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) s += x[v];
+      const float mean = warp_sum(s) / (float)W;
+      float q = 0.f;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float d = lane + 32 * v < W ? x[v] - mean : 0.f;
+        q += d * d;
+      }
+      const float rstd = rsqrtf(warp_sum(q) / (float)W + 1e-5f);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int c = lane + 32 * v;
+        x[v] = c < W ? (x[v] - mean) * rstd * __ldg(a.fuse_g + c) + __ldg(a.fuse_b + c) : 0.f;
+      }
+    }
+    if (a.x0_out) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int c = lane + 32 * v;
+        if (c < W) a.x0_out[m * W + c] = x[v];
+      }
+    }
+    if (a.head_w) {
+      for (int q = 0; q < a.Q; ++q) {
+        float s = 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int c = lane + 32 * v;
+          if (c < W) s += __ldg(a.head_w + q * W + c) * x[v];
+        }
+        s = warp_sum(s);
+        if (lane == 0) {
+          const float v = s + __ldg(a.head_b + q);
+          a.llr[m * a.Q + q] = v;
+          if (!(fabsf(v) <= FLT_MAX)) *a.nonfinite = 1;
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int launch_fuse(const FuseArgs& a, cudaStream_t s) {
+  if (a.fuse && a.op == 2) {
+    if (a.n_br * a.C > 128) return fail(CONET_ERR_UNSUPPORTED, "concatenated width %d > 128", a.n_br * a.C);
+    concat_fuse_kernel<<<grid_for(a.M * 32, 256, 152 * 16), 256, 0, s>>>(a);
+    return check_launch("concat_fuse_kernel");
+  }
   if (a.C > 128) return fail(CONET_ERR_UNSUPPORTED, "width %d > 128", a.C);
   const int g = grid_for(a.M * 32, 256, 152 * 16);
   switch (a.C) {

@@ -105,6 +105,8 @@ int net_setup(conet_s* h) {
       (h->prec != CONET_FP32 || (h->cfg.residual && h->cfg.recompute && h->cfg.feedback)))
     return fail(CONET_ERR_UNSUPPORTED,
                 "sum interaction and Example II feedback train on FP32 handles only (feedback: without recompute)");
+  if (h->cfg.fuse_op == 2 && (h->prec != CONET_FP32 || h->cfg.train))
+    return fail(CONET_ERR_UNSUPPORTED, "concatenation (fuse_op 2): FP32 inference only");
   if (h->cfg.depthwise && (!h->cfg.residual || (h->cfg.train && h->prec != CONET_FP32) ||
                             (h->prec != CONET_FP32 && h->prec != CONET_BF16 && h->prec != CONET_FP16)))
     return fail(CONET_ERR_UNSUPPORTED,
@@ -144,6 +146,7 @@ int net_setup(conet_s* h) {
   for (size_t i = 0; i < na; ++i) CONET_TRY(dev_alloc_t(h, &h->act[i], re * h->C));
   if (h->cfg.depthwise && h->prec == CONET_FP32)
     for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->dw_out[b], re * h->C));
+  if (h->cfg.fuse_op == 2) CONET_TRY(dev_alloc_t(h, &h->xcat, re * h->nb * h->C));
   CONET_TRY(dev_alloc_t(h, &h->d_loss, 1));
   CONET_TRY(dev_alloc_t(h, &h->d_cnt, 2));
   CONET_CUDA(cudaMemset(h->params, 0, n * sizeof(float)));
@@ -237,11 +240,26 @@ int net_weights_changed(conet_s* h, cudaStream_t s) {
   return tc_weights_changed(h, s);
 }
 
-static int conv_layer(conet_s* h, ConvArgs& a, int cin, cudaStream_t s) {
-  prof_begin(h, cin == h->C ? PK_CONV : PK_CONV_IN, s);
-  const int rc = launch_conv3x3_fp32(a, h->nb, cin, h->C, s);
+static int conv_layer(conet_s* h, ConvArgs& a, int cin, cudaStream_t s, int n_br = 0) {
+  prof_begin(h, cin == h->C || n_br ? PK_CONV : PK_CONV_IN, s);
+  const int rc = launch_conv3x3_fp32(a, n_br ? n_br : h->nb, cin, h->C, s);
   prof_end(h, s);
   return rc;
+}
+
+// A plain layer whose main input is the concatenation of the previous layer's activations
+// (fuse_op 2): the main branch's conv reads n_branches x width channels, so it launches on
+// its own, the supports' convs together.
+static int conv_layer_concat(conet_s* h, const ConvArgs& a, cudaStream_t s) {
+  ConvArgs m = a, sup = a;
+  CONET_TRY(conv_layer(h, m, h->nb * h->C, s, 1));
+  for (int b = 1; b < h->nb; ++b) {
+    sup.in[b - 1] = a.in[b];
+    sup.w[b - 1] = a.w[b];
+    sup.bias[b - 1] = a.bias[b];
+    sup.out0[b - 1] = a.out0[b];
+  }
+  return conv_layer(h, sup, h->C, s, h->nb - 1);
 }
 
 static int fuse_stage(conet_s* h, const FuseArgs& f, cudaStream_t s) {
@@ -443,20 +461,25 @@ int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* l
   if (!h->cfg.residual) {
     for (int l = 0; l < depth; ++l) {
       ConvArgs c = conv_args(h, B);
+      // the main activation after a concatenating fusion point is n_branches x width wide
+      const bool wide_in = l > 0 && fused_width(h->cfg, l - 1) != h->C;
       for (int b = 0; b < nb; ++b) {
-        c.in[b] = l == 0 ? h->X0 : (b == 0 ? A.XM(l - 1) : A.A(l - 1, b));
+        c.in[b] = l == 0 ? h->X0 : (b == 0 ? (wide_in ? h->xcat : A.XM(l - 1)) : A.A(l - 1, b));
         c.w[b] = W(h, l == 0 ? L.in_w[b] : L.lw[b][l - 1]);
         c.bias[b] = P(h, l == 0 ? L.in_b[b] : L.lb[b][l - 1]);
         c.out0[b] = A.A(l, b);
       }
       c.relu0 = 1;
-      CONET_TRY(conv_layer(h, c, l == 0 ? h->c_pad : h->C, s));
+      if (wide_in)
+        CONET_TRY(conv_layer_concat(h, c, s));
+      else
+        CONET_TRY(conv_layer(h, c, l == 0 ? h->c_pad : h->C, s));
       FuseArgs f = fuse_args(h, B);
       for (int b = 0; b < nb; ++b) f.u[b] = A.A(l, b);
       f.fuse = fused_at(h->cfg, l);
       f.fuse_g = P(h, L.fg[l]);
       f.fuse_b = P(h, L.fb[l]);
-      f.x0_out = A.XM(l);
+      f.x0_out = fused_width(h->cfg, l) != h->C ? h->xcat : A.XM(l);
       if (l == depth - 1) {
         f.head_w = P(h, L.hw);
         f.head_b = P(h, L.hb);

@@ -41,6 +41,7 @@ struct Layout {
 };
 
 bool fused_at(const conet_config& c, int i);
+int fused_width(const conet_config& c, int i);
 Layout build_layout(const conet_config& c);
 
 }  // namespace conet
@@ -88,6 +89,7 @@ struct conet_s {
   float* zero_c = nullptr;                   // C zeros: the dgrad conv has no bias
   std::vector<conet::TcMaps> dg_maps;        // per body conv (in wd_off order)
   std::map<size_t, size_t> dg_index;         // branch 0's conv weight offset -> dg_maps index
+  float* xcat = nullptr;                     // FP32 plain networks, fuse_op 2: the concatenated main input
   int* d_err = nullptr;                      // device error word of the tensor-core kernels
   // E4M3 path
   float* fp8_wscale = nullptr;               // per conv: [Cout] per-output-channel weight scales

@@ -54,7 +54,8 @@ def test_param_count_matches_oracle_layout(lib, name):
 @pytest.mark.parametrize("kw", [dict(), dict(norm=1), dict(residual=1, norm=1, n_branches=3),
                                 dict(residual=1, norm=1, depthwise=1),
                                 dict(n_branches=1, residual=1, norm=1, resnet_baseline=1),
-                                dict(fuse_mask=0b01, norm=1)])
+                                dict(fuse_mask=0b01, norm=1), dict(fuse_op=2), dict(fuse_op=2, norm=1, fuse_mask=0b01),
+                                dict(fuse_op=2, n_branches=3, depth=3, norm=1)])
 def test_param_count_tiny(lib, kw):
     from oracle import net as onet
     from paper_2510_12739_gb300 import api
@@ -68,7 +69,8 @@ def test_host_side_argument_errors(lib):
     base = WORKLOADS["plain_14x72_b16_fp32"].net
     for bad in (dict(qam_bits=5), dict(n_branches=0), dict(n_branches=5), dict(n_rx=0),
                 dict(pilot_syms=(11, 2)), dict(pilot_syms=(2, 14)), dict(width=0), dict(support_inputs=2),
-                dict(support_inputs=1, n_branches=1, residual=1, resnet_baseline=1)):
+                dict(support_inputs=1, n_branches=1, residual=1, resnet_baseline=1), dict(fuse_op=3),
+                dict(fuse_op=2, residual=1, norm=1), dict(fuse_op=2, n_branches=3, width=48)):
         with pytest.raises(ConetError) as e:
             api.param_count(replace(base, **bad))
         assert e.value.code == -1

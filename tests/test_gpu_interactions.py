@@ -156,6 +156,31 @@ def test_depthwise_separable_blocks_16bit(key, kw, precision):
         assert np.all(np.isfinite(L)) and err < EMU_MAX_LN[precision], err
 
 
+@pytest.mark.parametrize("kw", [dict(fuse_op=2), dict(fuse_op=2, norm=1), dict(fuse_op=2, norm=1, fuse_mask=0b0101),
+                                dict(fuse_op=2, feedback=1, norm=1), dict(fuse_op=2, n_branches=3, width=16, norm=1)])
+def test_concatenation_fp32(kw):
+    """The concatenation interaction (reading R9) on the FP32 path: the stage writes the
+    branches' activations side by side (normalised over all of them), the main's next conv
+    reads n_branches x width channels in a launch of its own, and the head the same width
+    after the last layer; against the FP64 oracle at the FP32 bar (1e-4 normwise)."""
+    w = WORKLOADS["plain_14x72_b16_fp32"]
+    net = replace(w.net, n_sc=40, **kw)
+    L, R = _run(net, w.sim, 2, "fp32")
+    err = normwise(L, R)
+    print(f"concatenation {kw}: {err:.2e}")
+    assert np.all(np.isfinite(L)) and err < 1e-4, err
+
+
+def test_concatenation_refused_outside_fp32_inference():
+    from paper_2510_12739_gb300 import api
+    from paper_2510_12739_gb300._lib import ConetError
+    net = replace(WORKLOADS["plain_14x72_b16_fp32"].net, fuse_op=2, n_sc=40)
+    for prec, train in (("bf16", False), ("fp8", False), ("fp32", True)):
+        with pytest.raises(ConetError) as e:
+            api.Receiver(net, prec, max_batch=1, train=train)
+        assert e.value.code == -8
+
+
 @pytest.mark.parametrize("kw,recompute", [(dict(), False), (dict(n_branches=2, width=32), True),
                                           (dict(n_branches=1, width=16, resnet_baseline=1), False)])
 def test_depthwise_training_gradients_fp32(kw, recompute):
