@@ -114,6 +114,13 @@ typedef enum {
  *                      weights on the Re / Im Y channels (the first 2 n_rx of the flat
  *                      layout's c_in) act as zero whatever the parameters hold, and their
  *                      gradients are zero.  Needs n_branches >= 2 (else CONET_ERR_ARG).
+ *   support_mask     : with support_inputs = 1, another subset of the inputs for the support
+ *                      nets: bit j set = input channel j (of the 2 n_rx + 3 assembled
+ *                      channels: Re Y per antenna, Im Y per antenna, pilot mask, Re and Im of
+ *                      the LS estimate) is fed; the other channels' weights act as zero and
+ *                      get zero gradients.  0 = the pilot information (bits 2 n_rx .. 2 n_rx
+ *                      + 2).  Bits at or above 2 n_rx + 3, or a mask without support_inputs,
+ *                      give CONET_ERR_ARG.
  */
 typedef struct {
   int n_rx, n_sym, n_sc, qam_bits;
@@ -130,6 +137,7 @@ typedef struct {
   int feedback;                /* 1 = Example II: supports add the main net's activation */
   int depthwise;               /* 1 = depthwise-separable convs inside RB / MRB blocks */
   int support_inputs;          /* 1 = support nets see only the pilot information */
+  unsigned support_mask;       /* with support_inputs: the input channels they see (0: pilots) */
 } conet_config;
 
 /*

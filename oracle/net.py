@@ -8,7 +8,8 @@ Architecture (Sec. III, Fig. "Example I", Fig. RB, Fig. MRB; readings O7-O13):
   III's generalisation: subsets of the inputs, such as the pilot symbols, fed selectively
   to supporting nets).  Their input layers read the pilot mask and the LS estimate at the
   pilots but not the received signal: the weights on the Re / Im Y channels of every
-  antenna are held at zero (reading O15).
+  antenna are held at zero (reading O15); ``support_mask`` names another subset of the
+  input channels (bit j = channel j fed).
 * Input layer of every branch: 3x3 conv + bias + ReLU.
 * Plain networks: ``depth`` 3x3 conv + ReLU layers per branch (the input layer
   included).  Residual networks: input layer then ``depth`` blocks; support branches
@@ -354,8 +355,13 @@ def forward(cfg, flat, X0, keep_tape=False, quant=None, taps=None):
         w = ids[f"b{b}.in.w"]
         if b == 0 or not getattr(cfg, "support_inputs", 0):
             return w
+        # the channels fed: support_mask's bits, by default the pilot information (pilot
+        # mask and LS estimate, channels 2 N .. 2 N + 2)
+        keep = getattr(cfg, "support_mask", 0) or (7 << (2 * cfg.n_rx))
         M = np.ones(P[f"b{b}.in.w"].shape)
-        M[..., :2 * cfg.n_rx] = 0.0
+        for j in range(cfg.c_in):
+            if not (keep >> j) & 1:
+                M[..., j] = 0.0
         return tp.op(tp[w] * M, (w,), lambda g: (g * M,))
 
     acts = [relu(tp, conv(x_in, input_w(b), ids[f"b{b}.in.b"])) for b in range(nb)]

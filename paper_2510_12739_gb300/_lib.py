@@ -21,7 +21,7 @@ class conet_config(C.Structure):
                 ("max_batch", C.c_int), ("train", C.c_int),
                 ("pilot_syms", C.c_int * 4), ("n_pilot_syms", C.c_int), ("pilot_comb", C.c_int),
                 ("pilot_seed", C.c_uint64), ("recompute", C.c_int), ("fuse_op", C.c_int), ("feedback", C.c_int),
-                ("depthwise", C.c_int), ("support_inputs", C.c_int)]
+                ("depthwise", C.c_int), ("support_inputs", C.c_int), ("support_mask", C.c_uint)]
 
 
 class conet_sim_params(C.Structure):

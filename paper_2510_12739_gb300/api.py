@@ -32,6 +32,7 @@ def make_config(net, max_batch: int = 1, train: bool = False, recompute: bool = 
     c.feedback = int(getattr(net, "feedback", 0))
     c.depthwise = int(getattr(net, "depthwise", 0))
     c.support_inputs = int(getattr(net, "support_inputs", 0))
+    c.support_mask = int(getattr(net, "support_mask", 0))
     return c
 
 

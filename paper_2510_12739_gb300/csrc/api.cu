@@ -156,6 +156,9 @@ static int validate_config(const conet_config* c) {
   if (c->support_inputs < 0 || c->support_inputs > 1)
     return fail(CONET_ERR_ARG, "support_inputs %d not in {0, 1}", c->support_inputs);
   if (c->support_inputs && c->n_branches < 2) return fail(CONET_ERR_ARG, "support_inputs needs a support net");
+  if (c->support_mask && !c->support_inputs) return fail(CONET_ERR_ARG, "support_mask needs support_inputs = 1");
+  if (c->support_mask >> (2 * c->n_rx + 3))
+    return fail(CONET_ERR_ARG, "support_mask 0x%x names channels beyond the %d inputs", c->support_mask, 2 * c->n_rx + 3);
   return CONET_OK;
 }
 
@@ -512,6 +515,7 @@ uint64_t config_hash(const conet_config& c) {
                    c.fuse_op, c.feedback, c.depthwise};
   for (int v : f) mix(v);
   if (c.support_inputs) mix(0x5e1ec7 + c.support_inputs);   // (absent from hashes of full-input networks)
+  if (c.support_mask) mix(0x5a3c0000ull + c.support_mask);
   for (int i = 0; i < c.n_pilot_syms && i < 4; ++i) mix(c.pilot_syms[i]);
   mix((int64_t)c.pilot_seed);
   return h;

@@ -734,14 +734,15 @@ int launch_weights_dgrad_layout(const float* w, int C, float* out, cudaStream_t 
   return check_launch("weights_dgrad_kernel");
 }
 
-__global__ void zero_input_channels_kernel(float* __restrict__ w, int n, int cin, int n_zero) {
+__global__ void zero_input_channels_kernel(float* __restrict__ w, int n, int cin, unsigned keep) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    if (i % cin < n_zero) w[i] = 0.f;
+    if (!((keep >> (i % cin)) & 1u)) w[i] = 0.f;
 }
 
-int launch_zero_input_channels(float* w, int cout, int cin, int n_zero, cudaStream_t s) {
+int launch_zero_input_channels(float* w, int cout, int cin, unsigned keep, cudaStream_t s) {
+  if (cin > 32) return fail(CONET_ERR_ARG, "input channel mask over %d channels", cin);
   const int n = cout * 9 * cin;
-  zero_input_channels_kernel<<<grid_for(n, 256), 256, 0, s>>>(w, n, cin, n_zero);
+  zero_input_channels_kernel<<<grid_for(n, 256), 256, 0, s>>>(w, n, cin, keep);
   return check_launch("zero_input_channels_kernel");
 }
 

@@ -225,9 +225,9 @@ int launch_dw_wgrad(const DwWgradArgs& a, cudaStream_t s);
 int wgrad_tiled_splits(long long M, int n_br);
 // Fixed-order sum over S split partials [S][n_br][9][cin][cout] of branch br into the master
 // layout dW [cout][3][3][cin_src].
-// w [cout][3][3][cin]: the entries of input channels 0 .. n_zero - 1 set to zero (the
-// support nets' withheld received-signal inputs, Sec. III selective inputs).
-int launch_zero_input_channels(float* w, int cout, int cin, int n_zero, cudaStream_t s);
+// w [cout][3][3][cin] (cin <= 32): the entries of the input channels whose bit in `keep` is
+// clear set to zero (the support nets' withheld inputs, Sec. III selective inputs).
+int launch_zero_input_channels(float* w, int cout, int cin, unsigned keep, cudaStream_t s);
 int launch_wgrad_reduce(const float* part, int S, int n_br, int br, int cin, int cout, int cin_src, float* dW,
                         cudaStream_t s);
 // The weight gradient on the tensor cores from BF16 copies of the operands (wgrad_tc.cu):

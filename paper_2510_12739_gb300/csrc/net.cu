@@ -208,11 +208,13 @@ int net_setup(conet_s* h) {
 }
 
 // Selective support inputs (Sec. III): the support nets' input-layer weights on the
-// received-signal channels (the first 2 N of the input) held at zero in `w` (the master
-// parameters' effective copy, or their gradient).
+// withheld channels -- by default the received signal (the first 2 N of the input), else
+// every channel outside support_mask -- held at zero in `w` (the master parameters'
+// effective copy, or their gradient).
 static int zero_withheld_inputs(const conet_s* h, float* w, cudaStream_t s) {
   if (!h->cfg.support_inputs) return CONET_OK;
-  for (int b = 1; b < h->nb; ++b) CONET_TRY(launch_zero_input_channels(w + h->L.in_w[b], h->C, h->cin, 2 * h->N, s));
+  const unsigned keep = h->cfg.support_mask ? h->cfg.support_mask : 7u << (2 * h->N);   // mask, Re / Im LS
+  for (int b = 1; b < h->nb; ++b) CONET_TRY(launch_zero_input_channels(w + h->L.in_w[b], h->C, h->cin, keep, s));
   return CONET_OK;
 }
 

@@ -70,7 +70,8 @@ def test_host_side_argument_errors(lib):
     for bad in (dict(qam_bits=5), dict(n_branches=0), dict(n_branches=5), dict(n_rx=0),
                 dict(pilot_syms=(11, 2)), dict(pilot_syms=(2, 14)), dict(width=0), dict(support_inputs=2),
                 dict(support_inputs=1, n_branches=1, residual=1, resnet_baseline=1), dict(fuse_op=3),
-                dict(fuse_op=2, residual=1, norm=1), dict(fuse_op=2, n_branches=3, width=48)):
+                dict(fuse_op=2, residual=1, norm=1), dict(fuse_op=2, n_branches=3, width=48),
+                dict(support_mask=1), dict(support_inputs=1, support_mask=1 << 7)):
         with pytest.raises(ConetError) as e:
             api.param_count(replace(base, **bad))
         assert e.value.code == -1
@@ -98,10 +99,13 @@ def test_checkpoint_hash_tracks_the_network_shape(lib):
     assert h0 == api.checkpoint_hash(base)
     for kw in (dict(n_rx=2), dict(n_sc=73), dict(qam_bits=6), dict(n_branches=3), dict(depth=5), dict(width=16),
                dict(norm=1), dict(fuse_mask=0b11), dict(pilot_syms=(2, 12)), dict(pilot_comb=3),
-               dict(pilot_seed=1), dict(residual=1), dict(fuse_op=1), dict(feedback=1), dict(support_inputs=1)):
+               dict(pilot_seed=1), dict(residual=1), dict(fuse_op=1), dict(feedback=1), dict(support_inputs=1),
+               dict(fuse_op=2)):
         assert api.checkpoint_hash(replace(base, **kw)) != h0, kw
     # a full-input network's hash is the one it had before the selective-inputs field existed
     assert h0 == api.checkpoint_hash(replace(base, support_inputs=0))
+    sel = replace(base, support_inputs=1)
+    assert api.checkpoint_hash(replace(sel, support_mask=0b11)) != api.checkpoint_hash(sel)
     cfg = api.make_config(base, max_batch=7, train=True)
     h = C.c_uint64()
     assert lib.conet_checkpoint_hash(C.byref(cfg), C.byref(h)) == 0 and h.value == h0

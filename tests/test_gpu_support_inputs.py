@@ -89,6 +89,30 @@ def test_plain_network(key, kw, B, precision):
     np.testing.assert_array_equal(L, L0)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_support_mask_subset(precision):
+    """support_mask names another subset of the inputs for the support nets (here Re Y, Im Y
+    and the Im part of the LS estimate): parity with the oracle, and bitwise the full-input
+    network whose support input layers have zero weights on the other channels."""
+    w = WORKLOADS["plain_14x72_b16_fp32"]
+    keep = 0b10011
+    net = replace(w.net, n_branches=3, depth=3, n_sc=40, support_inputs=1, support_mask=keep)
+    params = _params(net)
+    L, ref = _forward(net, w.sim, 2, precision, params)
+    err = normwise(L, _reference(net, ref, params, precision))
+    print(f"support mask {keep:#b} {precision}: {err:.2e}")
+    assert np.all(np.isfinite(L)) and err < {"fp32": 1e-4, "bf16": 1e-3}[precision], err
+    full = replace(net, support_inputs=0, support_mask=0)
+    zeroed = params.copy()
+    for b in range(1, net.n_branches):
+        wb = _in_w(net, zeroed, b)
+        for j in range(net.c_in):
+            if not (keep >> j) & 1:
+                wb[..., j] = 0.0
+    L0, _ = _forward(full, w.sim, 2, precision, zeroed)
+    np.testing.assert_array_equal(L, L0)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_residual_network(precision):
     w = WORKLOADS["resid_14x624_b256_fp32"]

@@ -192,6 +192,7 @@ FD_CASES = [
     dict(depthwise=1, residual=1, norm=1, width=4),
     dict(support_inputs=1, n_branches=3),
     dict(support_inputs=1, residual=1, norm=1),
+    dict(support_inputs=1, support_mask=0b10011, n_branches=3),
     dict(fuse_op=2, norm=1, n_branches=3),
     dict(fuse_op=2, fuse_mask=0b01),
     dict(fuse_op=2, feedback=1, norm=1),
@@ -368,3 +369,28 @@ def test_concatenation_with_zero_support_weights_is_the_unfused_main():
     assert onet.param_count(cfg) - onet.param_count(plain) == extra
     with pytest.raises(ValueError):
         onet.forward(replace(cfg, residual=1, norm=1), onet.init_params(replace(cfg, residual=1, norm=1), 1), X0)
+
+
+def test_support_mask_names_the_fed_channels():
+    """support_mask: the default subset is the pilot information (channels 2 N .. 2 N + 2), so
+    naming those bits gives the default network exactly; a mask keeping only channel j makes
+    the support nets' input layers blind to every other channel (changing them changes
+    nothing), while changing channel j does."""
+    cfg = tiny_net(support_inputs=1, n_branches=3)
+    flat = onet.init_params(cfg, 6)
+    X0, _, _ = _inputs(cfg, 7)
+    pil = 7 << (2 * cfg.n_rx)
+    assert np.array_equal(onet.forward(cfg, flat, X0), onet.forward(replace(cfg, support_mask=pil), flat, X0))
+    j = 1
+    one = replace(cfg, support_mask=1 << j, fuse_mask=0b01)
+    L = onet.forward(one, flat, X0)
+    # only the support nets' view of the input matters through the fusion; perturb their
+    # other channels' weights, then channel j's
+    P = onet.unflatten(one, flat.copy())
+    for b in (1, 2):
+        P[f"b{b}.in.w"][..., [c for c in range(cfg.c_in) if c != j]] += 1.0
+    flat2 = np.concatenate([P[n].ravel() for n, _ in onet.param_layout(one)])
+    assert np.array_equal(onet.forward(one, flat2, X0), L)
+    P[f"b1.in.w"][..., j] += 1.0
+    flat3 = np.concatenate([P[n].ravel() for n, _ in onet.param_layout(one)])
+    assert not np.allclose(onet.forward(one, flat3, X0), L)

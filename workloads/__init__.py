@@ -43,6 +43,8 @@ class NetConfig:
         3x3 conv followed by a 1x1 conv with bias (Sec. II-A, Sec. III).
     support_inputs: 1 = the support nets are fed only the pilot information (pilot mask and
         LS estimate at the pilots), not the received signal (Sec. III, selective inputs).
+    support_mask: with support_inputs = 1, another subset: bit j = input channel j of the
+        assembled grid is fed to the support nets (0 = the pilot information).
     """
     n_rx: int
     n_sc: int
@@ -58,6 +60,7 @@ class NetConfig:
     feedback: int = 0
     depthwise: int = 0
     support_inputs: int = 0
+    support_mask: int = 0
     n_sym: int = 14
     pilot_syms: tuple = (2, 11)
     pilot_comb: int = 2
