@@ -88,7 +88,7 @@ typedef enum {
  *                      addition or concatenation of the subnets' activations): 0 = the
  *                      element-wise product (default), 1 = the element-wise sum, 2 = the
  *                      concatenation over channels (plain networks, n_branches x width <=
- *                      128, FP32 inference handles only): the main's next conv and the
+ *                      128, FP32 handles only, inference and training): the main's next conv and the
  *                      head then read n_branches x width channels, so in the flat layout
  *                      the main's layer weights after a fused layer are [C][3][3][nb C],
  *                      the fusion LayerNorm's gamma / beta [nb C] and the head [Q][nb C].

@@ -442,13 +442,65 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 }
 
 // dgrad weights: Wd[tap'][co][ci] = W[co][8 - tap'][ci]  (conv of dz with the kernel
-// rotated by 180 degrees, input and output channels exchanged)
-__global__ void weights_dgrad_kernel(const float* __restrict__ w, int C, float* __restrict__ out) {
-  const int n = 9 * C * C;
+// rotated by 180 degrees, input and output channels exchanged) for W [cout][3][3][cin]
+__global__ void weights_dgrad_kernel(const float* __restrict__ w, int cout, int cin, float* __restrict__ out) {
+  const int n = 9 * cout * cin;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int ci = i % C, rem = i / C, co = rem % C, tp = rem / C;
-    out[i] = w[((size_t)co * 9 + (8 - tp)) * C + ci];
+    const int ci = i % cin, rem = i / cin, co = rem % cout, tp = rem / cout;
+    out[i] = w[((size_t)co * 9 + (8 - tp)) * cin + ci];
   }
+}
+
+// Backward of the concatenation interaction (op 2) of a plain network: the main's fused
+// activation x = [u_0, u_1, ...] (W = n_br x C channels, the supports' rows with the main's
+// subtracted again when Example II's feedback added it in place) with the gradient gx0
+// [M][W]; through the LayerNorm over W when ln_g is set, each branch's slice goes back to
+// its activation, plus the support's own stream gradient gxs[b], plus (feedback) every
+// support's stream gradient into the main; then the ReLU mask of the activation.
+__global__ void __launch_bounds__(EW_THREADS) concat_fuse_bwd_kernel(FuseBwdArgs a) {
+  constexpr int CPL = 4;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int C = a.C, W = a.n_br * a.C;
+  float pv[2][CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) pv[0][j] = pv[1][j] = 0.f;
+  for (long long m = warp0; m < a.M; m += nwarps) {
+    float x[CPL], g[CPL], dx[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j;
+      x[j] = g[j] = 0.f;
+      if (c < W) {
+        const int b = c / C, cc = c % C;
+        float v = a.u[b][m * C + cc];
+        if (a.feedback && b > 0) v -= a.u[0][m * C + cc];
+        x[j] = v;
+        g[j] = a.gx0[m * W + c];
+      }
+    }
+    if (a.ln_g) {
+      ln_backward(x, g, a.ln_g, W, lane, dx, pv[0], pv[1]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) dx[j] = g[j];
+    }
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j;
+      if (c >= W) continue;
+      const int b = c / C, cc = c % C;
+      float o = dx[j];
+      if (b > 0 && a.gxs[b]) o += a.gxs[b][m * C + cc];
+      if (b == 0 && a.feedback)
+        for (int s = 1; s < a.n_br; ++s)
+          if (a.gxs[s]) o += a.gxs[s][m * C + cc];
+      if (a.relu_mask && !(x[j] > 0.f)) o = 0.f;
+      a.gu[b][m * C + cc] = o;
+    }
+  }
+  if (a.part) block_store_partials<2, CPL>(pv, W, a.part);
 }
 
 }  // namespace
@@ -456,6 +508,11 @@ __global__ void weights_dgrad_kernel(const float* __restrict__ w, int C, float* 
 int ew_grid(long long M) { return grid_for(M * 32, EW_THREADS, EW_PART_CTAS); }
 
 int launch_fuse_bwd(const FuseBwdArgs& a, cudaStream_t s) {
+  if (a.fuse && a.op == 2) {
+    if (a.n_br * a.C > 128) return fail(CONET_ERR_UNSUPPORTED, "concatenated width %d > 128", a.n_br * a.C);
+    concat_fuse_bwd_kernel<<<ew_grid(a.M), EW_THREADS, 0, s>>>(a);
+    return check_launch("concat_fuse_bwd_kernel");
+  }
   const int cpl = (a.C + 31) / 32;
   if (cpl < 1 || cpl > 4) return fail(CONET_ERR_UNSUPPORTED, "width %d > 128", a.C);
   const int g = ew_grid(a.M);
@@ -729,8 +786,9 @@ int launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr
   return check_launch("adam_kernel");
 }
 
-int launch_weights_dgrad_layout(const float* w, int C, float* out, cudaStream_t s) {
-  weights_dgrad_kernel<<<grid_for(9LL * C * C, 256, 512), 256, 0, s>>>(w, C, out);
+int launch_weights_dgrad_layout(const float* w, int cout, float* out, cudaStream_t s, int cin) {
+  if (cin <= 0) cin = cout;
+  weights_dgrad_kernel<<<grid_for(9LL * cout * cin, 256, 512), 256, 0, s>>>(w, cout, cin, out);
   return check_launch("weights_dgrad_kernel");
 }
 

@@ -310,6 +310,8 @@ int launch_conv3x3_fp32(const ConvArgs& a, int n_br, int cin, int cout, cudaStre
   CONV_CASE(88, 88, 8)
   CONV_CASE(64, 32, 8)   // main layers after a concatenating fusion point: 2 x 32 -> 32
   CONV_CASE(48, 16, 8)   // 3 x 16 -> 16
+  CONV_CASE(32, 64, 8)   // ... and their data gradients: 32 -> 2 x 32
+  CONV_CASE(16, 48, 8)   // 16 -> 3 x 16
 #undef CONV_CASE
   return fail(CONET_ERR_UNSUPPORTED, "FP32 conv3x3 with Cin=%d Cout=%d is not instantiated", cin, cout);
 }

@@ -148,7 +148,8 @@ struct FuseBwdArgs {
   const float* ln_g;          // post-fusion LN gain or NULL
   float* part;                // [grid][2][C] dgamma / dbeta partials (when ln_g)
   int n_br, fuse, relu_mask, C;
-  int op;                     // interaction: 0 = product, 1 = sum
+  int op;                     // interaction: 0 = product, 1 = sum, 2 = concatenation (gx0 and
+                              // the LN partials then n_br x C wide)
   int feedback;               // Example II: the supports' u hold a_b + a_0 (their next input)
   long long M;
 };
@@ -241,7 +242,8 @@ int launch_wgrad_tc(const WgradArgs& a, int slots, void* scratch, int* err, cuda
 
 int launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2, float eps,
                 float bc1, float bc2, cudaStream_t s);
-int launch_weights_dgrad_layout(const float* w, int C, float* out, cudaStream_t s);
+// (cin = 0: square, cin = cout)
+int launch_weights_dgrad_layout(const float* w, int cout, float* out, cudaStream_t s, int cin = 0);
 
 // ---------------------------------------------------------------- tensor-core convolution
 struct TcMaps {

@@ -90,6 +90,13 @@ struct Acts {
 };
 
 const float* P(const conet_s* h, long off) { return off < 0 ? nullptr : h->params + off; }
+
+// Plain networks with the concatenation interaction: whether the main activation after
+// layer l is n_branches x width wide, and its buffer (one per layer when training).
+bool wide_at(const conet_s* h, int l) { return l >= 0 && fused_width(h->cfg, l) != h->C; }
+float* xcat_at(const conet_s* h, int l) {
+  return h->xcat + (h->cfg.train ? (size_t)l * h->chunk * h->T * h->F * h->nb * h->C : 0);
+}
 const float* W(const conet_s* h, long off) { return h->wt + h->wt_off.at((size_t)off); }
 
 }  // namespace
@@ -105,8 +112,8 @@ int net_setup(conet_s* h) {
       (h->prec != CONET_FP32 || (h->cfg.residual && h->cfg.recompute && h->cfg.feedback)))
     return fail(CONET_ERR_UNSUPPORTED,
                 "sum interaction and Example II feedback train on FP32 handles only (feedback: without recompute)");
-  if (h->cfg.fuse_op == 2 && (h->prec != CONET_FP32 || h->cfg.train))
-    return fail(CONET_ERR_UNSUPPORTED, "concatenation (fuse_op 2): FP32 inference only");
+  if (h->cfg.fuse_op == 2 && h->prec != CONET_FP32)
+    return fail(CONET_ERR_UNSUPPORTED, "concatenation (fuse_op 2): FP32 handles only");
   if (h->cfg.depthwise && (!h->cfg.residual || (h->cfg.train && h->prec != CONET_FP32) ||
                             (h->prec != CONET_FP32 && h->prec != CONET_BF16 && h->prec != CONET_FP16)))
     return fail(CONET_ERR_UNSUPPORTED,
@@ -146,7 +153,9 @@ int net_setup(conet_s* h) {
   for (size_t i = 0; i < na; ++i) CONET_TRY(dev_alloc_t(h, &h->act[i], re * h->C));
   if (h->cfg.depthwise && h->prec == CONET_FP32)
     for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->dw_out[b], re * h->C));
-  if (h->cfg.fuse_op == 2) CONET_TRY(dev_alloc_t(h, &h->xcat, re * h->nb * h->C));
+  // concatenated main activations: one buffer, or (training) one per layer for the backward
+  if (h->cfg.fuse_op == 2)
+    CONET_TRY(dev_alloc_t(h, &h->xcat, re * h->nb * h->C * (h->cfg.train ? h->cfg.depth : 1)));
   CONET_TRY(dev_alloc_t(h, &h->d_loss, 1));
   CONET_TRY(dev_alloc_t(h, &h->d_cnt, 2));
   CONET_CUDA(cudaMemset(h->params, 0, n * sizeof(float)));
@@ -187,7 +196,9 @@ int net_setup(conet_s* h) {
     }
     for (int k = 0; k < 3; ++k)
       for (int b = 0; b < h->nb; ++b) CONET_TRY(dev_alloc_t(h, &h->G[k][b], re * h->C));
-    CONET_TRY(dev_alloc_t(h, &h->ew_part, (size_t)EW_PART_CTAS * (size_t)(h->Q * h->C + h->Q + 2 * h->C)));
+    const size_t cw = (size_t)(h->cfg.fuse_op == 2 ? h->nb * h->C : h->C);   // widest fused activation
+    CONET_TRY(dev_alloc_t(h, &h->ew_part, (size_t)EW_PART_CTAS * (h->Q * cw + h->Q + 2 * cw)));
+    if (h->cfg.fuse_op == 2) CONET_TRY(dev_alloc_t(h, &h->gcat, re * cw));
     // split partials of the weight gradient, sized for the largest split count of either kernel
     const size_t splits = (size_t)(WG_MAX_SPLITS * h->nb > WG_TILED_MAX_CTAS ? WG_MAX_SPLITS * h->nb : WG_TILED_MAX_CTAS);
     const size_t wg = splits * 9 * (size_t)(h->C > h->c_pad ? h->C : h->c_pad) * h->C;
@@ -236,7 +247,7 @@ int net_weights_changed(conet_s* h, cudaStream_t s) {
         CONET_TRY(launch_weights_dgrad_bf16(h->params + c.off, c.cout,
                                             static_cast<uint16_t*>(h->wd16) + h->wd_off.at(c.off), s));
       else
-        CONET_TRY(launch_weights_dgrad_layout(h->params + c.off, c.cout, h->wd + h->wd_off.at(c.off), s));
+        CONET_TRY(launch_weights_dgrad_layout(h->params + c.off, c.cout, h->wd + h->wd_off.at(c.off), s, c.cin));
     }
   }
   return tc_weights_changed(h, s);
@@ -466,7 +477,7 @@ int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* l
       // the main activation after a concatenating fusion point is n_branches x width wide
       const bool wide_in = l > 0 && fused_width(h->cfg, l - 1) != h->C;
       for (int b = 0; b < nb; ++b) {
-        c.in[b] = l == 0 ? h->X0 : (b == 0 ? (wide_in ? h->xcat : A.XM(l - 1)) : A.A(l - 1, b));
+        c.in[b] = l == 0 ? h->X0 : (b == 0 ? (wide_in ? xcat_at(h, l - 1) : A.XM(l - 1)) : A.A(l - 1, b));
         c.w[b] = W(h, l == 0 ? L.in_w[b] : L.lw[b][l - 1]);
         c.bias[b] = P(h, l == 0 ? L.in_b[b] : L.lb[b][l - 1]);
         c.out0[b] = A.A(l, b);
@@ -481,7 +492,7 @@ int net_forward(conet_s* h, const float* Y, const uint8_t* mask, int B, float* l
       f.fuse = fused_at(h->cfg, l);
       f.fuse_g = P(h, L.fg[l]);
       f.fuse_b = P(h, L.fb[l]);
-      f.x0_out = fused_width(h->cfg, l) != h->C ? h->xcat : A.XM(l);
+      f.x0_out = wide_at(h, l) ? xcat_at(h, l) : A.XM(l);
       if (l == depth - 1) {
         f.head_w = P(h, L.hw);
         f.head_b = P(h, L.hb);
@@ -925,20 +936,24 @@ struct Bwd {
     CONET_TRY(launch_channel_sums(g, M, h->C, h->ew_part, s));
     return reduce_ew(h->C, off);
   }
-  // weight + bias gradients of one conv layer of every branch
-  int wgrad(const float* const* x, const float* const* g, bool input_layer, const long* w_off, const long* b_off) {
-    const int cin_pad = input_layer ? h->c_pad : h->C;
+  // weight + bias gradients of one conv layer of every branch (or of branches b0 .. b0 +
+  // nbr - 1, whose input has cin channels: the main's layer after a concatenation)
+  int wgrad(const float* const* x, const float* const* g, bool input_layer, const long* w_off, const long* b_off,
+            int b0 = 0, int nbr = 0, int cin = 0) {
+    if (!nbr) nbr = h->nb;
+    const int cin_pad = cin ? cin : input_layer ? h->c_pad : h->C;
     WgradArgs w = {};
-    for (int b = 0; b < h->nb; ++b) {
-      w.x[b] = x[b];
-      w.g[b] = g[b];
-      w.dW[b] = h->grads + w_off[b];
-      w.cin_src[b] = input_layer ? h->cin : h->C;
+    for (int i = 0; i < nbr; ++i) {
+      const int b = b0 + i;
+      w.x[i] = x[b];
+      w.g[i] = g[b];
+      w.dW[i] = h->grads + w_off[b];
+      w.cin_src[i] = cin ? cin : input_layer ? h->cin : h->C;
     }
     w.part = h->wg_part;
     w.cin = cin_pad;
     w.cout = h->C;
-    w.n_br = h->nb;
+    w.n_br = nbr;
     w.T = h->T;
     w.F = h->F;
     w.M = M;
@@ -949,7 +964,7 @@ struct Bwd {
                        : launch_wgrad_tiled(w, s);
     prof_end(h, s);
     CONET_TRY(rc);
-    for (int b = 0; b < h->nb; ++b) CONET_TRY(bias(g[b], b_off[b]));
+    for (int b = b0; b < b0 + nbr; ++b) CONET_TRY(bias(g[b], b_off[b]));
     return CONET_OK;
   }
   // tensor maps of the BF16 dgrad conv of one layer (built on first use; host-side encoding)
@@ -973,8 +988,9 @@ struct Bwd {
     return CONET_OK;
   }
   // data gradient of a body conv of every branch: out = conv3x3(g, rotated W); with BF16
-  // training on the tensor cores (BF16 operands, FP32 accumulation and output)
-  int dgrad(float* const* g, const long* w_off, float* const* out) {
+  // training on the tensor cores (BF16 operands, FP32 accumulation and output).  FP32: or of
+  // branches b0 .. b0 + nbr - 1 with cout-channel outputs (the main's concatenated input).
+  int dgrad(float* const* g, const long* w_off, float* const* out, int b0 = 0, int nbr = 0, int cout = 0) {
     if (h->tc_dgrad) {
       const TcMaps* maps = nullptr;
       CONET_TRY(dg_maps_for(w_off, &maps));
@@ -996,17 +1012,18 @@ struct Bwd {
       prof_end(h, s);
       return rc;
     }
+    if (!nbr) nbr = h->nb;
     ConvArgs c = {};
     c.M = (int)M;
     c.T = h->T;
     c.F = h->F;
-    for (int b = 0; b < h->nb; ++b) {
-      c.in[b] = g[b];
-      c.w[b] = h->wd + h->wd_off.at((size_t)w_off[b]);
-      c.out0[b] = out[b];
+    for (int i = 0; i < nbr; ++i) {
+      c.in[i] = g[b0 + i];
+      c.w[i] = h->wd + h->wd_off.at((size_t)w_off[b0 + i]);
+      c.out0[i] = out[b0 + i];
     }
     prof_begin(h, PK_BACKWARD, s);
-    const int rc = launch_conv3x3_fp32(c, h->nb, h->C, h->C, s);
+    const int rc = launch_conv3x3_fp32(c, nbr, h->C, cout ? cout : h->C, s);
     prof_end(h, s);
     return rc;
   }
@@ -1083,7 +1100,7 @@ struct Bwd {
     f.C = h->C;
     f.M = M;
     CONET_TRY(launch_fuse_bwd(f, s));
-    if (f.ln_g) CONET_TRY(reduce_ew(2 * h->C, h->L.fg[point]));
+    if (f.ln_g) CONET_TRY(reduce_ew(2 * fused_width(h->cfg, point), h->L.fg[point]));
     return CONET_OK;
   }
   int ln_relu(const float* g, const float* x, long lng, long lnb, const float* add, float* out) {
@@ -1117,33 +1134,52 @@ int net_backward(conet_s* h, const float* dllr, int B, cudaStream_t s) {
   float* const* G2 = h->G[2];
   float* nulw[MAX_BR] = {};
   // head: grad wrt the head input, dW_h and db_h (stored contiguously)
+  // (plain networks whose last layer concatenates: the head reads n_branches x width channels)
+  const bool wide_head = !h->cfg.residual && wide_at(h, depth - 1);
+  const int head_c = wide_head ? nb * C : C;
   HeadBwdArgs hb = {};
   hb.dllr = dllr;
-  hb.x0 = h->cfg.residual ? A.RXM(depth) : A.XM(depth - 1);
+  hb.x0 = h->cfg.residual ? A.RXM(depth) : wide_head ? xcat_at(h, depth - 1) : A.XM(depth - 1);
   hb.w = P(h, L.hw);
-  hb.gx0 = G0[0];
+  hb.gx0 = wide_head ? h->gcat : G0[0];
   hb.part = h->ew_part;
-  hb.C = C;
+  hb.C = head_c;
   hb.Q = h->Q;
   hb.M = bw.M;
   CONET_TRY(launch_head_bwd(hb, s));
-  CONET_TRY(bw.reduce_ew(h->Q * C + h->Q, L.hw));
+  CONET_TRY(bw.reduce_ew(h->Q * head_c + h->Q, L.hw));
   long w_off[MAX_BR], b_off[MAX_BR];
   if (!h->cfg.residual) {
     float* const* gxs = nulw;   // support gradients entering the top layer: zero
+    // with the concatenation interaction the main's fused activations and their gradients
+    // (gcat) are n_branches x width wide, and the main's convs after them run on their own
+    float* gmain[MAX_BR];
+    for (int b = 0; b < nb; ++b) gmain[b] = G0[b];
     for (int l = depth - 1; l >= 0; --l) {
       const float* u[MAX_BR];
       for (int b = 0; b < nb; ++b) u[b] = A.A(l, b);
-      CONET_TRY(bw.fuse(u, G0[0], gxs, G1, l, 1));
+      CONET_TRY(bw.fuse(u, wide_at(h, l) ? h->gcat : G0[0], gxs, G1, l, 1));
+      const bool wide_in = l > 0 && wide_at(h, l - 1);
       const float* x[MAX_BR];
       for (int b = 0; b < nb; ++b) {
-        x[b] = l == 0 ? h->X0 : (b == 0 ? A.XM(l - 1) : A.A(l - 1, b));
+        x[b] = l == 0 ? h->X0 : (b == 0 ? (wide_in ? xcat_at(h, l - 1) : A.XM(l - 1)) : A.A(l - 1, b));
         w_off[b] = l == 0 ? L.in_w[b] : L.lw[b][l - 1];
         b_off[b] = l == 0 ? L.in_b[b] : L.lb[b][l - 1];
       }
-      CONET_TRY(bw.wgrad(x, G1, l == 0, w_off, b_off));
+      if (wide_in) {
+        CONET_TRY(bw.wgrad(x, G1, false, w_off, b_off, 0, 1, nb * C));
+        CONET_TRY(bw.wgrad(x, G1, false, w_off, b_off, 1, nb - 1));
+      } else {
+        CONET_TRY(bw.wgrad(x, G1, l == 0, w_off, b_off));
+      }
       if (l > 0) {
-        CONET_TRY(bw.dgrad(G1, w_off, G0));
+        if (wide_in) {
+          gmain[0] = h->gcat;
+          CONET_TRY(bw.dgrad(G1, w_off, gmain, 0, 1, nb * C));
+          CONET_TRY(bw.dgrad(G1, w_off, G0, 1, nb - 1));
+        } else {
+          CONET_TRY(bw.dgrad(G1, w_off, G0));
+        }
         gxs = G0;
       }
     }

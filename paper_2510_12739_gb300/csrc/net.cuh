@@ -90,6 +90,7 @@ struct conet_s {
   std::vector<conet::TcMaps> dg_maps;        // per body conv (in wd_off order)
   std::map<size_t, size_t> dg_index;         // branch 0's conv weight offset -> dg_maps index
   float* xcat = nullptr;                     // FP32 plain networks, fuse_op 2: the concatenated main input
+  float* gcat = nullptr;                     // ... and, training, the gradient of a concatenated activation
   int* d_err = nullptr;                      // device error word of the tensor-core kernels
   // E4M3 path
   float* fp8_wscale = nullptr;               // per conv: [Cout] per-output-channel weight scales

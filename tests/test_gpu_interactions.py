@@ -83,11 +83,14 @@ def test_unsupported_combinations_are_refused():
 
 @pytest.mark.parametrize("kw", VARIANTS + [dict(fuse_op=1, norm=1), dict(feedback=1, norm=1, fuse_mask=0b0101),
                                 dict(fuse_op=1, residual=1, norm=1), dict(feedback=1, residual=1, norm=1),
-                                dict(fuse_op=1, feedback=1, residual=1, norm=1, fuse_mask=0b101)])
+                                dict(fuse_op=1, feedback=1, residual=1, norm=1, fuse_mask=0b101),
+                                dict(fuse_op=2), dict(fuse_op=2, norm=1), dict(fuse_op=2, feedback=1, norm=1, fuse_mask=0b101)])
 def test_training_gradients_fp32(kw):
     """Backward of the sum interaction and of Example II's feedback (FP32 plain and residual
-    networks): the GPU gradient against the FP64 oracle's, per parameter tensor, within the
-    product-fusion bar (2e-4 normwise)."""
+    networks) and of the concatenation (plain networks: the fusion backward splits the
+    gradient of the wide activation back to the branches, the main's wide conv has its own
+    weight and data gradients): the GPU gradient against the FP64 oracle's, per parameter
+    tensor, within the product-fusion bar (2e-4 normwise)."""
     from oracle import net as onet, rx as orx
     from paper_2510_12739_gb300 import api
     from workloads import random_grid
@@ -171,11 +174,11 @@ def test_concatenation_fp32(kw):
     assert np.all(np.isfinite(L)) and err < 1e-4, err
 
 
-def test_concatenation_refused_outside_fp32_inference():
+def test_concatenation_refused_outside_fp32():
     from paper_2510_12739_gb300 import api
     from paper_2510_12739_gb300._lib import ConetError
     net = replace(WORKLOADS["plain_14x72_b16_fp32"].net, fuse_op=2, n_sc=40)
-    for prec, train in (("bf16", False), ("fp8", False), ("fp32", True)):
+    for prec, train in (("bf16", False), ("fp8", False), ("bf16", True)):
         with pytest.raises(ConetError) as e:
             api.Receiver(net, prec, max_batch=1, train=train)
         assert e.value.code == -8
