@@ -95,7 +95,7 @@ typedef enum {
  *   feedback         : 1 = Example II (Sec. III, Fig. "conet2"): at every fusion point each
  *                      support net continues with its own activation plus the main net's
  *                      (taken before the fusion).
- *   fuse_op = 1 and feedback = 1 train only on FP32 handles, feedback without recompute
+ *   fuse_op = 1 trains on FP32 and BF16 handles, feedback = 1 on FP32 handles without recompute
  *   (train = 1 otherwise returns CONET_ERR_UNSUPPORTED), and on the tensor-core paths (inference) need
  *   a network whose accumulators fit TMEM twice (not the 4 x 96 network).
  *   depthwise        : residual networks: 1 = every conv inside an RB / MRB is depthwise-

@@ -107,11 +107,13 @@ int net_forward_tc(conet_s* h, const float* Y, const uint8_t* mask, int B, float
 
 int net_setup(conet_s* h) {
   // (Example II's feedback adds the main activation into the supports' rows in place, so a
-  // per-block recompute would add it twice)
-  if ((h->cfg.fuse_op || h->cfg.feedback) && h->cfg.train &&
-      (h->prec != CONET_FP32 || (h->cfg.residual && h->cfg.recompute && h->cfg.feedback)))
+  // per-block recompute would add it twice; the tensor-core epilogue's training tape holds a
+  // support's activation before the feedback, so BF16 handles train the sum interaction only)
+  if (h->cfg.train && ((h->cfg.feedback && (h->prec != CONET_FP32 || (h->cfg.residual && h->cfg.recompute))) ||
+                       (h->cfg.fuse_op == 1 && h->prec != CONET_FP32 && h->prec != CONET_BF16)))
     return fail(CONET_ERR_UNSUPPORTED,
-                "sum interaction and Example II feedback train on FP32 handles only (feedback: without recompute)");
+                "training: the sum interaction on FP32 / BF16 handles, Example II feedback on FP32 handles "
+                "without recompute");
   if (h->cfg.fuse_op == 2 && h->prec != CONET_FP32)
     return fail(CONET_ERR_UNSUPPORTED, "concatenation (fuse_op 2): FP32 handles only");
   if (h->cfg.depthwise && (!h->cfg.residual || (h->cfg.train && h->prec != CONET_FP32) ||

@@ -94,6 +94,27 @@ def test_bf16_training_gradients(n_sc, B):
     check_grads(net, g, g16, tol=2e-3)
 
 
+@pytest.mark.parametrize("kw", [dict(fuse_op=1), dict(fuse_op=1, fuse_mask=0b1011)])
+def test_bf16_training_gradients_sum_interaction(kw):
+    """A BF16 training handle with the sum interaction at the fusion points (the tensor-core
+    run-time epilogue forms the sum; the FP32 fusion backward passes the gradient to every
+    branch unchanged): against the oracle's 16-bit training emulation at the BF16 bar."""
+    from oracle import half, net as onet, rx as orx
+    w = WORKLOADS["train_14x72_b128_bf16"]
+    net = replace(w.net, n_sc=24, **kw)
+    B = 3
+    L, _, g, _ = grad_pair(net, w.sim, B, precision="bf16")
+    ref = oracle_inputs(net, w.sim, 3, 0, B)
+    params = onet.init_params(net, 4)
+    params = (params + 0.05 * np.random.default_rng(4).standard_normal(params.size)).astype(np.float32)
+    Yd = ref["Y32"][..., 0].astype(np.float64) + 1j * ref["Y32"][..., 1]
+    X0 = orx.assemble_input(Yd, ref["pilot_sym"], ref["pilot_mask"])
+    assert normwise(L, half.forward_16(net, params.astype(np.float64), X0)) < 1e-3
+    dllr = random_grid(3 + 10, L.shape, scale=1e-3)
+    g16 = half.grad_16(net, params.astype(np.float64), X0, dllr.astype(np.float64))
+    print(f"bf16 training {kw}: worst {check_grads(net, g, g16, tol=2e-3)}")
+
+
 @pytest.mark.parametrize("name,kw", [("resid_14x624_b256_fp32", dict(n_sc=21, depth=2)),
                                      ("resnet_14x624_b256_fp32", dict(n_sc=13, depth=2)),
                                      ("resid_14x3276_b1024_bf16", dict(n_sc=11, depth=1))])

@@ -72,8 +72,8 @@ def test_unsupported_combinations_are_refused():
     with pytest.raises(ConetError) as e:                  # branch-group network on the tensor cores
         api.Receiver(replace(w.net, n_sc=29, feedback=1), "bf16", max_batch=1)
     assert e.value.code == -8
-    with pytest.raises(ConetError) as e:                  # training with the sum interaction: FP32 only
-        api.Receiver(replace(WORKLOADS["plain_14x72_b16_fp32"].net, fuse_op=1), "bf16", max_batch=1, train=True)
+    with pytest.raises(ConetError) as e:                  # training with feedback: FP32 only
+        api.Receiver(replace(WORKLOADS["plain_14x72_b16_fp32"].net, feedback=1), "bf16", max_batch=1, train=True)
     assert e.value.code == -8
     with pytest.raises(ConetError) as e:                  # feedback adds in place: no per-block recompute
         api.Receiver(replace(WORKLOADS["resid_14x624_b256_fp32"].net, n_sc=37, feedback=1), "fp32", max_batch=1,
