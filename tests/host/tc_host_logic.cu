@@ -29,6 +29,22 @@ void check_plan() {
   CHECK((long)K::THREADS * (K::EP == 3 ? 128 : 96) <= 65536);
 }
 
+// The one-tap stage of the 1x1 convs of depthwise-separable blocks (HALO = 2): the tile's
+// own rows and one weight tap per stage, Cin / KC K steps per tile, with the same fixed
+// epilogue shapes as the 3x3 body convs.
+template <int KI, int NB, int C>
+void check_pointwise_plan() {
+  constexpr int KC = tc_plan(KI, NB, C, C, false);
+  static_assert(KC > 0, "a one-tap stage plan exists");
+  using K = Cfg<KI, NB, C, C, KC, 2, 2>;
+  using K3 = Cfg<KI, NB, C, C, tc_kc(KI, NB, C, C), tc_halo(KI, NB, C, C), 2>;
+  CHECK(K::TAPS == 1 && K::A_BOX == TILE_M);
+  CHECK(K::K_ITERS == C / KC);
+  CHECK(K::STAGE_TX == K::G * (TILE_M * K::ROW + (C / 2) * K::ROW));   // both TMA boxes of a stage
+  CHECK(K::SMEM <= SMEM_LIMIT && K::STAGES >= 2);
+  CHECK(K::TMEM_COLS == K3::TMEM_COLS && K::EP == K3::EP && K::STAGED == K3::STAGED);
+}
+
 static TcConvArgs base_args(int nb) {
   static float f[64];
   static float out[64];
@@ -43,6 +59,10 @@ static TcConvArgs base_args(int nb) {
 }
 
 int main() {
+  check_pointwise_plan<0, 2, 32>();
+  check_pointwise_plan<0, 3, 64>();
+  check_pointwise_plan<0, 4, 96>();
+  check_pointwise_plan<3, 3, 64>();
   check_plan<0, 3, 16, 64>();
   check_plan<0, 3, 64, 64>();
   check_plan<0, 4, 16, 96>();
